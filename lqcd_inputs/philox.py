@@ -1,0 +1,61 @@
+"""Philox4x32-10 counter-based generator (Salmon et al., SC 2011) and Box-Muller normals.
+
+One Philox call maps a 128-bit counter and a 64-bit key to 128 random bits.  Ten rounds; each
+round multiplies counter words 0 and 2 by the published multipliers, mixes the high halves with
+words 1 and 3 and the key, and the key is advanced by the published Weyl increments between
+rounds.  Implemented with numpy uint64 arithmetic on whole index arrays.
+"""
+import numpy as np
+
+_MASK = np.uint64(0xFFFFFFFF)
+_M0 = np.uint64(0xD2511F53)
+_M1 = np.uint64(0xCD9E8D57)
+_W0 = np.uint64(0x9E3779B9)
+_W1 = np.uint64(0xBB67AE85)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Return the four 32-bit output words (uint32 arrays) for counters (c0..c3) and key (k0, k1).
+
+    Counter words may be arrays (broadcast together); the key words are scalars.
+    """
+    c0 = np.asarray(c0, dtype=np.uint64) & _MASK
+    c1 = np.asarray(c1, dtype=np.uint64) & _MASK
+    c2 = np.asarray(c2, dtype=np.uint64) & _MASK
+    c3 = np.asarray(c3, dtype=np.uint64) & _MASK
+    c0, c1, c2, c3 = np.broadcast_arrays(c0, c1, c2, c3)
+    k0 = np.uint64(int(k0) & 0xFFFFFFFF)
+    k1 = np.uint64(int(k1) & 0xFFFFFFFF)
+    for _ in range(10):
+        p0 = _M0 * c0
+        p1 = _M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+        k0 = (k0 + _W0) & _MASK
+        k1 = (k1 + _W1) & _MASK
+    return tuple(c.astype(np.uint32) for c in (c0, c1, c2, c3))
+
+
+def uniforms(seed, purpose, index):
+    """Two uniforms in (0, 1) with 53-bit resolution per index: shape index.shape + (2,).
+
+    Counter = (index low word, index high word, purpose, 0); key = (seed low, seed high).
+    """
+    index = np.asarray(index, dtype=np.uint64)
+    seed = int(seed)
+    w = philox4x32_10(index & _MASK, index >> np.uint64(32), np.uint64(purpose), 0,
+                      seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    w = [x.astype(np.float64) for x in w]
+    # 27 high bits of one word and 26 of the next make a 53-bit integer; +0.5 keeps it off 0 and 1.
+    u1 = (np.floor(w[0] / 32.0) * 67108864.0 + np.floor(w[1] / 64.0) + 0.5) / 9007199254740992.0
+    u2 = (np.floor(w[2] / 32.0) * 67108864.0 + np.floor(w[3] / 64.0) + 0.5) / 9007199254740992.0
+    return np.stack([u1, u2], axis=-1)
+
+
+def gaussians(seed, purpose, index):
+    """Two independent N(0,1) numbers per index (Box-Muller): shape index.shape + (2,)."""
+    u = uniforms(seed, purpose, index)
+    r = np.sqrt(-2.0 * np.log(u[..., 0]))
+    th = 2.0 * np.pi * u[..., 1]
+    return np.stack([r * np.cos(th), r * np.sin(th)], axis=-1)

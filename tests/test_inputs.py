@@ -1,0 +1,56 @@
+"""Seeded input generators: Philox known answers, SU(3) links, orthonormal colour vectors."""
+import os
+
+import numpy as np
+
+from lqcd_inputs import (philox4x32_10, gauge_field, colour_vectors, random_spinors,
+                         random_gauge_transform, gell_mann)
+
+HERE = os.path.dirname(__file__)
+
+
+def test_philox_known_answers():
+    for line in open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out = philox4x32_10(w[0], w[1], w[2], w[3], w[4], w[5])
+        assert [int(o) for o in out] == w[6:10]
+
+
+def test_gell_mann_algebra():
+    l = gell_mann()
+    for a in range(8):
+        assert np.allclose(l[a], l[a].conj().T)
+        assert abs(np.trace(l[a])) < 1e-15
+        for b in range(8):
+            assert np.isclose(np.trace(l[a] @ l[b]).real, 2.0 * (a == b))
+
+
+def test_gauge_field_su3_and_deterministic():
+    dims = (4, 4, 2, 4)
+    U = gauge_field(dims, 0.5, 7)
+    I = np.einsum("...ab,...cb->...ac", U, U.conj())
+    assert np.abs(I - np.eye(3)).max() < 1e-13
+    assert np.abs(np.linalg.det(U) - 1).max() < 1e-13
+    assert np.array_equal(U, gauge_field(dims, 0.5, 7))
+    assert not np.allclose(U, gauge_field(dims, 0.5, 8))
+    # eps -> 0 approaches the unit field
+    assert np.abs(gauge_field(dims, 1e-9, 7) - np.eye(3)).max() < 1e-8
+
+
+def test_colour_vectors_orthonormal_and_subset_consistent():
+    dims = (4, 4, 4, 4)
+    V = colour_vectors(dims, 6, 11)
+    for t in range(4):
+        X = V[t].reshape(6, -1)
+        assert np.abs(X @ X.conj().T - np.eye(6)).max() < 1e-13
+    Vs = colour_vectors(dims, 6, 11, timeslices=[2])
+    assert np.array_equal(Vs[0], V[2])
+
+
+def test_random_fields_shapes():
+    psi = random_spinors((2, 2, 2, 4), 3, 1)
+    assert psi.shape == (3, 4, 2, 2, 2, 4, 3)
+    G = random_gauge_transform((2, 2, 2, 4), 3)
+    assert np.abs(np.einsum("...ab,...cb->...ac", G, G.conj()) - np.eye(3)).max() < 1e-13
