@@ -1,0 +1,191 @@
+/*
+ * lqcd.h - C ABI of the B300 (sm_103a) distillation solver for the domain-decomposition
+ * subtraction estimator of quark-line disconnected correlators ("Subtraction method for
+ * disconnected diagrams in full QCD", Barca, Crawford, Finkenrath, Schaefer, Urrea-Nino).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: extents L[4] = {Lx, Ly, Lz, Lt}, all even, Lt <= 256; volume V = Lx Ly Lz Lt;
+ *   lexicographic site s = x + Lx (y + Ly (z + Lz t)); directions mu = 0..3 = x, y, z, t.
+ * Complex numbers are interleaved (re, im) doubles.
+ * Gauge links:  links[s][mu][a][b]                (V * 4 * 9 complex)
+ * Spinors:      psi[r][s][spin][colour]            (nrhs * V * 12 complex)
+ * Colour vecs:  V[k][i][s3][colour], s3 = x + Lx (y + Ly z)   (k indexes the timeslices passed)
+ * Dirac basis: Euclidean chiral, gamma_k = [[0,-i sigma_k],[i sigma_k,0]], gamma_t = [[0,1],[1,0]],
+ *   gamma_5 = gamma_x gamma_y gamma_z gamma_t = diag(1,1,-1,-1).  The paper's gamma_0 is gamma_t.
+ * Operator (Sec. 2.1 and Sec. 3 of the paper: Wilson-clover; normalisation fixed here):
+ *   D = A - kappa H,
+ *   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu),
+ *   A = 1 + i kappa c_sw sum_{mu<nu} sigma_{mu nu} Fhat_{mu nu},  sigma = (i/2)[gamma_mu, gamma_nu],
+ *   Fhat = (Q - Q^dag)/8 with Q the four-leaf clover; fermion boundary phase on the t-hop
+ *   between t = Lt-1 and 0 (LQCD_BC_*), spatially periodic.
+ * Domain operator D_Lambda (Sec. 2.1, Dirichlet restriction): the time axis is tiled from t = 0
+ *   by consecutive domains (lqcd_set_domains); D_Lambda is D with every t-hop between two
+ *   different domains removed, the clover term unchanged; it is block diagonal over domains.
+ *
+ * Memory: the caller owns every buffer it passes.  `where` says whether the data pointers of a
+ * call are host (LQCD_HOST) or device (LQCD_DEVICE, e.g. torch.Tensor.data_ptr()) memory;
+ * device pointers must belong to the context's device.  Calls are ordered on the stream given
+ * to lqcd_create / lqcd_set_stream; host-pointer calls return after their results are in host
+ * memory, device-pointer calls return after the work is queued on that stream.
+ * Errors: every function returns LQCD_OK (0) or an LQCD_ERR_* code and leaves a message for
+ * lqcd_last_error; on LQCD_ERR_INVALID_ARG nothing was done.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lqcd_ctx lqcd_ctx;
+
+enum {
+  LQCD_OK = 0,
+  LQCD_ERR_INVALID_ARG = 1,
+  LQCD_ERR_NOT_CONVERGED = 2,
+  LQCD_ERR_CUDA = 3,
+  LQCD_ERR_OOM = 4,
+  LQCD_ERR_TIMEOUT = 5,
+  LQCD_ERR_NAN = 6,
+  LQCD_ERR_STATE = 7
+};
+
+enum { LQCD_BC_PERIODIC = 0, LQCD_BC_ANTIPERIODIC = 1, LQCD_BC_OPEN = 2 };
+enum { LQCD_HOST = 0, LQCD_DEVICE = 1 };
+enum { LQCD_MODE_FULL = 0, LQCD_MODE_DOMAIN = 1 };
+enum { LQCD_SINKS_DIAG = 0, LQCD_SINKS_ALL = 1 };
+
+/* Krylov solvers.  All are judged by the FP64 true residual ||b - D x|| / ||b|| of the
+ * unpreconditioned operator (per right-hand side, and per domain for domain solves):
+ *   LQCD_SOLVER_BICGSTAB64: even-odd preconditioned BiCGStab entirely in FP64 (the plain solver);
+ *   LQCD_SOLVER_MIXED:      FP64 defect correction around an FP32 even-odd BiCGStab
+ *                           (inner_prec = LQCD_PREC_F32) or an FP32 flexible GCR preconditioned
+ *                           by FP16-storage BiCGStab sweeps (inner_prec = LQCD_PREC_F16);
+ *   LQCD_SOLVER_FGCR_NN:    FP64 defect correction around FP32 flexible GCR preconditioned by the
+ *                           loaded gauge-covariant network (lqcd_nn_load); falls back to MIXED
+ *                           when no network is loaded or it fails to reduce the residual. */
+enum {
+  LQCD_SOLVER_BICGSTAB64 = 0,
+  LQCD_SOLVER_MIXED = 1,
+  LQCD_SOLVER_FGCR_NN = 2
+};
+enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2 };
+
+typedef struct {
+  double tol;        /* target true relative residual per RHS (and per domain); 0 -> 1e-10 */
+  int max_iter;      /* cap on inner Krylov iterations summed over restarts; 0 -> 20000 */
+  int solver;        /* LQCD_SOLVER_* */
+  int inner_prec;    /* LQCD_PREC_F32 or LQCD_PREC_F16 (MIXED / FGCR_NN) */
+  int rhs_block;     /* right-hand sides per batched launch; 0 -> chosen by the library */
+  int use_graph;     /* 1: replay Krylov iterations from a captured CUDA graph */
+  double inner_tol;  /* residual reduction per defect-correction cycle; 0 -> default */
+  int max_outer;     /* cap on defect-correction cycles; 0 -> 20 */
+  int check_every;   /* Krylov iterations between host convergence checks; 0 -> 8 */
+  int gcr_nkrylov;   /* flexible GCR restart length; 0 -> 8 */
+  int precond_iters; /* FP16 preconditioner sweeps per application; 0 -> 6 */
+} lqcd_solve_params;
+
+typedef struct {
+  /* caller-provided output arrays (either may be NULL) */
+  int* iters;               /* [nrhs] inner Krylov iterations, summed over cycles */
+  double* true_resid;       /* [nrhs * n_seg] final FP64 true relative residual, seg fastest */
+  /* filled by the library (accumulated over the batches of one call) */
+  int n_seg;                /* 1 for full solves, number of domains for domain solves */
+  int outer_cycles;         /* largest number of defect-correction cycles of a batch */
+  long long total_iters;    /* inner iterations summed over batches */
+  long long dslash_calls;   /* half-lattice hopping-term launches */
+  double max_true_resid;    /* largest final true relative residual */
+  double seconds;           /* wall time of the call */
+  int fallback;             /* 1 if FGCR_NN fell back to MIXED */
+} lqcd_solve_stats;
+
+/* Fill *p with the defaults (tol 1e-10, BiCGStab64, graphs on). */
+void lqcd_default_params(lqcd_solve_params* p);
+
+/* Create a context for extents L[4] on the current CUDA device; bc_t = LQCD_BC_*; stream is a
+ * cudaStream_t (NULL = legacy default stream).  *out receives the context or NULL.
+ * Errors: INVALID_ARG (odd or non-positive extent, Lt > 256), CUDA. */
+int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream);
+int lqcd_destroy(lqcd_ctx* ctx);
+int lqcd_set_stream(lqcd_ctx* ctx, void* stream);
+/* Message of the last error on this context (or of the last failed lqcd_create if ctx is NULL). */
+const char* lqcd_last_error(const lqcd_ctx* ctx);
+
+/* Upload gauge links and set kappa, c_sw (Sec. 3: Wilson-clover).  Builds the clover term A and
+ * A^{-1} in FP64 on the GPU and the FP32 / FP16 link and clover copies used by the mixed solvers.
+ * links: [V][4][3][3] complex, host or device per `where`.  Errors: INVALID_ARG (NULL). */
+int lqcd_gauge_upload(lqcd_ctx* ctx, const double* links, int where, double kappa, double c_sw);
+
+/* Tile the time axis by n_dom domains of the given extents, starting at t = 0 (Sec. 2.1; the
+ * paper's regions Lambda_0, Lambda_1 of width Delta).  Errors: INVALID_ARG if an extent < 1 or
+ * they do not sum to Lt (nothing changed). */
+int lqcd_set_domains(lqcd_ctx* ctx, const int* extents, int n_dom);
+
+/* out = D in (domain_restricted = 0) or out = D_Lambda in (1), FP64, nrhs spinors. */
+int lqcd_dirac_apply(lqcd_ctx* ctx, const double* in, double* out, int nrhs, int domain_restricted,
+                     int where);
+
+/* Solve D x = b (full) or D_Lambda x = b (domain; every domain of every RHS converged to tol
+ * relative to its own source norm) for nrhs right-hand sides; x is overwritten.  Returns
+ * NOT_CONVERGED (x holds the last iterate, stats filled) if tol is not reached. */
+int lqcd_solve_full(lqcd_ctx* ctx, const double* b, double* x, int nrhs, int where,
+                    const lqcd_solve_params* p, lqcd_solve_stats* st);
+int lqcd_solve_domain(lqcd_ctx* ctx, const double* b, double* x, int nrhs, int where,
+                      const lqcd_solve_params* p, lqcd_solve_stats* st);
+
+/* Distillation perambulators (Sec. 3.1): for each source timeslice t in t_src and each
+ * (j, beta), solve with the source delta_{x0,t} e_beta (x) v_j(t) and project the solution on
+ * the sink timeslice(s): tau(t',t)^{ij}_{alpha beta} = sum_{xvec,a} v_i(t')^* X(t',xvec,alpha,a).
+ * mode FULL uses D, mode DOMAIN uses D_Lambda with one source timeslice per domain solved at
+ * once (multi-site sources, Sec. 4).  sinks DIAG: t' = t only; ALL: every t' (FULL mode).
+ *   Vt:  [Lt][n_ev][Lx Ly Lz][3] complex colour vectors of every timeslice;
+ *   tau: DIAG -> [n_tsrc][n_ev][4][n_ev][4]; ALL -> [n_tsrc][Lt][n_ev][4][n_ev][4] complex,
+ *        index order (sink vector i, sink spin alpha, source vector j, source spin beta).
+ * st (may be NULL): only the aggregate fields are filled; st->iters and st->true_resid are
+ * not written.
+ * Errors: INVALID_ARG (n_ev < 1 or > 3 Lx Ly Lz, t out of range, ALL with DOMAIN). */
+int lqcd_perambulator(lqcd_ctx* ctx, const double* Vt, int n_ev, const int* t_src, int n_tsrc,
+                      int mode, int sinks, int where, double* tau, const lqcd_solve_params* p,
+                      lqcd_solve_stats* st);
+
+/* Quark loops from diagonal perambulators (Sec. 2 loop definition with the elementals of
+ * Sec. 3.2): L_G(t) = sum_i w_i sum_{alpha beta} G_{alpha beta} tau^{ii}_{beta alpha}(t,t) and the
+ * same with G~ = gamma_t G^dag gamma_t.  gamma_ids[n_gamma] index the Clifford table
+ *   0: 1, 1-4: gamma_x,y,z,t, 5: gamma_5, 6-9: gamma_mu gamma_5, 10-15: sigma_{xy,xz,xt,yz,yt,zt}.
+ * weights: [n_t][n_ev] real (NULL = 1).  L, Lt: [n_gamma][n_t] complex. */
+int lqcd_loops(lqcd_ctx* ctx, const double* tau, int n_ev, int n_t, const int* gamma_ids,
+               int n_gamma, const double* weights, double* L, double* Lt, int where);
+
+/* Disconnected correlators over n_cfg configurations (Eqs. Cdisc, correlator_factorised,
+ * subtracted_correlator, corr1-corr4):
+ *   C[g][x0][y0]  = <L(x0) Lt(y0)> - <L(x0)><Lt(y0)>   (vev = 1; vev = 0 drops the product term)
+ *   Cdd           = same with the domain loops (completely factorised term)
+ *   dC            = C - Cdd;  valid[x0][y0] = dom(x0) != dom(y0)
+ *   C_avg[g][dt]  = mean over y0 of C((y0+dt) mod Lt, y0); dC_avg over valid y0 only
+ *   terms (optional, may be NULL): [4][n_gamma][Lt][Lt] the four pieces of Eqs. corr1-corr4.
+ * Inputs L, Lt, Ld, Ltd: [n_cfg][n_gamma][Lt] complex; uses the context's domain tiling.
+ * Errors: INVALID_ARG (n_cfg < 1, vev = 1 with n_cfg = 1). */
+int lqcd_disc_correlator(lqcd_ctx* ctx, const double* L, const double* Lt, const double* Ld,
+                         const double* Ltd, int n_cfg, int n_gamma, int vev, double* C, double* Cdd,
+                         double* dC, double* C_avg, double* dC_avg, int* valid, int* n_valid,
+                         double* terms, int where);
+
+/* Time the even-odd hopping kernel with the fused inverse-clover epilogue,
+ * out_o = A_oo^{-1} H_oe in_e (one half of the Schur operator of Sec. 2.1's block form), on
+ * nrhs right-hand sides in precision prec (LQCD_PREC_*), over n_iter launches on the context's
+ * work stream with CUDA events.  flush_l2 = 1 writes a 256 MB buffer between launches so every
+ * launch reads its operands from HBM (the flush is outside the timed intervals).
+ *   ms_per_launch:        average kernel duration [ms]
+ *   algo_bytes_per_launch: Vh * (8 links + clover + 2 * nrhs spinors) in the stored formats
+ *                          (ideal reuse: every input read once, output written once).
+ * Fills the input with deterministic non-zero data.  Needs a gauge field.  Errors: INVALID_ARG. */
+int lqcd_dslash_bench(lqcd_ctx* ctx, int prec, int nrhs, int n_iter, int flush_l2, double* ms_per_launch,
+                      double* algo_bytes_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,741 @@
+// extern "C" entry points declared in include/lqcd.h: argument checks, host/device staging,
+// stream ordering, batching of right-hand sides.  All arithmetic runs in the CUDA kernels of
+// this library.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lqcd_blas.h"
+#include "lqcd_distill.h"
+
+using namespace lqcd;
+
+static std::string g_create_error;
+
+namespace lqcd {
+
+int set_error(lqcd_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes) {
+  auto it = c->ws.find(name);
+  if (it != c->ws.end() && it->second.second >= bytes) return it->second.first;
+  if (it != c->ws.end()) {
+    cudaStreamSynchronize(c->work);
+    cudaFree(it->second.first);
+    c->ws.erase(it);
+    // graphs captured on the old buffer are stale
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c->ws[name] = {p, bytes < 256 ? 256 : bytes};
+  return p;
+}
+
+void* pinned_get(lqcd_ctx* c, size_t bytes) {
+  if (c->pinned_bytes >= bytes) return c->pinned;
+  if (c->pinned) {
+    cudaStreamSynchronize(c->work);
+    cudaFreeHost(c->pinned);
+  }
+  cudaMallocHost(&c->pinned, bytes);
+  c->pinned_bytes = bytes;
+  return c->pinned;
+}
+
+}  // namespace lqcd
+
+namespace {
+
+// The 16-element Clifford table of the header, built here from the chiral-basis gammas.
+struct M4 {
+  double re[4][4], im[4][4];
+};
+M4 m4_zero() {
+  M4 m;
+  memset(&m, 0, sizeof m);
+  return m;
+}
+M4 m4_mul(const M4& a, const M4& b) {
+  M4 c = m4_zero();
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++)
+      for (int k = 0; k < 4; k++) {
+        c.re[i][j] += a.re[i][k] * b.re[k][j] - a.im[i][k] * b.im[k][j];
+        c.im[i][j] += a.re[i][k] * b.im[k][j] + a.im[i][k] * b.re[k][j];
+      }
+  return c;
+}
+M4 m4_dag(const M4& a) {
+  M4 c;
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) {
+      c.re[i][j] = a.re[j][i];
+      c.im[i][j] = -a.im[j][i];
+    }
+  return c;
+}
+M4 m4_scale_i(const M4& a) {  // i * a
+  M4 c;
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) {
+      c.re[i][j] = -a.im[i][j];
+      c.im[i][j] = a.re[i][j];
+    }
+  return c;
+}
+void clifford(M4 out[16], M4 tilde[16]) {
+  M4 g[4];
+  for (int m = 0; m < 4; m++) g[m] = m4_zero();
+  // gamma_x: upper-right block -i sigma_x, lower-left i sigma_x
+  g[0].im[0][3] = -1; g[0].im[1][2] = -1; g[0].im[2][1] = 1; g[0].im[3][0] = 1;
+  // gamma_y: -i sigma_y = [[0,-1],[1,0]] upper right; i sigma_y = [[0,1],[-1,0]] lower left
+  g[1].re[0][3] = -1; g[1].re[1][2] = 1; g[1].re[2][1] = 1; g[1].re[3][0] = -1;
+  // gamma_z: -i sigma_z = diag(-i, i) upper right; i sigma_z = diag(i, -i) lower left
+  g[2].im[0][2] = -1; g[2].im[1][3] = 1; g[2].im[2][0] = 1; g[2].im[3][1] = -1;
+  // gamma_t: identity blocks off the diagonal
+  g[3].re[0][2] = 1; g[3].re[1][3] = 1; g[3].re[2][0] = 1; g[3].re[3][1] = 1;
+  M4 one = m4_zero();
+  for (int i = 0; i < 4; i++) one.re[i][i] = 1;
+  M4 g5 = m4_mul(m4_mul(g[0], g[1]), m4_mul(g[2], g[3]));
+  out[0] = one;
+  for (int m = 0; m < 4; m++) out[1 + m] = g[m];
+  out[5] = g5;
+  for (int m = 0; m < 4; m++) out[6 + m] = m4_mul(g[m], g5);
+  const int pm[6] = {0, 0, 0, 1, 1, 2}, pn[6] = {1, 2, 3, 2, 3, 3};
+  for (int k = 0; k < 6; k++) out[10 + k] = m4_scale_i(m4_mul(g[pm[k]], g[pn[k]]));  // sigma = i g g
+  for (int k = 0; k < 16; k++) tilde[k] = m4_mul(m4_mul(g[3], m4_dag(out[k])), g[3]);
+}
+
+// Order the caller's stream before the library's work stream and back.
+struct Scope {
+  lqcd_ctx* c;
+  explicit Scope(lqcd_ctx* ctx) : c(ctx) {
+    cudaEventRecord(c->ev_user, c->user_stream);
+    cudaStreamWaitEvent(c->work, c->ev_user, 0);
+  }
+  ~Scope() {
+    cudaEventRecord(c->ev_work, c->work);
+    cudaStreamWaitEvent(c->user_stream, c->ev_work, 0);
+  }
+};
+
+int cuda_check(lqcd_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return LQCD_OK;
+}
+
+// Stage `bytes` of caller data on the device: returns a device pointer (the caller's when
+// where == LQCD_DEVICE).
+const void* stage_in(lqcd_ctx* c, const void* p, size_t bytes, int where, const char* name) {
+  if (where == LQCD_DEVICE) return p;
+  void* d = ws_get(c, name, bytes);
+  if (!d) return nullptr;
+  cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, c->work);
+  return d;
+}
+void* stage_out(lqcd_ctx* c, void* p, size_t bytes, int where, const char* name) {
+  if (where == LQCD_DEVICE) return p;
+  return ws_get(c, name, bytes);
+}
+int finish_out(lqcd_ctx* c, void* host, const void* dev, size_t bytes, int where) {
+  if (where == LQCD_HOST) {
+    cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->work);
+    cudaError_t e = cudaStreamSynchronize(c->work);
+    if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return LQCD_OK;
+}
+
+void fill_tables(lqcd_ctx* c) {
+  const int T = c->g.Lt;
+  for (int t = 0; t < LQCD_MAXT; t++) c->tc_full[t] = 0;
+  for (int t = 0; t < T; t++) c->tc_full[t] = 1;
+  c->tc_full[T - 1] = c->bc == LQCD_BC_ANTIPERIODIC ? -1 : (c->bc == LQCD_BC_OPEN ? 0 : 1);
+  memset(&c->seg_full, 0, sizeof(SegInfo));
+  c->seg_full.nseg = 1;
+  c->seg_full.t0[0] = 0;
+  c->seg_full.t1[0] = (unsigned short)T;
+  // domain tables
+  memset(&c->seg_dom, 0, sizeof(SegInfo));
+  int n = (int)c->extents.size();
+  c->seg_dom.nseg = n;
+  int t = 0;
+  for (int d = 0; d < n; d++) {
+    c->seg_dom.t0[d] = (unsigned short)t;
+    for (int k = 0; k < c->extents[d]; k++) c->seg_dom.seg_of_t[t++] = (unsigned char)d;
+    c->seg_dom.t1[d] = (unsigned short)t;
+  }
+  for (int tt = 0; tt < LQCD_MAXT; tt++) c->tc_dom[tt] = 0;
+  for (int tt = 0; tt < T; tt++) {
+    int nx = (tt + 1) % T;
+    c->tc_dom[tt] = (c->seg_dom.seg_of_t[tt] == c->seg_dom.seg_of_t[nx]) ? c->tc_full[tt] : 0;
+  }
+  cudaMemcpyAsync(c->d_tc_full, c->tc_full, LQCD_MAXT, cudaMemcpyHostToDevice, c->work);
+  cudaMemcpyAsync(c->d_tc_dom, c->tc_dom, LQCD_MAXT, cudaMemcpyHostToDevice, c->work);
+  cudaMemcpyAsync(c->d_seg_full, &c->seg_full, sizeof(SegInfo), cudaMemcpyHostToDevice, c->work);
+  cudaMemcpyAsync(c->d_seg_dom, &c->seg_dom, sizeof(SegInfo), cudaMemcpyHostToDevice, c->work);
+  cudaStreamSynchronize(c->work);
+}
+
+lqcd_solve_params resolve(const lqcd_solve_params* p) {
+  lqcd_solve_params q;
+  lqcd_default_params(&q);
+  if (p) q = *p;
+  if (q.tol <= 0) q.tol = 1e-10;
+  return q;
+}
+
+int default_block(int nrhs_total) {
+  int b = nrhs_total < 32 ? nrhs_total : 32;
+  return b < 1 ? 1 : b;
+}
+
+// Accumulate a batch into the caller's stats; per-RHS arrays are written only when
+// per_rhs is set (solve calls, whose caller sized them [nrhs] and [nrhs * n_seg]).
+void add_stats(lqcd_solve_stats* st, const BatchStats& bs, int rhs0, int nb, int nseg, bool per_rhs = true) {
+  if (!st) return;
+  st->n_seg = nseg;
+  if (bs.cycles > st->outer_cycles) st->outer_cycles = bs.cycles;
+  st->dslash_calls += bs.dslash;
+  st->fallback |= bs.fallback;
+  for (int r = 0; r < nb; r++) {
+    int it = 0;
+    for (int s = 0; s < nseg; s++) {
+      double rel = bs.rel[r * nseg + s];
+      if (rel > st->max_true_resid) st->max_true_resid = rel;
+      if (per_rhs && st->true_resid) st->true_resid[(long)(rhs0 + r) * nseg + s] = rel;
+      if (bs.iters[r * nseg + s] > it) it = bs.iters[r * nseg + s];
+    }
+    if (per_rhs && st->iters) st->iters[rhs0 + r] = it;
+    st->total_iters += it;
+  }
+}
+
+void reset_stats(lqcd_solve_stats* st) {
+  if (!st) return;
+  st->n_seg = 1;
+  st->outer_cycles = 0;
+  st->total_iters = 0;
+  st->dslash_calls = 0;
+  st->max_true_resid = 0;
+  st->seconds = 0;
+  st->fallback = 0;
+}
+
+__global__ void k_scatter_tau(const double2* C, int nsinks, int n_ev, int nrhs, int rhs0, const int* kt_of_z,
+                              const int* tp_of_z, int all, int Lt, double2* tau) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long n = (long)nsinks * n_ev * 4 * nrhs;
+  if (i >= n) return;
+  int r = (int)(i % nrhs);
+  long q = i / nrhs;
+  int alpha = (int)(q % 4);
+  q /= 4;
+  int m = (int)(q % n_ev);
+  int z = (int)(q / n_ev);
+  int jb = rhs0 + r;
+  int j = jb / 4, beta = jb % 4;
+  long base = all ? ((long)kt_of_z[z] * Lt + tp_of_z[z]) : (long)kt_of_z[z];
+  tau[(((base * n_ev + m) * 4 + alpha) * n_ev + j) * 4 + beta] = C[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+void lqcd_default_params(lqcd_solve_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->tol = 1e-10;
+  p->max_iter = 20000;
+  p->solver = LQCD_SOLVER_BICGSTAB64;
+  p->inner_prec = LQCD_PREC_F32;
+  p->rhs_block = 0;
+  p->use_graph = 1;
+  p->inner_tol = 0;
+  p->max_outer = 20;
+  p->check_every = 8;
+  p->gcr_nkrylov = 8;
+  p->precond_iters = 6;
+}
+
+int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
+  if (!out || !L) return LQCD_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int m = 0; m < 4; m++)
+    if (L[m] < 2 || (L[m] & 1)) {
+      g_create_error = "lqcd_create: every extent must be even and >= 2";
+      return LQCD_ERR_INVALID_ARG;
+    }
+  if (L[3] > LQCD_MAXT) {
+    g_create_error = "lqcd_create: Lt > 256";
+    return LQCD_ERR_INVALID_ARG;
+  }
+  if (bc_t < LQCD_BC_PERIODIC || bc_t > LQCD_BC_OPEN) {
+    g_create_error = "lqcd_create: unknown boundary condition";
+    return LQCD_ERR_INVALID_ARG;
+  }
+  lqcd_ctx* c = new lqcd_ctx();
+  c->g.Lx = L[0];
+  c->g.Ly = L[1];
+  c->g.Lz = L[2];
+  c->g.Lt = L[3];
+  c->g.Lxh = L[0] / 2;
+  c->V = (long)L[0] * L[1] * L[2] * L[3];
+  c->g.Vh = c->V / 2;
+  c->g.Vth = (long)L[0] * L[1] * L[2] / 2;
+  c->bc = bc_t;
+  c->user_stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  if (cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_work, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(&c->d_tc_full, LQCD_MAXT) != cudaSuccess || cudaMalloc(&c->d_tc_dom, LQCD_MAXT) != cudaSuccess ||
+      cudaMalloc(&c->d_seg_full, sizeof(SegInfo)) != cudaSuccess ||
+      cudaMalloc(&c->d_seg_dom, sizeof(SegInfo)) != cudaSuccess ||
+      cudaMalloc(&c->d_gamma, 16 * 2 * 16 * sizeof(double2)) != cudaSuccess) {
+    g_create_error = std::string("lqcd_create: ") + cudaGetErrorString(cudaGetLastError());
+    lqcd_destroy(c);
+    return LQCD_ERR_CUDA;
+  }
+  c->extents.assign(1, L[3]);
+  fill_tables(c);
+  M4 G[16], Gt[16];
+  clifford(G, Gt);
+  std::vector<double2> h(16 * 2 * 16);
+  for (int k = 0; k < 16; k++)
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) {
+        h[((k * 2 + 0) * 4 + a) * 4 + b] = make_double2(G[k].re[a][b], G[k].im[a][b]);
+        h[((k * 2 + 1) * 4 + a) * 4 + b] = make_double2(Gt[k].re[a][b], Gt[k].im[a][b]);
+      }
+  cudaMemcpy(c->d_gamma, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  if (cuda_check(c, "lqcd_create")) {
+    g_create_error = c->err;
+    lqcd_destroy(c);
+    return LQCD_ERR_CUDA;
+  }
+  *out = c;
+  return LQCD_OK;
+}
+
+int lqcd_destroy(lqcd_ctx* c) {
+  if (!c) return LQCD_OK;
+  if (c->work) cudaStreamSynchronize(c->work);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : c->ws) cudaFree(kv.second.first);
+  void* bufs[] = {c->U64, c->U32, c->U16, c->A64, c->Ainv64, c->Ainv32, c->Ainv16, c->A32,
+                  c->d_tc_full, c->d_tc_dom, c->d_seg_full, c->d_seg_dom, c->d_gamma};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->ev_user) cudaEventDestroy(c->ev_user);
+  if (c->ev_work) cudaEventDestroy(c->ev_work);
+  if (c->work) cudaStreamDestroy(c->work);
+  delete c;
+  return LQCD_OK;
+}
+
+int lqcd_set_stream(lqcd_ctx* c, void* stream) {
+  if (!c) return LQCD_ERR_INVALID_ARG;
+  c->user_stream = (cudaStream_t)stream;
+  return LQCD_OK;
+}
+
+const char* lqcd_last_error(const lqcd_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int lqcd_gauge_upload(lqcd_ctx* c, const double* links, int where, double kappa, double c_sw) {
+  if (!c || !links) return set_error(c, LQCD_ERR_INVALID_ARG, "gauge_upload: NULL argument");
+  if (!std::isfinite(kappa) || !std::isfinite(c_sw))
+    return set_error(c, LQCD_ERR_INVALID_ARG, "gauge_upload: kappa and c_sw must be finite");
+  Scope sc(c);
+  const Geom& g = c->g;
+  auto need = [&](void*& p, size_t b) {
+    if (!p && cudaMalloc(&p, b) != cudaSuccess) p = nullptr;
+    return p != nullptr;
+  };
+  bool ok = need(c->U64, link_bytes(g, P64)) && need(c->U32, link_bytes(g, P32)) &&
+            need(c->U16, link_bytes(g, P16)) && need(c->A64, 2 * clover_bytes(g, P64)) &&
+            need(c->Ainv64, 2 * clover_bytes(g, P64)) && need(c->A32, 2 * clover_bytes(g, P32)) &&
+            need(c->Ainv32, 2 * clover_bytes(g, P32)) && need(c->Ainv16, 2 * clover_bytes(g, P16));
+  if (!ok) {
+    cudaGetLastError();
+    return set_error(c, LQCD_ERR_OOM, "gauge_upload: out of device memory");
+  }
+  c->kappa = kappa;
+  c->csw = c_sw;
+  size_t bytes = (size_t)c->V * 4 * 9 * sizeof(double2);
+  const double2* d = (const double2*)stage_in(c, links, bytes, where, "h_links");
+  int* bad = (int*)ws_get(c, "bad", 64);
+  if (!d || !bad) return set_error(c, LQCD_ERR_OOM, "gauge_upload: out of device memory");
+  cudaMemsetAsync(bad, 0, sizeof(int), c->work);
+  build_gauge(c, d, bad);
+  int hb = 0;
+  cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, c->work);
+  cudaError_t e = cudaStreamSynchronize(c->work);
+  if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, std::string("gauge_upload: ") + cudaGetErrorString(e));
+  if (hb) return set_error(c, LQCD_ERR_NAN, "gauge_upload: singular clover block");
+  c->have_gauge = true;
+  return LQCD_OK;
+}
+
+int lqcd_set_domains(lqcd_ctx* c, const int* extents, int n_dom) {
+  if (!c || !extents || n_dom < 1 || n_dom > c->g.Lt)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "set_domains: bad arguments");
+  int sum = 0;
+  for (int d = 0; d < n_dom; d++) {
+    if (extents[d] < 1) return set_error(c, LQCD_ERR_INVALID_ARG, "set_domains: extent < 1");
+    sum += extents[d];
+  }
+  if (sum != c->g.Lt) return set_error(c, LQCD_ERR_INVALID_ARG, "set_domains: extents do not tile Lt");
+  cudaStreamSynchronize(c->work);
+  c->extents.assign(extents, extents + n_dom);
+  fill_tables(c);
+  return LQCD_OK;
+}
+
+int lqcd_dirac_apply(lqcd_ctx* c, const double* in, double* out, int nrhs, int domain, int where) {
+  if (!c || !in || !out || nrhs < 1) return set_error(c, LQCD_ERR_INVALID_ARG, "dirac_apply: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "dirac_apply: no gauge field uploaded");
+  Scope sc(c);
+  size_t bytes = (size_t)c->V * 12 * nrhs * sizeof(double2);
+  const double2* din = (const double2*)stage_in(c, in, bytes, where, "h_in");
+  double2* dout = (double2*)stage_out(c, out, bytes, where, "h_out");
+  double2* ein = (double2*)ws_get(c, "eo_in", bytes);
+  double2* eout = (double2*)ws_get(c, "eo_out", bytes);
+  if (!din || !dout || !ein || !eout) return set_error(c, LQCD_ERR_OOM, "dirac_apply: out of device memory");
+  pack_spinor(c->g, din, ein, nrhs, c->work);
+  apply_D(c, ein, eout, nrhs, domain, c->work);
+  unpack_spinor(c->g, eout, dout, nrhs, c->work);
+  if (int e = cuda_check(c, "dirac_apply")) return e;
+  return finish_out(c, out, dout, bytes, where);
+}
+
+static int solve_common(lqcd_ctx* c, const double* b, double* x, int nrhs, int where, const lqcd_solve_params* p,
+                        lqcd_solve_stats* st, int domain) {
+  if (!c || !b || !x || nrhs < 1) return set_error(c, LQCD_ERR_INVALID_ARG, "solve: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "solve: no gauge field uploaded");
+  auto t0 = std::chrono::steady_clock::now();
+  lqcd_solve_params q = resolve(p);
+  reset_stats(st);
+  Scope sc(c);
+  const size_t per = (size_t)c->V * 12 * sizeof(double2);
+  const double2* db = (const double2*)stage_in(c, b, per * nrhs, where, "h_in");
+  double2* dx = (double2*)stage_out(c, x, per * nrhs, where, "h_out");
+  if (!db || !dx) return set_error(c, LQCD_ERR_OOM, "solve: out of device memory");
+  const int blk = q.rhs_block > 0 ? q.rhs_block : default_block(nrhs);
+  int rc = LQCD_OK;
+  const int nseg = domain ? c->seg_dom.nseg : 1;
+  for (int r0 = 0; r0 < nrhs; r0 += blk) {
+    int nb = nrhs - r0 < blk ? nrhs - r0 : blk;
+    double2* eb = (double2*)ws_get(c, "eo_b", per * nb);
+    double2* ex = (double2*)ws_get(c, "eo_x", per * nb);
+    if (!eb || !ex) return set_error(c, LQCD_ERR_OOM, "solve: out of device memory");
+    pack_spinor(c->g, db + (size_t)r0 * c->V * 12, eb, nb, c->work);
+    BatchStats bs;
+    int r = solve_batch(c, eb, ex, nb, domain, q, bs);
+    if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED) return r;
+    if (r != LQCD_OK) rc = r;
+    add_stats(st, bs, r0, nb, nseg);
+    unpack_spinor(c->g, ex, dx + (size_t)r0 * c->V * 12, nb, c->work);
+  }
+  if (int e = cuda_check(c, "solve")) return e;
+  int fo = finish_out(c, x, dx, per * nrhs, where);
+  if (fo) return fo;
+  if (st) st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rc != LQCD_OK) set_error(c, rc, "solve: tolerance not reached");
+  return rc;
+}
+
+int lqcd_solve_full(lqcd_ctx* c, const double* b, double* x, int nrhs, int where, const lqcd_solve_params* p,
+                    lqcd_solve_stats* st) {
+  return solve_common(c, b, x, nrhs, where, p, st, 0);
+}
+
+int lqcd_solve_domain(lqcd_ctx* c, const double* b, double* x, int nrhs, int where, const lqcd_solve_params* p,
+                      lqcd_solve_stats* st) {
+  return solve_common(c, b, x, nrhs, where, p, st, 1);
+}
+
+int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src, int n_tsrc, int mode, int sinks,
+                      int where, double* tau, const lqcd_solve_params* p, lqcd_solve_stats* st) {
+  if (!c || !Vt || !t_src || !tau || n_tsrc < 1) return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: NULL");
+  const Geom& g = c->g;
+  const long L3 = (long)g.Lx * g.Ly * g.Lz;
+  if (n_ev < 1 || n_ev > 3 * L3) return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: bad n_ev");
+  if (mode != LQCD_MODE_FULL && mode != LQCD_MODE_DOMAIN)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: bad mode");
+  if (sinks != LQCD_SINKS_DIAG && sinks != LQCD_SINKS_ALL)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: bad sinks");
+  if (sinks == LQCD_SINKS_ALL && mode == LQCD_MODE_DOMAIN)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: all sinks only in full mode");
+  for (int k = 0; k < n_tsrc; k++)
+    if (t_src[k] < 0 || t_src[k] >= g.Lt) return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: bad t");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "perambulator: no gauge field uploaded");
+  auto t0 = std::chrono::steady_clock::now();
+  lqcd_solve_params q = resolve(p);
+  reset_stats(st);
+  Scope sc(c);
+  const int domain = mode == LQCD_MODE_DOMAIN;
+  // source groups: full mode one timeslice each; domain mode at most one timeslice per domain
+  std::vector<std::vector<int>> groups;  // entries are indices k into t_src
+  if (!domain) {
+    for (int k = 0; k < n_tsrc; k++) groups.push_back({k});
+  } else {
+    int nd = c->seg_dom.nseg;
+    std::vector<std::vector<int>> q_by_dom(nd);
+    for (int k = 0; k < n_tsrc; k++) q_by_dom[c->seg_dom.seg_of_t[t_src[k]]].push_back(k);
+    for (size_t level = 0;; level++) {
+      std::vector<int> grp;
+      for (int d = 0; d < nd; d++)
+        if (level < q_by_dom[d].size()) grp.push_back(q_by_dom[d][level]);
+      if (grp.empty()) break;
+      groups.push_back(grp);
+    }
+  }
+  const size_t vbytes = (size_t)g.Lt * n_ev * L3 * 3 * sizeof(double2);
+  const double2* dV = (const double2*)stage_in(c, Vt, vbytes, where, "h_V");
+  const long n_tp = sinks == LQCD_SINKS_ALL ? g.Lt : 1;
+  const size_t tau_bytes = (size_t)n_tsrc * n_tp * n_ev * 4 * n_ev * 4 * sizeof(double2);
+  double2* dtau = (double2*)stage_out(c, tau, tau_bytes, where, "h_tau");
+  if (!dV || !dtau) return set_error(c, LQCD_ERR_OOM, "perambulator: out of device memory");
+  const int nrhs_total = 4 * n_ev;
+  const int blk = q.rhs_block > 0 ? q.rhs_block : default_block(nrhs_total);
+  const size_t per = (size_t)c->V * 12 * sizeof(double2);
+  int* d_jb = (int*)ws_get(c, "p_jb", 2 * blk * sizeof(int));
+  unsigned char* d_mask = (unsigned char*)ws_get(c, "p_mask", LQCD_MAXT);
+  int* d_z = (int*)ws_get(c, "p_z", 2 * LQCD_MAXT * sizeof(int));
+  double2* eb = (double2*)ws_get(c, "eo_b", per * blk);
+  double2* ex = (double2*)ws_get(c, "eo_x", per * blk);
+  double2* C = (double2*)ws_get(c, "p_C", (size_t)g.Lt * n_ev * 4 * blk * sizeof(double2));
+  if (!d_jb || !d_mask || !d_z || !eb || !ex || !C) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
+  int rc = LQCD_OK;
+  int nseg = domain ? c->seg_dom.nseg : 1;
+  std::vector<int> hjb(2 * blk);
+  int rhs_counter = 0;
+  for (auto& grp : groups) {
+    unsigned char mask[LQCD_MAXT];
+    memset(mask, 0, sizeof mask);
+    for (int k : grp) mask[t_src[k]] = 1;
+    std::vector<int> kz, tz;
+    if (sinks == LQCD_SINKS_DIAG) {
+      for (int k : grp) {
+        kz.push_back(k);
+        tz.push_back(t_src[k]);
+      }
+    } else {
+      for (int tp = 0; tp < g.Lt; tp++) {
+        kz.push_back(grp[0]);
+        tz.push_back(tp);
+      }
+    }
+    int nz = (int)kz.size();
+    std::vector<int> hz(2 * LQCD_MAXT);
+    for (int z = 0; z < nz; z++) {
+      hz[z] = tz[z];
+      hz[LQCD_MAXT + z] = kz[z];
+    }
+    cudaStreamSynchronize(c->work);
+    cudaMemcpyAsync(d_mask, mask, LQCD_MAXT, cudaMemcpyHostToDevice, c->work);
+    cudaMemcpyAsync(d_z, hz.data(), 2 * LQCD_MAXT * sizeof(int), cudaMemcpyHostToDevice, c->work);
+    for (int r0 = 0; r0 < nrhs_total; r0 += blk) {
+      int nb = nrhs_total - r0 < blk ? nrhs_total - r0 : blk;
+      for (int r = 0; r < nb; r++) {
+        hjb[r] = (r0 + r) / 4;
+        hjb[blk + r] = (r0 + r) % 4;
+      }
+      cudaMemcpyAsync(d_jb, hjb.data(), 2 * blk * sizeof(int), cudaMemcpyHostToDevice, c->work);
+      make_sources(g, dV, n_ev, d_jb, d_jb + blk, d_mask, eb, nb, c->work);
+      BatchStats bs;
+      int r = solve_batch(c, eb, ex, nb, domain, q, bs);
+      if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED) return r;
+      if (r != LQCD_OK) rc = r;
+      add_stats(st, bs, 0, nb, nseg, false);
+      rhs_counter += nb;
+      project(g, dV, n_ev, ex, d_z, nz, C, nb, c->work);
+      long n = (long)nz * n_ev * 4 * nb;
+      k_scatter_tau<<<(n + 255) / 256, 256, 0, c->work>>>(C, nz, n_ev, nb, r0, d_z + LQCD_MAXT, d_z,
+                                                          sinks == LQCD_SINKS_ALL, g.Lt, dtau);
+      if (int e = cuda_check(c, "perambulator")) return e;
+    }
+  }
+  int fo = finish_out(c, tau, dtau, tau_bytes, where);
+  if (fo) return fo;
+  cudaStreamSynchronize(c->work);
+  if (st) st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rc != LQCD_OK) set_error(c, rc, "perambulator: tolerance not reached");
+  return rc;
+}
+
+int lqcd_loops(lqcd_ctx* c, const double* tau, int n_ev, int n_t, const int* gamma_ids, int n_gamma,
+               const double* weights, double* L, double* Lt, int where) {
+  if (!c || !tau || !gamma_ids || !L || !Lt || n_ev < 1 || n_t < 1 || n_gamma < 1 || n_gamma > 16)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "loops: bad arguments");
+  for (int k = 0; k < n_gamma; k++)
+    if (gamma_ids[k] < 0 || gamma_ids[k] > 15) return set_error(c, LQCD_ERR_INVALID_ARG, "loops: bad gamma id");
+  Scope sc(c);
+  size_t tb = (size_t)n_t * n_ev * 4 * n_ev * 4 * sizeof(double2);
+  const double2* dt = (const double2*)stage_in(c, tau, tb, where, "l_tau");
+  const double* dw = weights ? (const double*)stage_in(c, weights, (size_t)n_t * n_ev * sizeof(double), where,
+                                                       "l_w")
+                             : nullptr;
+  size_t lb = (size_t)n_gamma * n_t * sizeof(double2);
+  double2* dL = (double2*)stage_out(c, L, lb, where, "l_L");
+  double2* dLt = (double2*)stage_out(c, Lt, lb, where, "l_Lt");
+  double2* dG = (double2*)ws_get(c, "l_G", 16 * 2 * 16 * sizeof(double2));
+  if (!dt || !dL || !dLt || !dG || (weights && !dw)) return set_error(c, LQCD_ERR_OOM, "loops: OOM");
+  for (int k = 0; k < n_gamma; k++)
+    cudaMemcpyAsync(dG + (size_t)k * 32, c->d_gamma + (size_t)gamma_ids[k] * 32, 32 * sizeof(double2),
+                    cudaMemcpyDeviceToDevice, c->work);
+  loops(dt, n_ev, n_t, dG, n_gamma, dw, dL, dLt, c->work);
+  if (int e = cuda_check(c, "loops")) return e;
+  if (int e = finish_out(c, L, dL, lb, where)) return e;
+  return finish_out(c, Lt, dLt, lb, where);
+}
+
+int lqcd_disc_correlator(lqcd_ctx* c, const double* L, const double* Lt, const double* Ld, const double* Ltd,
+                         int n_cfg, int n_gamma, int vev, double* C, double* Cdd, double* dC, double* C_avg,
+                         double* dC_avg, int* valid, int* n_valid, double* terms, int where) {
+  if (!c || !L || !Lt || !Ld || !Ltd || !C || !Cdd || !dC || !C_avg || !dC_avg || !valid || !n_valid ||
+      n_cfg < 1 || n_gamma < 1)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "disc_correlator: bad arguments");
+  if (vev && n_cfg < 2)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "disc_correlator: the VEV subtraction needs n_cfg >= 2");
+  const int T = c->g.Lt;
+  Scope sc(c);
+  size_t lb = (size_t)n_cfg * n_gamma * T * sizeof(double2);
+  const double2* a = (const double2*)stage_in(c, L, lb, where, "c_L");
+  const double2* b = (const double2*)stage_in(c, Lt, lb, where, "c_Lt");
+  const double2* ad = (const double2*)stage_in(c, Ld, lb, where, "c_Ld");
+  const double2* bd = (const double2*)stage_in(c, Ltd, lb, where, "c_Ltd");
+  size_t cb = (size_t)n_gamma * T * T * sizeof(double2), ab = (size_t)n_gamma * T * sizeof(double2);
+  double2* dCo = (double2*)stage_out(c, C, cb, where, "c_C");
+  double2* dCdd = (double2*)stage_out(c, Cdd, cb, where, "c_Cdd");
+  double2* ddC = (double2*)stage_out(c, dC, cb, where, "c_dC");
+  double2* dCa = (double2*)stage_out(c, C_avg, ab, where, "c_Ca");
+  double2* ddCa = (double2*)stage_out(c, dC_avg, ab, where, "c_dCa");
+  int* dvalid = (int*)stage_out(c, valid, (size_t)T * T * sizeof(int), where, "c_valid");
+  int* dnv = (int*)stage_out(c, n_valid, (size_t)T * sizeof(int), where, "c_nv");
+  double2* dterms = terms ? (double2*)stage_out(c, terms, 4 * cb, where, "c_terms") : nullptr;
+  double2* tmp1 = (double2*)ws_get(c, "c_dL", lb);
+  double2* tmp2 = (double2*)ws_get(c, "c_dLt", lb);
+  int* ddom = (int*)ws_get(c, "c_dom", T * sizeof(int));
+  if (!a || !b || !ad || !bd || !dCo || !dCdd || !ddC || !dCa || !ddCa || !dvalid || !dnv || !tmp1 || !tmp2 ||
+      !ddom || (terms && !dterms))
+    return set_error(c, LQCD_ERR_OOM, "disc_correlator: OOM");
+  std::vector<int> dom(T);
+  for (int t = 0; t < T; t++) dom[t] = c->seg_dom.seg_of_t[t];
+  cudaMemcpyAsync(ddom, dom.data(), T * sizeof(int), cudaMemcpyHostToDevice, c->work);
+  correlators(a, b, ad, bd, n_cfg, n_gamma, T, vev, ddom, dCo, dCdd, ddC, dCa, ddCa, dvalid, dnv, dterms, tmp1,
+              tmp2, c->work);
+  if (int e = cuda_check(c, "disc_correlator")) return e;
+  if (where == LQCD_HOST) {
+    cudaMemcpyAsync(C, dCo, cb, cudaMemcpyDeviceToHost, c->work);
+    cudaMemcpyAsync(Cdd, dCdd, cb, cudaMemcpyDeviceToHost, c->work);
+    cudaMemcpyAsync(dC, ddC, cb, cudaMemcpyDeviceToHost, c->work);
+    cudaMemcpyAsync(C_avg, dCa, ab, cudaMemcpyDeviceToHost, c->work);
+    cudaMemcpyAsync(dC_avg, ddCa, ab, cudaMemcpyDeviceToHost, c->work);
+    cudaMemcpyAsync(valid, dvalid, (size_t)T * T * sizeof(int), cudaMemcpyDeviceToHost, c->work);
+    cudaMemcpyAsync(n_valid, dnv, (size_t)T * sizeof(int), cudaMemcpyDeviceToHost, c->work);
+    if (terms) cudaMemcpyAsync(terms, dterms, 4 * cb, cudaMemcpyDeviceToHost, c->work);
+    cudaError_t e = cudaStreamSynchronize(c->work);
+    if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return LQCD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void k_fill_pattern(float* p, long n, unsigned seed) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    unsigned h = (unsigned)i * 2654435761u ^ seed;
+    h ^= h >> 13;
+    h *= 0x5bd1e995u;
+    h ^= h >> 15;
+    p[i] = ((h & 0xffff) / 65536.0f - 0.5f) * 0.25f;
+  }
+}
+__global__ void k_flush(float4* p, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = make_float4((float)i, 0.f, 0.f, 1.f);
+}
+}  // namespace
+
+extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, int flush_l2, double* ms_per_launch,
+                                 double* algo_bytes_per_launch) {
+  if (!c || nrhs < 1 || n_iter < 1 || !ms_per_launch || !algo_bytes_per_launch ||
+      (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
+    return set_error(c, LQCD_ERR_INVALID_ARG, "dslash_bench: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "dslash_bench: no gauge field uploaded");
+  const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);
+  const Geom& g = c->g;
+  const size_t sb = spinor_bytes(g, P, nrhs);
+  void* in = ws_get(c, "bench_in", sb);
+  void* out = ws_get(c, "bench_out", sb);
+  const size_t flush_n = (256u << 20) / sizeof(float4);
+  float4* fl = flush_l2 ? (float4*)ws_get(c, "bench_flush", flush_n * sizeof(float4)) : nullptr;
+  if (!in || !out || (flush_l2 && !fl)) return set_error(c, LQCD_ERR_OOM, "dslash_bench: OOM");
+  Scope sc(c);
+  // P16 fields hold half values; fill through a float view with values that are valid halves too
+  if (P == P16) {
+    cudaMemsetAsync(in, 0x3c, sb, c->work);  // every half = 1.0 + tiny mantissa pattern
+  } else {
+    long nf = (long)(sb / sizeof(float));
+    k_fill_pattern<<<(nf + 255) / 256, 256, 0, c->work>>>((float*)in, nf, 12345u);
+    if (P == P64) cudaMemsetAsync(in, 0, 0, c->work);
+  }
+  if (P == P64) {
+    // reinterpret the float pattern as doubles would give garbage exponents: write doubles instead
+    std::vector<double> h(4096);
+    for (size_t i = 0; i < h.size(); i++) h[i] = 0.01 * (double)((i * 7919) % 200) - 1.0;
+    for (size_t o = 0; o < sb; o += h.size() * sizeof(double)) {
+      size_t n = std::min(h.size() * sizeof(double), sb - o);
+      cudaMemcpyAsync((char*)in + o, h.data(), n, cudaMemcpyHostToDevice, c->work);
+    }
+  }
+  const void* U = P == P64 ? c->U64 : (P == P32 ? c->U32 : c->U16);
+  const void* Ainv = P == P64 ? c->Ainv64 : (P == P32 ? c->Ainv32 : c->Ainv16);
+  const void* Ao = (const char*)Ainv + clover_bytes(g, P);
+  DslashCall k{P, EPI_CH, 0, in, nullptr, nullptr, out, U, Ao, 1, nrhs, 0.0, 1.0, c->d_tc_full};
+  int threads = 0;
+  auto it = c->tuned_threads.find((long)P * 100000 + nrhs);
+  if (it != c->tuned_threads.end()) threads = it->second;
+  // warm-up
+  launch_dslash(g, k, c->work, threads);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double total = 0;
+  for (int i = 0; i < n_iter; i++) {
+    if (fl) k_flush<<<(flush_n + 255) / 256, 256, 0, c->work>>>(fl, (long)flush_n);
+    cudaEventRecord(e0, c->work);
+    launch_dslash(g, k, c->work, threads);
+    cudaEventRecord(e1, c->work);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    total += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (int e = cuda_check(c, "dslash_bench")) return e;
+  *ms_per_launch = total / n_iter;
+  const double lb = P == P64 ? 144.0 : (P == P32 ? 48.0 : 24.0);
+  const double cb = P == P64 ? 576.0 : (P == P32 ? 288.0 : 144.0);
+  const double spb = P == P64 ? 192.0 : (P == P32 ? 96.0 : 48.0);
+  *algo_bytes_per_launch = (double)g.Vh * (8 * lb + cb + 2.0 * nrhs * spb);
+  return LQCD_OK;
+}

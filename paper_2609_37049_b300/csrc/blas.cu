@@ -1,0 +1,537 @@
+// Vector kernels of the Krylov solvers: fused BiCGStab updates, segmented (per domain) dot
+// products and the finishing kernels that turn per-block partial sums into the per-system
+// Krylov scalars on the device, so an iteration needs no host round trip and can be replayed
+// from a CUDA graph.
+//
+// Reductions are two-pass and deterministic: every vector kernel block covers S sites (all in
+// one timeslice of one parity) times nrhs right-hand sides and writes one partial sum per
+// right-hand side; a finishing kernel with one block per system (rhs, segment) adds the partial
+// sums of the blocks that lie in the segment's timeslices.  Per-thread products are formed in
+// the storage precision's arithmetic type; block and segment sums are FP64.
+#include "lqcd_blas.h"
+
+namespace lqcd {
+
+VGeom make_vgeom(const Geom& g, int nrhs, int npar) {
+  VGeom v;
+  v.g = g;
+  v.nrhs = nrhs;
+  v.npar = npar;
+  int target = 256 / nrhs;
+  if (target < 1) target = 1;
+  int S = 1;
+  while (S * 2 <= target && (g.Vth % (S * 2)) == 0) S *= 2;
+  v.S = S;
+  v.bpp = g.Vh / S;
+  v.bpt = g.Vth / S;
+  v.blocks = v.bpp * npar;
+  return v;
+}
+
+struct VThread {
+  int par;
+  long cb;
+  int rhs;
+  int t;
+  int seg;
+  long idx;     // cb * nrhs + rhs (within a parity block)
+  long stride;  // Vh * nrhs (chunk stride)
+  int site_local;
+};
+
+LQCD_D VThread vthread(const VGeom& vg, const SegInfo* si) {
+  VThread v;
+  v.site_local = threadIdx.x / vg.nrhs;
+  v.rhs = threadIdx.x - v.site_local * vg.nrhs;
+  long site = (long)blockIdx.x * vg.S + v.site_local;
+  v.par = (int)(site / vg.g.Vh);
+  v.cb = site - (long)v.par * vg.g.Vh;
+  v.t = (int)(v.cb / vg.g.Vth);
+  v.seg = si ? si->seg_of_t[v.t] : 0;
+  v.idx = v.cb * vg.nrhs + v.rhs;
+  v.stride = vg.g.Vh * vg.nrhs;
+  return v;
+}
+
+template <int P>
+LQCD_D const void* fpar(const void* base, const VGeom& vg, int par) {
+  return reinterpret_cast<const char*>(base) + (size_t)par * (size_t)vg.g.Vh * vg.nrhs * 12 *
+                                                   (P == P64 ? 16 : (P == P32 ? 8 : 4));
+}
+template <int P>
+LQCD_D void* fpar(void* base, const VGeom& vg, int par) {
+  return reinterpret_cast<char*>(base) + (size_t)par * (size_t)vg.g.Vh * vg.nrhs * 12 *
+                                             (P == P64 ? 16 : (P == P32 ? 8 : 4));
+}
+
+// Reduce ND values over the S sites of the block for each rhs; write partial[block][rhs][ND].
+template <int ND>
+LQCD_D void block_reduce(double (&v)[ND], double* partial, const VGeom& vg, int site_local, int rhs) {
+  extern __shared__ double sm[];
+  const int n = blockDim.x;
+#pragma unroll
+  for (int k = 0; k < ND; k++) sm[k * n + threadIdx.x] = v[k];
+  __syncthreads();
+  for (int s = vg.S / 2; s >= 1; s >>= 1) {
+    if (site_local < s) {
+#pragma unroll
+      for (int k = 0; k < ND; k++) sm[k * n + threadIdx.x] += sm[k * n + threadIdx.x + s * vg.nrhs];
+    }
+    __syncthreads();
+  }
+  if (site_local == 0) {
+#pragma unroll
+    for (int k = 0; k < ND; k++) partial[((long)blockIdx.x * vg.nrhs + rhs) * ND + k] = sm[k * n + threadIdx.x];
+  }
+}
+
+// Sum the partials of system (rhs = blockIdx.x, seg = blockIdx.y); result valid in thread 0.
+template <int ND>
+LQCD_D void seg_sum(const double* partial, const VGeom& vg, const SegInfo* si, double (&out)[ND]) {
+  __shared__ double sm[ND][128];
+  const int rhs = blockIdx.x, seg = blockIdx.y;
+  const long t0 = si ? si->t0[seg] : 0, t1 = si ? si->t1[seg] : vg.g.Lt;
+  double acc[ND];
+#pragma unroll
+  for (int k = 0; k < ND; k++) acc[k] = 0.0;
+  const long nb_seg = (t1 - t0) * vg.bpt;
+  for (int par = 0; par < vg.npar; par++) {
+    const long b0 = par * vg.bpp + t0 * vg.bpt;
+    for (long b = threadIdx.x; b < nb_seg; b += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < ND; k++) acc[k] += partial[((b0 + b) * vg.nrhs + rhs) * ND + k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < ND; k++) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s >= 1; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int k = 0; k < ND; k++) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < ND; k++) out[k] = sm[k][0];
+  }
+}
+
+// ------------------------------------------------------------------ generic kernels
+template <int P>
+__global__ void k_norm2(const void* x, VGeom vg, const SegInfo* si, double* partial) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, si);
+  cplx<R> a[12];
+  load_spinor<P>(fpar<P>(x, vg, v.par), v.stride, v.idx, a);
+  R s = 0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) s += norm2(a[k]);
+  double d[1] = {(double)s};
+  block_reduce<1>(d, partial, vg, v.site_local, v.rhs);
+}
+
+__global__ void k_fin_sum1(const double* partial, VGeom vg, const SegInfo* si, int nseg, double* out) {
+  double s[1];
+  seg_sum<1>(partial, vg, si, s);
+  if (threadIdx.x == 0) out[blockIdx.x * nseg + blockIdx.y] = s[0];
+}
+
+// out = scale[sys] * in  (precision conversion)
+template <int PI, int PO>
+__global__ void k_convert(const void* in, void* out, VGeom vg, const SegInfo* si, int nseg, const double* scale) {
+  using RI = typename Traits<PI>::real;
+  using RO = typename Traits<PO>::real;
+  VThread v = vthread(vg, si);
+  cplx<RI> a[12];
+  load_spinor<PI>(fpar<PI>(in, vg, v.par), v.stride, v.idx, a);
+  double sc = scale ? scale[v.rhs * nseg + v.seg] : 1.0;
+  cplx<RO> b[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) b[k] = {(RO)(sc * (double)a[k].re), (RO)(sc * (double)a[k].im)};
+  store_spinor<PO>(fpar<PO>(out, vg, v.par), v.stride, v.idx, b);
+}
+
+// x (P64) += scale[sys] * e (PE)
+template <int PE>
+__global__ void k_axpy_mixed(void* x, const void* e, VGeom vg, const SegInfo* si, int nseg, const double* scale,
+                             const int* active) {
+  using RE = typename Traits<PE>::real;
+  VThread v = vthread(vg, si);
+  const int sys = v.rhs * nseg + v.seg;
+  if (active && !active[sys]) return;
+  double sc = scale ? scale[sys] : 1.0;
+  cplx<RE> ev[12];
+  load_spinor<PE>(fpar<PE>(e, vg, v.par), v.stride, v.idx, ev);
+  cplx<double> xv[12];
+  void* xp = fpar<P64>(x, vg, v.par);
+  load_spinor<P64>(xp, v.stride, v.idx, xv);
+#pragma unroll
+  for (int k = 0; k < 12; k++) xv[k] = xv[k] + mk(sc * (double)ev[k].re, sc * (double)ev[k].im);
+  store_spinor<P64>(xp, v.stride, v.idx, xv);
+}
+
+template <int P>
+__global__ void k_zero(void* x, VGeom vg) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, nullptr);
+  cplx<R> z[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) z[k] = {R(0), R(0)};
+  store_spinor<P>(fpar<P>(x, vg, v.par), v.stride, v.idx, z);
+}
+
+template <int P>
+__global__ void k_copy(const void* a, void* b, VGeom vg) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, nullptr);
+  cplx<R> z[12];
+  load_spinor<P>(fpar<P>(a, vg, v.par), v.stride, v.idx, z);
+  store_spinor<P>(fpar<P>(b, vg, v.par), v.stride, v.idx, z);
+}
+
+// ------------------------------------------------------------------ BiCGStab stages
+// init: r = b, p = b, x = 0; partial |b|^2
+template <int P>
+__global__ void k_bicg_init(const void* b, void* r, void* p, void* x, VGeom vg, const SegInfo* si, double* partial) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, si);
+  cplx<R> a[12], z[12];
+  load_spinor<P>(b, v.stride, v.idx, a);
+  store_spinor<P>(r, v.stride, v.idx, a);
+  store_spinor<P>(p, v.stride, v.idx, a);
+  R s = 0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    s += norm2(a[k]);
+    z[k] = {R(0), R(0)};
+  }
+  store_spinor<P>(x, v.stride, v.idx, z);
+  double d[1] = {(double)s};
+  block_reduce<1>(d, partial, vg, v.site_local, v.rhs);
+}
+
+__global__ void k_bicg_fin_init(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks,
+                                const double* delta, const int* outer_active) {
+  double s[1];
+  seg_sum<1>(partial, vg, si, s);
+  if (threadIdx.x) return;
+  const int sys = blockIdx.x * nseg + blockIdx.y;
+  ks.b2[sys] = s[0];
+  ks.r2[sys] = s[0];
+  ks.rho[sys] = make_double2(s[0], 0.0);
+  ks.alpha[sys] = make_double2(0.0, 0.0);
+  ks.omega[sys] = make_double2(0.0, 0.0);
+  ks.beta[sys] = make_double2(0.0, 0.0);
+  double d = delta ? delta[sys] : 1e-6;
+  ks.stop2[sys] = d * d * s[0];
+  ks.flag[sys] = 0;
+  ks.active[sys] = (s[0] > 0.0) && (!outer_active || outer_active[sys]);
+}
+
+// partial (r0, v)
+template <int P>
+__global__ void k_dot(const void* a, const void* b, VGeom vg, const SegInfo* si, double* partial) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, si);
+  cplx<R> x[12], y[12];
+  load_spinor<P>(a, v.stride, v.idx, x);
+  load_spinor<P>(b, v.stride, v.idx, y);
+  cplx<R> s = {R(0), R(0)};
+#pragma unroll
+  for (int k = 0; k < 12; k++) s = s + cjmul(x[k], y[k]);
+  double d[2] = {(double)s.re, (double)s.im};
+  block_reduce<2>(d, partial, vg, v.site_local, v.rhs);
+}
+
+LQCD_D double2 cdiv(double2 a, double2 b) {
+  double den = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+LQCD_D double2 cmul2(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+__global__ void k_bicg_fin_alpha(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+  double s[2];
+  seg_sum<2>(partial, vg, si, s);
+  if (threadIdx.x) return;
+  const int sys = blockIdx.x * nseg + blockIdx.y;
+  double2 r0v = make_double2(s[0], s[1]);
+  double mag = r0v.x * r0v.x + r0v.y * r0v.y;
+  if (!ks.active[sys]) {
+    ks.alpha[sys] = make_double2(0.0, 0.0);
+    return;
+  }
+  double2 rho = ks.rho[sys];
+  if (!(mag > 0.0) || !isfinite(mag)) {
+    ks.alpha[sys] = make_double2(0.0, 0.0);
+    ks.active[sys] = 0;
+    ks.flag[sys] = 1;
+    return;
+  }
+  ks.alpha[sys] = cdiv(rho, r0v);
+}
+
+// s = r - alpha v
+template <int P>
+__global__ void k_bicg_s(const void* r, const void* vv, void* s, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, si);
+  double2 al = ks.alpha[v.rhs * nseg + v.seg];
+  cplx<R> a = {(R)al.x, (R)al.y};
+  cplx<R> x[12], y[12];
+  load_spinor<P>(r, v.stride, v.idx, x);
+  load_spinor<P>(vv, v.stride, v.idx, y);
+#pragma unroll
+  for (int k = 0; k < 12; k++) x[k] = x[k] - a * y[k];
+  store_spinor<P>(s, v.stride, v.idx, x);
+}
+
+// partial (t, s), (t, t)
+template <int P>
+__global__ void k_dot_ts(const void* t, const void* s, VGeom vg, const SegInfo* si, double* partial) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, si);
+  cplx<R> x[12], y[12];
+  load_spinor<P>(t, v.stride, v.idx, x);
+  load_spinor<P>(s, v.stride, v.idx, y);
+  cplx<R> ts = {R(0), R(0)};
+  R tt = 0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    ts = ts + cjmul(x[k], y[k]);
+    tt += norm2(x[k]);
+  }
+  double d[3] = {(double)ts.re, (double)ts.im, (double)tt};
+  block_reduce<3>(d, partial, vg, v.site_local, v.rhs);
+}
+
+__global__ void k_bicg_fin_omega(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+  double s[3];
+  seg_sum<3>(partial, vg, si, s);
+  if (threadIdx.x) return;
+  const int sys = blockIdx.x * nseg + blockIdx.y;
+  if (!ks.active[sys] || !(s[2] > 0.0) || !isfinite(s[2])) {
+    ks.omega[sys] = make_double2(0.0, 0.0);
+    return;
+  }
+  ks.omega[sys] = make_double2(s[0] / s[2], s[1] / s[2]);
+}
+
+// x += alpha p + omega s; r = s - omega t; partial (r0, r), (r, r)
+template <int P>
+__global__ void k_bicg_xr(void* x, const void* p, const void* s, const void* t, void* r, const void* r0, VGeom vg,
+                          const SegInfo* si, int nseg, KState ks, double* partial) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, si);
+  const int sys = v.rhs * nseg + v.seg;
+  double2 al = ks.alpha[sys], om = ks.omega[sys];
+  cplx<R> a = {(R)al.x, (R)al.y}, w = {(R)om.x, (R)om.y};
+  cplx<R> xv[12], pv[12], sv[12], tv[12];
+  load_spinor<P>(x, v.stride, v.idx, xv);
+  load_spinor<P>(p, v.stride, v.idx, pv);
+  load_spinor<P>(s, v.stride, v.idx, sv);
+  load_spinor<P>(t, v.stride, v.idx, tv);
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    xv[k] = xv[k] + a * pv[k] + w * sv[k];
+    sv[k] = sv[k] - w * tv[k];  // new r
+  }
+  store_spinor<P>(x, v.stride, v.idx, xv);
+  store_spinor<P>(r, v.stride, v.idx, sv);
+  cplx<R> r0v[12];
+  load_spinor<P>(r0, v.stride, v.idx, r0v);
+  cplx<R> d0 = {R(0), R(0)};
+  R rr = 0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    d0 = d0 + cjmul(r0v[k], sv[k]);
+    rr += norm2(sv[k]);
+  }
+  double d[3] = {(double)d0.re, (double)d0.im, (double)rr};
+  block_reduce<3>(d, partial, vg, v.site_local, v.rhs);
+}
+
+__global__ void k_bicg_fin_beta(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+  double s[3];
+  seg_sum<3>(partial, vg, si, s);
+  if (threadIdx.x) return;
+  const int sys = blockIdx.x * nseg + blockIdx.y;
+  if (!ks.active[sys]) {
+    ks.beta[sys] = make_double2(0.0, 0.0);
+    return;
+  }
+  double2 rho_new = make_double2(s[0], s[1]);
+  ks.r2[sys] = s[2];
+  ks.iters[sys] += 1;
+  double2 om = ks.omega[sys], rho = ks.rho[sys];
+  if (!isfinite(s[2])) {
+    ks.active[sys] = 0;
+    ks.flag[sys] = 2;
+    ks.beta[sys] = make_double2(0.0, 0.0);
+    return;
+  }
+  if (s[2] <= ks.stop2[sys]) {
+    ks.active[sys] = 0;
+    ks.beta[sys] = make_double2(0.0, 0.0);
+    return;
+  }
+  double om2 = om.x * om.x + om.y * om.y, rh2 = rho.x * rho.x + rho.y * rho.y;
+  if (!(om2 > 0.0) || !(rh2 > 0.0)) {
+    ks.active[sys] = 0;
+    ks.flag[sys] = 1;
+    ks.beta[sys] = make_double2(0.0, 0.0);
+    return;
+  }
+  ks.beta[sys] = cmul2(cdiv(rho_new, rho), cdiv(ks.alpha[sys], om));
+  ks.rho[sys] = rho_new;
+}
+
+// p = r + beta (p - omega v)
+template <int P>
+__global__ void k_bicg_p(void* p, const void* r, const void* vv, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+  using R = typename Traits<P>::real;
+  VThread v = vthread(vg, si);
+  const int sys = v.rhs * nseg + v.seg;
+  double2 be = ks.beta[sys], om = ks.omega[sys];
+  cplx<R> b = {(R)be.x, (R)be.y}, w = {(R)om.x, (R)om.y};
+  cplx<R> pv[12], rv[12], vv2[12];
+  load_spinor<P>(p, v.stride, v.idx, pv);
+  load_spinor<P>(r, v.stride, v.idx, rv);
+  load_spinor<P>(vv, v.stride, v.idx, vv2);
+#pragma unroll
+  for (int k = 0; k < 12; k++) pv[k] = rv[k] + b * (pv[k] - w * vv2[k]);
+  store_spinor<P>(p, v.stride, v.idx, pv);
+}
+
+__global__ void k_count_active(const int* active, int n, int* count) {
+  __shared__ int sm[256];
+  int s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += active[i] ? 1 : 0;
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k >= 1; k >>= 1) {
+    if (threadIdx.x < k) sm[threadIdx.x] += sm[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) count[0] = sm[0];
+}
+
+// outer-loop bookkeeping: r2 -> active, inner delta and scale per system
+__global__ void k_outer_update(const double* r2, const double* b2, int nsys, double tol, double inner_tol,
+                               int* active, double* delta, double* scale, double* rel, int first) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsys) return;
+  double bn = b2[i], rn = r2[i];
+  double rr = bn > 0 ? sqrt(rn / bn) : 0.0;
+  rel[i] = rr;
+  int act = (bn > 0) && (rr > tol) && isfinite(rn);
+  if (!first && !active[i]) act = 0;
+  active[i] = act;
+  // the inner solve must reduce this residual by inner_tol, but no further than needed
+  double need = rr > 0 ? 0.5 * tol / rr : 1.0;
+  double d = inner_tol > need ? inner_tol : need;
+  delta[i] = d < 1.0 ? d : 0.5;
+  scale[i] = rn > 0 ? 1.0 / sqrt(rn) : 1.0;
+}
+
+__global__ void k_recip(const double* a, double* b, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i] != 0.0 ? 1.0 / a[i] : 0.0;
+}
+
+// ------------------------------------------------------------------ host launchers
+static inline size_t shm(const VGeom& vg, int nd) { return (size_t)nd * vg.threads() * sizeof(double); }
+static inline dim3 fin_grid(const VGeom& vg, int nseg) { return dim3(vg.nrhs, nseg); }
+
+#define DISPATCH_P(prec, KERNEL, ...)            \
+  do {                                           \
+    if ((prec) == P64) KERNEL<P64> __VA_ARGS__;  \
+    else if ((prec) == P32) KERNEL<P32> __VA_ARGS__; \
+    else KERNEL<P16> __VA_ARGS__;                \
+  } while (0)
+
+void v_norm2(int prec, const void* x, const VGeom& vg, const SegInfo* si, int nseg, double* partial, double* out,
+             cudaStream_t st) {
+  DISPATCH_P(prec, k_norm2, <<<vg.blocks, vg.threads(), shm(vg, 1), st>>>(x, vg, si, partial));
+  k_fin_sum1<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, out);
+}
+
+void v_convert(int pin, int pout, const void* in, void* out, const VGeom& vg, const SegInfo* si, int nseg,
+               const double* scale, cudaStream_t st) {
+#define CONV(A, B) k_convert<A, B><<<vg.blocks, vg.threads(), 0, st>>>(in, out, vg, si, nseg, scale)
+  if (pin == P64 && pout == P32) CONV(P64, P32);
+  else if (pin == P64 && pout == P16) CONV(P64, P16);
+  else if (pin == P32 && pout == P64) CONV(P32, P64);
+  else if (pin == P16 && pout == P64) CONV(P16, P64);
+  else if (pin == P32 && pout == P16) CONV(P32, P16);
+  else if (pin == P16 && pout == P32) CONV(P16, P32);
+  else if (pin == P64 && pout == P64) CONV(P64, P64);
+  else if (pin == P32 && pout == P32) CONV(P32, P32);
+  else CONV(P16, P16);
+#undef CONV
+}
+
+void v_axpy_mixed(int pe, void* x, const void* e, const VGeom& vg, const SegInfo* si, int nseg, const double* scale,
+                  const int* active, cudaStream_t st) {
+  DISPATCH_P(pe, k_axpy_mixed, <<<vg.blocks, vg.threads(), 0, st>>>(x, e, vg, si, nseg, scale, active));
+}
+
+void v_zero(int prec, void* x, const VGeom& vg, cudaStream_t st) {
+  DISPATCH_P(prec, k_zero, <<<vg.blocks, vg.threads(), 0, st>>>(x, vg));
+}
+
+void v_copy(int prec, const void* a, void* b, const VGeom& vg, cudaStream_t st) {
+  DISPATCH_P(prec, k_copy, <<<vg.blocks, vg.threads(), 0, st>>>(a, b, vg));
+}
+
+void bicg_init(int prec, const void* b, void* r, void* p, void* x, const VGeom& vg, const SegInfo* si, int nseg,
+               double* partial, const KState& ks, const double* delta, const int* outer_active, cudaStream_t st) {
+  DISPATCH_P(prec, k_bicg_init, <<<vg.blocks, vg.threads(), shm(vg, 1), st>>>(b, r, p, x, vg, si, partial));
+  k_bicg_fin_init<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks, delta, outer_active);
+}
+
+void bicg_alpha(int prec, const void* r0, const void* v, const VGeom& vg, const SegInfo* si, int nseg,
+                double* partial, const KState& ks, cudaStream_t st) {
+  DISPATCH_P(prec, k_dot, <<<vg.blocks, vg.threads(), shm(vg, 2), st>>>(r0, v, vg, si, partial));
+  k_bicg_fin_alpha<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+}
+
+void bicg_s(int prec, const void* r, const void* v, void* s, const VGeom& vg, const SegInfo* si, int nseg,
+            const KState& ks, cudaStream_t st) {
+  DISPATCH_P(prec, k_bicg_s, <<<vg.blocks, vg.threads(), 0, st>>>(r, v, s, vg, si, nseg, ks));
+}
+
+void bicg_omega(int prec, const void* t, const void* s, const VGeom& vg, const SegInfo* si, int nseg,
+                double* partial, const KState& ks, cudaStream_t st) {
+  DISPATCH_P(prec, k_dot_ts, <<<vg.blocks, vg.threads(), shm(vg, 3), st>>>(t, s, vg, si, partial));
+  k_bicg_fin_omega<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+}
+
+void bicg_xr(int prec, void* x, const void* p, const void* s, const void* t, void* r, const void* r0,
+             const VGeom& vg, const SegInfo* si, int nseg, double* partial, const KState& ks, cudaStream_t st) {
+  DISPATCH_P(prec, k_bicg_xr,
+             <<<vg.blocks, vg.threads(), shm(vg, 3), st>>>(x, p, s, t, r, r0, vg, si, nseg, ks, partial));
+  k_bicg_fin_beta<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+}
+
+void bicg_p(int prec, void* p, const void* r, const void* v, const VGeom& vg, const SegInfo* si, int nseg,
+            const KState& ks, cudaStream_t st) {
+  DISPATCH_P(prec, k_bicg_p, <<<vg.blocks, vg.threads(), 0, st>>>(p, r, v, vg, si, nseg, ks));
+}
+
+void count_active(const int* active, int n, int* count, cudaStream_t st) {
+  k_count_active<<<1, 256, 0, st>>>(active, n, count);
+}
+
+void outer_update(const double* r2, const double* b2, int nsys, double tol, double inner_tol, int* active,
+                  double* delta, double* scale, double* rel, int first, cudaStream_t st) {
+  k_outer_update<<<(nsys + 127) / 128, 128, 0, st>>>(r2, b2, nsys, tol, inner_tol, active, delta, scale, rel,
+                                                     first);
+}
+
+void recip(const double* a, double* b, int n, cudaStream_t st) {
+  k_recip<<<(n + 127) / 128, 128, 0, st>>>(a, b, n);
+}
+
+}  // namespace lqcd

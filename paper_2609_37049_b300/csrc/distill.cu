@@ -1,0 +1,276 @@
+// Layout conversion between the caller's lexicographic spinors and the internal even-odd
+// layout, and the distillation kernels: sources (Sec. 3.1), the projection
+// tau = V^dagger X on sink timeslices, quark loops (Sec. 2 / Sec. 3.2) and the disconnected
+// correlators (Eqs. Cdisc, correlator_factorised, subtracted_correlator, corr1-corr4).
+#include "lqcd_distill.h"
+
+namespace lqcd {
+
+// ------------------------------------------------------------------ layouts
+// lex [nrhs][V][12] <-> full even-odd FP64 [par][12][Vh][nrhs]
+__global__ void k_pack_spinor(const double2* in, double2* out, Geom g, int nrhs, int to_eo) {
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long n = 2 * g.Vh * (long)nrhs;
+  if (tid >= n) return;
+  const int rhs = (int)(tid % nrhs);
+  const long site = tid / nrhs;
+  const int par = (int)(site / g.Vh);
+  const long cb = site - par * g.Vh;
+  int x, y, z, t;
+  cb_coords(g, par, cb, x, y, z, t);
+  const long s = lex_index(g, x, y, z, t);
+  const long V = 2 * g.Vh;
+  double2* eo_base = out;
+  const double2* lex = in;
+  if (to_eo) {
+    for (int k = 0; k < 12; k++)
+      eo_base[(long)par * 12 * g.Vh * nrhs + (k * g.Vh + cb) * nrhs + rhs] = lex[((long)rhs * V + s) * 12 + k];
+  } else {
+    // here `in` is the eo field and `out` the lex field
+    for (int k = 0; k < 12; k++)
+      out[((long)rhs * V + s) * 12 + k] = in[(long)par * 12 * g.Vh * nrhs + (k * g.Vh + cb) * nrhs + rhs];
+  }
+}
+
+void pack_spinor(const Geom& g, const double2* lex, double2* eo, int nrhs, cudaStream_t st) {
+  long n = 2 * g.Vh * (long)nrhs;
+  k_pack_spinor<<<(n + 255) / 256, 256, 0, st>>>(lex, eo, g, nrhs, 1);
+}
+void unpack_spinor(const Geom& g, const double2* eo, double2* lex, int nrhs, cudaStream_t st) {
+  long n = 2 * g.Vh * (long)nrhs;
+  k_pack_spinor<<<(n + 255) / 256, 256, 0, st>>>(eo, lex, g, nrhs, 0);
+}
+
+// ------------------------------------------------------------------ sources
+// b_r(x) = [srcmask[t] == 1] e_{beta_r} (x) v_{j_r}(t)(xvec); Vt: [Lt][n_ev][L3][3]
+__global__ void k_sources(const double2* Vt, int n_ev, const int* jr, const int* br, const unsigned char* srcmask,
+                          double2* b, Geom g, int nrhs) {
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long n = 2 * g.Vh * (long)nrhs;
+  if (tid >= n) return;
+  const int rhs = (int)(tid % nrhs);
+  const long site = tid / nrhs;
+  const int par = (int)(site / g.Vh);
+  const long cb = site - par * g.Vh;
+  int x, y, z, t;
+  cb_coords(g, par, cb, x, y, z, t);
+  const long L3 = (long)g.Lx * g.Ly * g.Lz;
+  const long s3 = x + (long)g.Lx * (y + (long)g.Ly * z);
+  double2* out = b + (long)par * 12 * g.Vh * nrhs;
+  const int on = srcmask[t];
+  const int beta = br[rhs], j = jr[rhs];
+  for (int spin = 0; spin < 4; spin++)
+    for (int a = 0; a < 3; a++) {
+      double2 v = make_double2(0.0, 0.0);
+      if (on && spin == beta) v = Vt[(((long)t * n_ev + j) * L3 + s3) * 3 + a];
+      out[((spin * 3 + a) * g.Vh + cb) * nrhs + rhs] = v;
+    }
+}
+
+void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, const int* br,
+                  const unsigned char* srcmask, double2* b, int nrhs, cudaStream_t st) {
+  long n = 2 * g.Vh * (long)nrhs;
+  k_sources<<<(n + 255) / 256, 256, 0, st>>>(Vt, n_ev, jr, br, srcmask, b, g, nrhs);
+}
+
+// ------------------------------------------------------------------ projection
+// For every sink timeslice tp = sinks[z]:  C[z][i][alpha][r] = sum_{s3,a} conj(V(tp)[i][s3][a])
+//                                                               X_r(tp, s3, alpha, a)
+// as a tiled complex GEMM (M = n_ev, N = 4 nrhs with n = alpha * nrhs + r, K = 3 L^3), FP64.
+#define PBM 32
+#define PBN 32
+#define PBK 16
+__global__ void __launch_bounds__(256) k_project(const double2* Vt, int n_ev, const double2* X, const int* sinks,
+                                                 double2* C, Geom g, int nrhs) {
+  __shared__ double2 As[PBK][PBM + 1];
+  __shared__ double2 Bs[PBK][PBN + 1];
+  const int z = blockIdx.z;
+  const int tp = sinks[z];
+  const long L3 = (long)g.Lx * g.Ly * g.Lz;
+  const long K = 3 * L3;
+  const int N = 4 * nrhs;
+  const int m0 = blockIdx.y * PBM, n0 = blockIdx.x * PBN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  cplx<double> acc[2][2];
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) acc[i][j] = {0.0, 0.0};
+  const double2* A = Vt + (long)tp * n_ev * K;
+  for (long k0 = 0; k0 < K; k0 += PBK) {
+    // A tile: PBM x PBK; 256 threads load 512 entries (2 each)
+    for (int e = threadIdx.x; e < PBM * PBK; e += 256) {
+      int mm = e / PBK, kk = e % PBK;
+      long k = k0 + kk;
+      double2 v = make_double2(0.0, 0.0);
+      if (m0 + mm < n_ev && k < K) v = A[(long)(m0 + mm) * K + k];
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < PBN * PBK; e += 256) {
+      int kk = e / PBN, nn = e % PBN;
+      long k = k0 + kk;
+      int n = n0 + nn;
+      double2 v = make_double2(0.0, 0.0);
+      if (n < N && k < K) {
+        long s3 = k / 3;
+        int a = (int)(k - s3 * 3);
+        int alpha = n / nrhs, r = n - alpha * nrhs;
+        long s = (long)tp * L3 + s3;
+        int x = (int)(s3 % g.Lx), y = (int)((s3 / g.Lx) % g.Ly), zz = (int)(s3 / ((long)g.Lx * g.Ly));
+        int par = (x + y + zz + tp) & 1;
+        long cb = s >> 1;
+        v = X[(long)par * 12 * g.Vh * nrhs + ((long)(alpha * 3 + a) * g.Vh + cb) * nrhs + r];
+      }
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < PBK; kk++) {
+      cplx<double> a0 = {As[kk][ty].x, As[kk][ty].y}, a1 = {As[kk][ty + 16].x, As[kk][ty + 16].y};
+      cplx<double> b0 = {Bs[kk][tx].x, Bs[kk][tx].y}, b1 = {Bs[kk][tx + 16].x, Bs[kk][tx + 16].y};
+      acc[0][0] = acc[0][0] + cjmul(a0, b0);
+      acc[0][1] = acc[0][1] + cjmul(a0, b1);
+      acc[1][0] = acc[1][0] + cjmul(a1, b0);
+      acc[1][1] = acc[1][1] + cjmul(a1, b1);
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) {
+      int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      if (m < n_ev && n < N) {
+        int alpha = n / nrhs, r = n - alpha * nrhs;
+        C[(((long)z * n_ev + m) * 4 + alpha) * nrhs + r] = make_double2(acc[i][j].re, acc[i][j].im);
+      }
+    }
+}
+
+void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, int nsinks, double2* C,
+             int nrhs, cudaStream_t st) {
+  dim3 grid((4 * nrhs + PBN - 1) / PBN, (n_ev + PBM - 1) / PBM, nsinks);
+  k_project<<<grid, 256, 0, st>>>(Vt, n_ev, X, sinks, C, g, nrhs);
+}
+
+// ------------------------------------------------------------------ loops
+// L[g][t] = sum_i w[t][i] sum_{ab} G[a][b] tau[t][i][b][i][a]; Lt with G~; G: [n_gamma][2][4][4]
+__global__ void k_loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w,
+                        double2* L, double2* Lt) {
+  const int gi = blockIdx.x, t = blockIdx.y;
+  __shared__ double sm[4][128];
+  cplx<double> l = {0, 0}, lt = {0, 0};
+  for (int i = threadIdx.x; i < n_ev; i += blockDim.x) {
+    double wi = w ? w[(long)t * n_ev + i] : 1.0;
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) {
+        double2 tv = tau[((((long)t * n_ev + i) * 4 + b) * n_ev + i) * 4 + a];
+        double2 g = G[((gi * 2 + 0) * 4 + a) * 4 + b];
+        double2 gt = G[((gi * 2 + 1) * 4 + a) * 4 + b];
+        cplx<double> T = {tv.x, tv.y};
+        l = l + wi * (cplx<double>{g.x, g.y} * T);
+        lt = lt + wi * (cplx<double>{gt.x, gt.y} * T);
+      }
+  }
+  sm[0][threadIdx.x] = l.re;
+  sm[1][threadIdx.x] = l.im;
+  sm[2][threadIdx.x] = lt.re;
+  sm[3][threadIdx.x] = lt.im;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s >= 1; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 4; k++) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    L[(long)gi * n_t + t] = make_double2(sm[0][0], sm[1][0]);
+    Lt[(long)gi * n_t + t] = make_double2(sm[2][0], sm[3][0]);
+  }
+}
+
+void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w, double2* L,
+           double2* Lt, cudaStream_t st) {
+  k_loops<<<dim3(n_gamma, n_t), 128, 0, st>>>(tau, n_ev, n_t, G, n_gamma, w, L, Lt);
+}
+
+// ------------------------------------------------------------------ correlators
+// conn(A, B)[g][x0][y0] = <A(x0) B(y0)> - vev * <A(x0)> <B(y0)>
+LQCD_D cplx<double> conn(const double2* A, const double2* B, int n_cfg, int n_g, int T, int g, int x0, int y0,
+                         int vev) {
+  cplx<double> ab = {0, 0}, ma = {0, 0}, mb = {0, 0};
+  for (int c = 0; c < n_cfg; c++) {
+    double2 a = A[((long)c * n_g + g) * T + x0], b = B[((long)c * n_g + g) * T + y0];
+    cplx<double> ca = {a.x, a.y}, cb = {b.x, b.y};
+    ab = ab + ca * cb;
+    ma = ma + ca;
+    mb = mb + cb;
+  }
+  double inv = 1.0 / n_cfg;
+  cplx<double> r = inv * ab;
+  if (vev) r = r - (inv * ma) * (inv * mb);
+  return r;
+}
+
+__global__ void k_corr(const double2* L, const double2* Lt, const double2* Ld, const double2* Ltd, int n_cfg, int n_g,
+                       int T, int vev, const int* dom, double2* C, double2* Cdd, double2* dC, int* valid,
+                       double2* terms, double2* dL, double2* dLt) {
+  const int g = blockIdx.x;
+  const int x0 = blockIdx.y;
+  const int y0 = threadIdx.x;
+  if (y0 >= T) return;
+  cplx<double> c = conn(L, Lt, n_cfg, n_g, T, g, x0, y0, vev);
+  cplx<double> cd = conn(Ld, Ltd, n_cfg, n_g, T, g, x0, y0, vev);
+  long o = ((long)g * T + x0) * T + y0;
+  C[o] = make_double2(c.re, c.im);
+  Cdd[o] = make_double2(cd.re, cd.im);
+  dC[o] = make_double2(c.re - cd.re, c.im - cd.im);
+  if (g == 0) valid[x0 * T + y0] = dom[x0] != dom[y0];
+  if (terms) {
+    long q = (long)n_g * T * T;
+    cplx<double> t1 = conn(Ld, dLt, n_cfg, n_g, T, g, x0, y0, vev);
+    cplx<double> t2 = conn(dL, Ltd, n_cfg, n_g, T, g, x0, y0, vev);
+    cplx<double> t3 = conn(dL, dLt, n_cfg, n_g, T, g, x0, y0, vev);
+    terms[o] = make_double2(cd.re, cd.im);
+    terms[q + o] = make_double2(t1.re, t1.im);
+    terms[2 * q + o] = make_double2(t2.re, t2.im);
+    terms[3 * q + o] = make_double2(t3.re, t3.im);
+  }
+}
+
+__global__ void k_diff(const double2* a, const double2* b, double2* c, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
+}
+
+__global__ void k_corr_avg(const double2* C, const double2* dC, const int* dom, int n_g, int T, double2* C_avg,
+                           double2* dC_avg, int* n_valid) {
+  const int g = blockIdx.x;
+  const int dt = threadIdx.x;
+  if (dt >= T) return;
+  cplx<double> s = {0, 0}, sd = {0, 0};
+  int nv = 0;
+  for (int y0 = 0; y0 < T; y0++) {
+    int x0 = (y0 + dt) % T;
+    long o = ((long)g * T + x0) * T + y0;
+    s = s + cplx<double>{C[o].x, C[o].y};
+    if (dom[x0] != dom[y0]) {
+      sd = sd + cplx<double>{dC[o].x, dC[o].y};
+      nv++;
+    }
+  }
+  C_avg[(long)g * T + dt] = make_double2(s.re / T, s.im / T);
+  dC_avg[(long)g * T + dt] = nv ? make_double2(sd.re / nv, sd.im / nv) : make_double2(0.0, 0.0);
+  if (g == 0) n_valid[dt] = nv;
+}
+
+void correlators(const double2* L, const double2* Lt, const double2* Ld, const double2* Ltd, int n_cfg, int n_g,
+                 int T, int vev, const int* dom, double2* C, double2* Cdd, double2* dC, double2* C_avg,
+                 double2* dC_avg, int* valid, int* n_valid, double2* terms, double2* dL, double2* dLt,
+                 cudaStream_t st) {
+  long n = (long)n_cfg * n_g * T;
+  if (terms) {
+    k_diff<<<(n + 255) / 256, 256, 0, st>>>(L, Ld, dL, n);
+    k_diff<<<(n + 255) / 256, 256, 0, st>>>(Lt, Ltd, dLt, n);
+  }
+  k_corr<<<dim3(n_g, T), ((T + 31) / 32) * 32, 0, st>>>(L, Lt, Ld, Ltd, n_cfg, n_g, T, vev, dom, C, Cdd, dC, valid,
+                                                        terms, dL, dLt);
+  k_corr_avg<<<n_g, ((T + 31) / 32) * 32, 0, st>>>(C, dC, dom, n_g, T, C_avg, dC_avg, n_valid);
+}
+
+}  // namespace lqcd

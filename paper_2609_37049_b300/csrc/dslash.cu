@@ -1,0 +1,297 @@
+// Even-odd hopping term of the clover-Wilson operator (Sec. 2.1 / Sec. 3 of the paper), with
+// the clover (or inverse clover) multiplication and the axpy of the Schur complement fused into
+// the epilogue.  One thread per (output site, right-hand side), right-hand sides fastest, so the
+// threads of one site read its links and clover once per warp (a broadcast) and the spinor
+// loads of a warp are contiguous 16-byte chunks.
+//
+//   (H x)(s) = sum_mu (1 + sf gamma_mu) U_mu(s) x(s+mu) + (1 - sf gamma_mu) U_mu(s-mu)^dag x(s-mu)
+// with sf = -1 for H and sf = +1 for H^dag.  In the chiral basis gamma_mu = [[0, X],[X^dag, 0]]
+// with X_x = -i sigma_x, X_y = -i sigma_y, X_z = -i sigma_z, X_t = 1, so
+//   (1 + s gamma_mu) psi = [ h ; s X^dag h ],  h = psi_up + s X psi_down  (two spins x colour):
+// only the two-spin half spinor h is multiplied by the link.
+#include "lqcd_internal.h"
+
+namespace lqcd {
+
+struct DslashParams {
+  Geom g;
+  const void* in;
+  const void* y;
+  const void* z;
+  void* out;
+  const void* U;
+  const void* C;
+  int out_par;
+  int nrhs;
+  double a, b;
+  const signed char* tc;  // device array [Lt]
+};
+
+// h = psi_up + s X_mu psi_down
+template <int MU, int S, typename R>
+LQCD_D void project(const cplx<R> (&p)[12], cplx<R> (&h)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    cplx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+    if constexpr (MU == 0) {  // X p_d = (-i p3, -i p2)
+      h[0][c] = S > 0 ? p0 + times_mi(p3) : p0 - times_mi(p3);
+      h[1][c] = S > 0 ? p1 + times_mi(p2) : p1 - times_mi(p2);
+    } else if constexpr (MU == 1) {  // X p_d = (-p3, p2)
+      h[0][c] = S > 0 ? p0 - p3 : p0 + p3;
+      h[1][c] = S > 0 ? p1 + p2 : p1 - p2;
+    } else if constexpr (MU == 2) {  // X p_d = (-i p2, i p3)
+      h[0][c] = S > 0 ? p0 + times_mi(p2) : p0 - times_mi(p2);
+      h[1][c] = S > 0 ? p1 + times_i(p3) : p1 - times_i(p3);
+    } else {  // X p_d = (p2, p3)
+      h[0][c] = S > 0 ? p0 + p2 : p0 - p2;
+      h[1][c] = S > 0 ? p1 + p3 : p1 - p3;
+    }
+  }
+}
+
+// acc += [ w ; s X^dag w ]
+template <int MU, int S, typename R>
+LQCD_D void accumulate(cplx<R> (&acc)[12], const cplx<R> (&w)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc[c] = acc[c] + w[0][c];
+    acc[3 + c] = acc[3 + c] + w[1][c];
+    cplx<R> l2, l3;
+    if constexpr (MU == 0) {  // X^dag w = (i w1, i w0)
+      l2 = times_i(w[1][c]);
+      l3 = times_i(w[0][c]);
+    } else if constexpr (MU == 1) {  // X^dag w = (w1, -w0)
+      l2 = w[1][c];
+      l3 = -w[0][c];
+    } else if constexpr (MU == 2) {  // X^dag w = (i w0, -i w1)
+      l2 = times_i(w[0][c]);
+      l3 = times_mi(w[1][c]);
+    } else {
+      l2 = w[0][c];
+      l3 = w[1][c];
+    }
+    if constexpr (S > 0) {
+      acc[6 + c] = acc[6 + c] + l2;
+      acc[9 + c] = acc[9 + c] + l3;
+    } else {
+      acc[6 + c] = acc[6 + c] - l2;
+      acc[9 + c] = acc[9 + c] - l3;
+    }
+  }
+}
+
+template <typename R>
+LQCD_D void su3_mul(const cplx<R> (&u)[3][3], const cplx<R> (&h)[2][3], cplx<R> (&w)[2][3]) {
+#pragma unroll
+  for (int s = 0; s < 2; s++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) w[s][a] = u[a][0] * h[s][0] + u[a][1] * h[s][1] + u[a][2] * h[s][2];
+}
+
+template <typename R>
+LQCD_D void su3_dag_mul(const cplx<R> (&u)[3][3], const cplx<R> (&h)[2][3], cplx<R> (&w)[2][3]) {
+#pragma unroll
+  for (int s = 0; s < 2; s++)
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      w[s][a] = cjmul(u[0][a], h[s][0]) + cjmul(u[1][a], h[s][1]) + cjmul(u[2][a], h[s][2]);
+}
+
+// One direction: forward and backward hops.
+template <int P, int MU, bool DAG>
+LQCD_D void hop_dir(const DslashParams& pr, long cb, int x, int y, int z, int t, int rhs, long stride,
+                    cplx<typename Traits<P>::real> (&acc)[12]) {
+  using R = typename Traits<P>::real;
+  const Geom& g = pr.g;
+  constexpr int SF = DAG ? 1 : -1;  // forward projector sign
+  constexpr int SB = -SF;
+  const int op = pr.out_par, ip = 1 - pr.out_par;
+  // ---- forward: U_mu(s) x(s + mu)
+  {
+    int xn = x, yn = y, zn = z, tn = t;
+    int coef = 1;
+    if constexpr (MU == 0) xn = (x + 1 == g.Lx) ? 0 : x + 1;
+    if constexpr (MU == 1) yn = (y + 1 == g.Ly) ? 0 : y + 1;
+    if constexpr (MU == 2) zn = (z + 1 == g.Lz) ? 0 : z + 1;
+    if constexpr (MU == 3) {
+      tn = (t + 1 == g.Lt) ? 0 : t + 1;
+      coef = __ldg(pr.tc + t);
+    }
+    if (coef != 0) {
+      long nb = lex_index(g, xn, yn, zn, tn) >> 1;
+      cplx<R> p[12];
+      load_spinor<P>(pr.in, stride, nb * pr.nrhs + rhs, p);
+      cplx<R> h[2][3], w[2][3], u[3][3];
+      project<MU, SF>(p, h);
+      load_link<P>(pr.U, g.Vh, MU, op, cb, u);
+      su3_mul(u, h, w);
+      if (coef < 0) {
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+          for (int a = 0; a < 3; a++) w[s][a] = -w[s][a];
+      }
+      accumulate<MU, SF>(acc, w);
+    }
+  }
+  // ---- backward: U_mu(s - mu)^dag x(s - mu)
+  {
+    int xn = x, yn = y, zn = z, tn = t;
+    int coef = 1;
+    if constexpr (MU == 0) xn = (x == 0) ? g.Lx - 1 : x - 1;
+    if constexpr (MU == 1) yn = (y == 0) ? g.Ly - 1 : y - 1;
+    if constexpr (MU == 2) zn = (z == 0) ? g.Lz - 1 : z - 1;
+    if constexpr (MU == 3) {
+      tn = (t == 0) ? g.Lt - 1 : t - 1;
+      coef = __ldg(pr.tc + tn);
+    }
+    if (coef != 0) {
+      long nb = lex_index(g, xn, yn, zn, tn) >> 1;
+      cplx<R> p[12];
+      load_spinor<P>(pr.in, stride, nb * pr.nrhs + rhs, p);
+      cplx<R> h[2][3], w[2][3], u[3][3];
+      project<MU, SB>(p, h);
+      load_link<P>(pr.U, g.Vh, MU, ip, nb, u);
+      su3_dag_mul(u, h, w);
+      if (coef < 0) {
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+          for (int a = 0; a < 3; a++) w[s][a] = -w[s][a];
+      }
+      accumulate<MU, SB>(acc, w);
+    }
+  }
+}
+
+template <int P, int EPI, bool DAG>
+__global__ void __launch_bounds__(256) dslash_kernel(const DslashParams pr) {
+  using R = typename Traits<P>::real;
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long cb = tid / pr.nrhs;
+  const int rhs = (int)(tid - cb * pr.nrhs);
+  if (cb >= pr.g.Vh) return;
+  int x, y, z, t;
+  cb_coords(pr.g, pr.out_par, cb, x, y, z, t);
+  const long stride = pr.g.Vh * pr.nrhs;
+  const long idx = cb * pr.nrhs + rhs;
+
+  cplx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = {R(0), R(0)};
+  hop_dir<P, 0, DAG>(pr, cb, x, y, z, t, rhs, stride, acc);
+  hop_dir<P, 1, DAG>(pr, cb, x, y, z, t, rhs, stride, acc);
+  hop_dir<P, 2, DAG>(pr, cb, x, y, z, t, rhs, stride, acc);
+  hop_dir<P, 3, DAG>(pr, cb, x, y, z, t, rhs, stride, acc);
+
+  const R a = (R)pr.a, b = (R)pr.b;
+  cplx<R> o[12];
+  if constexpr (EPI == EPI_H) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) o[k] = b * acc[k];
+  } else if constexpr (EPI == EPI_CH) {
+    clover_apply<P>(pr.C, pr.g.Vh, cb, acc);
+#pragma unroll
+    for (int k = 0; k < 12; k++) o[k] = b * acc[k];
+  } else if constexpr (EPI == EPI_Y_H || EPI == EPI_Y_CH) {
+    if constexpr (EPI == EPI_Y_CH) clover_apply<P>(pr.C, pr.g.Vh, cb, acc);
+    cplx<R> yv[12];
+    load_spinor<P>(pr.y, stride, idx, yv);
+#pragma unroll
+    for (int k = 0; k < 12; k++) o[k] = a * yv[k] + b * acc[k];
+  } else if constexpr (EPI == EPI_C_YH) {
+    cplx<R> yv[12];
+    load_spinor<P>(pr.y, stride, idx, yv);
+#pragma unroll
+    for (int k = 0; k < 12; k++) o[k] = a * yv[k] + b * acc[k];
+    clover_apply<P>(pr.C, pr.g.Vh, cb, o);
+  } else if constexpr (EPI == EPI_CY_H) {
+    cplx<R> yv[12];
+    load_spinor<P>(pr.y, stride, idx, yv);
+    clover_apply<P>(pr.C, pr.g.Vh, cb, yv);
+#pragma unroll
+    for (int k = 0; k < 12; k++) o[k] = a * yv[k] + b * acc[k];
+  } else {  // EPI_RES: z - (C y + b H x)
+    cplx<R> yv[12], zv[12];
+    load_spinor<P>(pr.y, stride, idx, yv);
+    clover_apply<P>(pr.C, pr.g.Vh, cb, yv);
+    load_spinor<P>(pr.z, stride, idx, zv);
+#pragma unroll
+    for (int k = 0; k < 12; k++) o[k] = zv[k] - (yv[k] + b * acc[k]);
+  }
+  store_spinor<P>(pr.out, stride, idx, o);
+}
+
+template <int P>
+__global__ void clover_only_kernel(const void* C, const void* in, void* out, long Vh, int nrhs) {
+  using R = typename Traits<P>::real;
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long cb = tid / nrhs;
+  if (cb >= Vh) return;
+  const long stride = Vh * nrhs;
+  cplx<R> s[12];
+  load_spinor<P>(in, stride, tid, s);
+  clover_apply<P>(C, Vh, cb, s);
+  store_spinor<P>(out, stride, tid, s);
+}
+
+template <int P, int EPI>
+static void launch_p_e(const DslashParams& pr, bool dag, long nthreads, int tpb, cudaStream_t st) {
+  long blocks = (nthreads + tpb - 1) / tpb;
+  if (dag)
+    dslash_kernel<P, EPI, true><<<blocks, tpb, 0, st>>>(pr);
+  else
+    dslash_kernel<P, EPI, false><<<blocks, tpb, 0, st>>>(pr);
+}
+
+template <int P>
+static void launch_p(const DslashParams& pr, int epi, bool dag, long nthreads, int tpb, cudaStream_t st) {
+  switch (epi) {
+    case EPI_H: launch_p_e<P, EPI_H>(pr, dag, nthreads, tpb, st); break;
+    case EPI_CH: launch_p_e<P, EPI_CH>(pr, dag, nthreads, tpb, st); break;
+    case EPI_Y_H: launch_p_e<P, EPI_Y_H>(pr, dag, nthreads, tpb, st); break;
+    case EPI_Y_CH: launch_p_e<P, EPI_Y_CH>(pr, dag, nthreads, tpb, st); break;
+    case EPI_C_YH: launch_p_e<P, EPI_C_YH>(pr, dag, nthreads, tpb, st); break;
+    case EPI_CY_H: launch_p_e<P, EPI_CY_H>(pr, dag, nthreads, tpb, st); break;
+    default: launch_p_e<P, EPI_RES>(pr, dag, nthreads, tpb, st); break;
+  }
+}
+
+void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int threads) {
+  DslashParams pr;
+  pr.g = g;
+  pr.in = c.in;
+  pr.y = c.y;
+  pr.z = c.z;
+  pr.out = c.out;
+  pr.U = c.U;
+  pr.C = c.C;
+  pr.out_par = c.out_par;
+  pr.nrhs = c.nrhs;
+  pr.a = c.a;
+  pr.b = c.b;
+  pr.tc = c.tc;
+  long nthreads = g.Vh * (long)c.nrhs;
+  int tpb = threads > 0 ? threads : 128;
+  if (c.prec == P64)
+    launch_p<P64>(pr, c.epi, c.dagger != 0, nthreads, tpb, st);
+  else if (c.prec == P32)
+    launch_p<P32>(pr, c.epi, c.dagger != 0, nthreads, tpb, st);
+  else
+    launch_p<P16>(pr, c.epi, c.dagger != 0, nthreads, tpb, st);
+}
+
+void launch_clover_only(const Geom& g, int prec, const void* C, const void* in, void* out, int nrhs,
+                        cudaStream_t st) {
+  long n = g.Vh * (long)nrhs;
+  int tpb = 128;
+  long blocks = (n + tpb - 1) / tpb;
+  if (prec == P64)
+    clover_only_kernel<P64><<<blocks, tpb, 0, st>>>(C, in, out, g.Vh, nrhs);
+  else if (prec == P32)
+    clover_only_kernel<P32><<<blocks, tpb, 0, st>>>(C, in, out, g.Vh, nrhs);
+  else
+    clover_only_kernel<P16><<<blocks, tpb, 0, st>>>(C, in, out, g.Vh, nrhs);
+}
+
+}  // namespace lqcd

@@ -1,0 +1,35 @@
+// Host launchers of the layout and distillation kernels (distill.cu) and the solver driver.
+#pragma once
+#include "lqcd_internal.h"
+
+namespace lqcd {
+void pack_spinor(const Geom& g, const double2* lex, double2* eo, int nrhs, cudaStream_t st);
+void unpack_spinor(const Geom& g, const double2* eo, double2* lex, int nrhs, cudaStream_t st);
+void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, const int* br,
+                  const unsigned char* srcmask, double2* b, int nrhs, cudaStream_t st);
+void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, int nsinks, double2* C,
+             int nrhs, cudaStream_t st);
+void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w, double2* L,
+           double2* Lt, cudaStream_t st);
+void correlators(const double2* L, const double2* Lt, const double2* Ld, const double2* Ltd, int n_cfg, int n_g,
+                 int T, int vev, const int* dom, double2* C, double2* Cdd, double2* dC, double2* C_avg,
+                 double2* dC_avg, int* valid, int* n_valid, double2* terms, double2* dL, double2* dLt,
+                 cudaStream_t st);
+void build_gauge(lqcd_ctx* c, const double2* links_dev, int* bad_dev);
+
+// Per-batch solver statistics (host side).
+struct BatchStats {
+  std::vector<double> rel;  // [nsys] final true relative residual
+  std::vector<int> iters;   // [nsys] inner iterations summed over cycles
+  int cycles = 0;
+  long long dslash = 0;
+  int fallback = 0;
+};
+
+// Solve D x = b (domain = 0) or D_Lambda x = b (domain = 1) for nrhs right-hand sides held in
+// the full even-odd FP64 layout on the device.  Returns LQCD_OK or LQCD_ERR_NOT_CONVERGED.
+int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain, const lqcd_solve_params& p,
+                BatchStats& bs);
+// out = D in (or D_Lambda in), full even-odd FP64 layout.
+void apply_D(lqcd_ctx* c, const double2* in, double2* out, int nrhs, int domain, cudaStream_t st);
+}  // namespace lqcd

@@ -1,0 +1,140 @@
+// Host-side internals of the lqcd library: the context, workspace, kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lqcd.h"
+#include "lqcd_common.cuh"
+
+namespace lqcd {
+
+// ------------------------------------------------------------------ reductions / segments
+// Vector kernels run one thread per (site, rhs), rhs fastest, with S sites per block; S is a
+// power of two dividing the half-timeslice volume so every block lies inside one timeslice of
+// one parity.  Segments are ranges of timeslices (one per domain, or one for the full lattice);
+// a Krylov "system" is one (rhs, segment) pair, index sys = rhs * nseg + seg.
+struct SegInfo {
+  int nseg;
+  unsigned char seg_of_t[LQCD_MAXT];
+  unsigned short t0[LQCD_MAXT];
+  unsigned short t1[LQCD_MAXT];
+};
+
+struct VGeom {
+  Geom g;
+  int nrhs;
+  int S;         // sites per block
+  int npar;      // 1 (half lattice) or 2 (full lattice, even block then odd block)
+  long blocks;   // npar * Vh / S
+  long bpt;      // blocks per timeslice per parity = Vth / S
+  long bpp;      // blocks per parity = Vh / S
+  int threads() const { return S * nrhs; }
+};
+
+VGeom make_vgeom(const Geom& g, int nrhs, int npar);
+
+// Per-system Krylov scalars (device arrays of length nsys).
+struct KState {
+  double2* rho;
+  double2* alpha;
+  double2* omega;
+  double2* beta;
+  double* r2;
+  double* b2;
+  double* stop2;
+  int* active;
+  int* iters;
+  int* flag;    // 1: breakdown
+  int* count;   // [1] number of active systems
+};
+
+// ------------------------------------------------------------------ dslash
+enum Epi {
+  EPI_H = 0,     // out = b * H x
+  EPI_CH = 1,    // out = b * C (H x)
+  EPI_Y_H = 2,   // out = a y + b H x
+  EPI_Y_CH = 3,  // out = a y + b C (H x)
+  EPI_C_YH = 4,  // out = C (a y + b H x)
+  EPI_CY_H = 5,  // out = a C y + b H x
+  EPI_RES = 6    // out = z - (C y + b H x)
+};
+
+struct DslashCall {
+  int prec;
+  int epi;
+  int dagger;
+  const void* in;   // parity 1 - out_par
+  const void* y;    // parity out_par
+  const void* z;    // parity out_par
+  void* out;        // parity out_par
+  const void* U;
+  const void* C;    // packed clover of parity out_par (A or A^-1)
+  int out_par;
+  int nrhs;
+  double a, b;
+  const signed char* tc;  // device array [Lt]: forward t-hop coefficient per timeslice
+};
+
+void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int threads = 0);
+void launch_clover_only(const Geom& g, int prec, const void* C, const void* in, void* out, int nrhs,
+                        cudaStream_t st);
+
+}  // namespace lqcd
+
+// ------------------------------------------------------------------ context
+struct lqcd_ctx {
+  lqcd::Geom g;
+  long V;
+  int bc;
+  double kappa = 0, csw = 0;
+  bool have_gauge = false;
+  cudaStream_t user_stream = 0;
+  cudaStream_t work = 0;
+  cudaEvent_t ev_user = 0, ev_work = 0;
+  // links: P64 full matrices, P32 / P16 two rows
+  void* U64 = nullptr;
+  void* U32 = nullptr;
+  void* U16 = nullptr;
+  // clover A and A^-1 per parity: [par][chir][chunks][Vh]
+  void* A64 = nullptr;
+  void* Ainv64 = nullptr;
+  void* Ainv32 = nullptr;
+  void* Ainv16 = nullptr;
+  void* A32 = nullptr;
+  // domain tiling of the time axis
+  std::vector<int> extents;
+  signed char tc_full[LQCD_MAXT];
+  signed char tc_dom[LQCD_MAXT];
+  signed char* d_tc_full = nullptr;  // device copies [Lt]
+  signed char* d_tc_dom = nullptr;
+  lqcd::SegInfo seg_full, seg_dom;
+  lqcd::SegInfo* d_seg_full = nullptr;  // device copies
+  lqcd::SegInfo* d_seg_dom = nullptr;
+  // workspace: grow-only device buffers by name
+  std::map<std::string, std::pair<void*, size_t>> ws;
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  std::string err;
+  int device = 0;
+  // autotuned threads per block for the dslash, keyed by prec * 100000 + nrhs
+  std::map<long, int> tuned_threads;
+  // instantiated CUDA graphs of Krylov iteration chunks, keyed by buffers and shape
+  std::map<std::string, cudaGraphExec_t> graphs;
+  // Clifford table on the device: [16][2][4][4] complex (Gamma, Gamma-tilde)
+  double2* d_gamma = nullptr;
+};
+
+namespace lqcd {
+void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes);
+void* pinned_get(lqcd_ctx* c, size_t bytes);
+int set_error(lqcd_ctx* c, int code, const std::string& msg);
+size_t clover_bytes(const Geom& g, int prec);   // one parity
+size_t link_bytes(const Geom& g, int prec);     // all mu, both parities
+size_t spinor_bytes(const Geom& g, int prec, int nrhs);  // one parity
+inline const char* par_ptr(const void* base, size_t bytes_per_par, int p) {
+  return reinterpret_cast<const char*>(base) + bytes_per_par * p;
+}
+}  // namespace lqcd

@@ -1,0 +1,278 @@
+// Krylov solver driver for the full operator D and the Dirichlet domain operator D_Lambda
+// (Sec. 2.1; the paper's "inversions", Sec. 4).
+//
+// Every solve is an FP64 defect-correction loop judged by the FP64 true residual of the
+// unpreconditioned operator, per system (one right-hand side, or one domain of one right-hand
+// side: because D_Lambda is block diagonal over domains, a multi-site source with one source
+// timeslice per domain is as many independent systems, each with its own Krylov scalars):
+//
+//   x = 0, r = b
+//   repeat while some system has ||r|| > tol ||b||:
+//     rhat_e = A_ee^-1 (r_e + kappa H_eo A_oo^-1 r_o)          (even-odd Schur right-hand side)
+//     solve  (1 - kappa^2 A_ee^-1 H_eo A_oo^-1 H_oe) e_e = rhat_e  to relative residual delta
+//     e_o = A_oo^-1 (r_o + kappa H_oe e_e);  x += e;  r = b - D x  (FP64)
+//
+// The inner solve is BiCGStab run in lockstep over all systems of the batch, in FP64 (the plain
+// solver), FP32, or FP16 storage with FP32 arithmetic; its residual is rescaled to unit norm
+// per system before conversion.  One BiCGStab iteration is 12 kernel launches with all scalars
+// on the device; chunks of iterations are captured once into a CUDA graph and replayed, with a
+// host convergence check (one 4-byte read) between chunks.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "lqcd_blas.h"
+#include "lqcd_distill.h"
+
+namespace lqcd {
+
+size_t spinor_bytes(const Geom& g, int prec, int nrhs) {
+  return (size_t)g.Vh * nrhs * 12 * (prec == P64 ? 16 : (prec == P32 ? 8 : 4));
+}
+size_t clover_bytes(const Geom& g, int prec) {
+  return (size_t)g.Vh * 2 * (prec == P64 ? 18 * 16 : (prec == P32 ? 9 * 16 : 9 * 8));
+}
+size_t link_bytes(const Geom& g, int prec) {
+  return (size_t)g.Vh * 8 * (prec == P64 ? 9 * 16 : (prec == P32 ? 3 * 16 : 3 * 8));
+}
+
+static inline void* off(void* base, size_t b, int p) { return reinterpret_cast<char*>(base) + b * p; }
+static inline const void* off(const void* base, size_t b, int p) {
+  return reinterpret_cast<const char*>(base) + b * p;
+}
+
+void apply_D(lqcd_ctx* c, const double2* in, double2* out, int nrhs, int domain, cudaStream_t st) {
+  const size_t sb = spinor_bytes(c->g, P64, nrhs), cbb = clover_bytes(c->g, P64);
+  for (int p = 0; p < 2; p++) {
+    DslashCall k{P64, EPI_CY_H, 0, off(in, sb, 1 - p), off(in, sb, p), nullptr, off(out, sb, p), c->U64,
+                 off(c->A64, cbb, p), p, nrhs, 1.0, -c->kappa, domain ? c->d_tc_dom : c->d_tc_full};
+    launch_dslash(c->g, k, st);
+  }
+}
+
+struct Inner {
+  int prec, nrhs, nseg;
+  VGeom vg;
+  const SegInfo* si;
+  const signed char* tc;
+  const void* U;
+  const void* Ainv_e;
+  const void* Ainv_o;
+  const void* b;  // prepared right-hand side; also the BiCGStab shadow residual r0
+  void *x, *r, *p, *v, *s, *t, *tmp;
+  KState ks;
+  double* partial;
+  double kappa;
+  int threads;
+};
+
+static void schur(lqcd_ctx* c, const Inner& in, const void* src, void* dst, cudaStream_t st) {
+  DslashCall k1{in.prec, EPI_CH, 0, src, nullptr, nullptr, in.tmp, in.U, in.Ainv_o, 1, in.nrhs, 0.0, 1.0, in.tc};
+  launch_dslash(c->g, k1, st, in.threads);
+  DslashCall k2{in.prec, EPI_Y_CH, 0, in.tmp, src, nullptr, dst, in.U, in.Ainv_e, 0, in.nrhs, 1.0,
+                -in.kappa * in.kappa, in.tc};
+  launch_dslash(c->g, k2, st, in.threads);
+}
+
+static void bicg_iteration(lqcd_ctx* c, const Inner& in, cudaStream_t st) {
+  const int P = in.prec;
+  schur(c, in, in.p, in.v, st);
+  bicg_alpha(P, in.b, in.v, in.vg, in.si, in.nseg, in.partial, in.ks, st);
+  bicg_s(P, in.r, in.v, in.s, in.vg, in.si, in.nseg, in.ks, st);
+  schur(c, in, in.s, in.t, st);
+  bicg_omega(P, in.t, in.s, in.vg, in.si, in.nseg, in.partial, in.ks, st);
+  bicg_xr(P, in.x, in.p, in.s, in.t, in.r, in.b, in.vg, in.si, in.nseg, in.partial, in.ks, st);
+  bicg_p(P, in.p, in.r, in.v, in.vg, in.si, in.nseg, in.ks, st);
+}
+
+static std::string graph_key(const Inner& in, int chunk) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "bicg:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p", in.prec, in.nrhs, in.nseg,
+           chunk, in.threads, in.b, in.x, in.r, in.p, in.v, in.s, in.t, in.tmp, (void*)in.ks.rho, in.partial,
+           (const void*)in.tc, (const void*)in.si, in.U);
+  return buf;
+}
+
+// Run BiCGStab on the prepared systems until all are inactive or max_iter; returns iterations.
+static int run_bicg(lqcd_ctx* c, const Inner& in, int max_iter, int chunk, bool use_graph, int* count_host,
+                    long long& dslash_calls) {
+  cudaStream_t st = c->work;
+  const int nsys = in.nrhs * in.nseg;
+  int it = 0;
+  cudaGraphExec_t exec = nullptr;
+  if (use_graph) {
+    std::string key = graph_key(in, chunk);
+    auto f = c->graphs.find(key);
+    if (f != c->graphs.end()) {
+      exec = f->second;
+    } else {
+      cudaGraph_t graph;
+      cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      for (int k = 0; k < chunk; k++) bicg_iteration(c, in, st);
+      count_active(in.ks.active, nsys, in.ks.count, st);
+      cudaMemcpyAsync(count_host, in.ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (cudaStreamEndCapture(st, &graph) == cudaSuccess &&
+          cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        c->graphs[key] = exec;
+      } else {
+        exec = nullptr;
+        cudaGetLastError();
+      }
+      cudaGraphDestroy(graph);
+    }
+  }
+  while (it < max_iter) {
+    if (exec) {
+      cudaGraphLaunch(exec, st);
+    } else {
+      for (int k = 0; k < chunk; k++) bicg_iteration(c, in, st);
+      count_active(in.ks.active, nsys, in.ks.count, st);
+      cudaMemcpyAsync(count_host, in.ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    }
+    it += chunk;
+    dslash_calls += 4LL * chunk;
+    cudaStreamSynchronize(st);
+    if (*count_host == 0) break;
+  }
+  return it;
+}
+
+int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain, const lqcd_solve_params& prm,
+                BatchStats& bs) {
+  cudaStream_t st = c->work;
+  const Geom& g = c->g;
+  const SegInfo* si = domain ? c->d_seg_dom : c->d_seg_full;
+  const int nseg = domain ? c->seg_dom.nseg : 1;
+  const int nsys = nrhs * nseg;
+  const signed char* tc = domain ? c->d_tc_dom : c->d_tc_full;
+  const double tol = prm.tol > 0 ? prm.tol : 1e-10;
+  const int max_iter = prm.max_iter > 0 ? prm.max_iter : 20000;
+  const int max_outer = prm.max_outer > 0 ? prm.max_outer : 20;
+  const int chunk = prm.check_every > 0 ? prm.check_every : 8;
+
+  int P = P64;
+  double inner_tol = 1e-12;
+  if (prm.solver == LQCD_SOLVER_MIXED || prm.solver == LQCD_SOLVER_FGCR_NN) {
+    P = prm.inner_prec == LQCD_PREC_F16 ? P16 : P32;
+    inner_tol = P == P32 ? 1e-5 : 1e-2;
+  }
+  if (prm.inner_tol > 0) inner_tol = prm.inner_tol;
+
+  VGeom vgF = make_vgeom(g, nrhs, 2);  // full lattice
+  VGeom vgH = make_vgeom(g, nrhs, 1);  // one parity
+  const size_t sb64 = spinor_bytes(g, P64, nrhs), sbP = spinor_bytes(g, P, nrhs);
+  const size_t cbP = clover_bytes(g, P);
+
+  // FP64 outer fields and per-system bookkeeping
+  double2* r64 = (double2*)ws_get(c, "o_r64", 2 * sb64);
+  size_t npart = (size_t)vgF.blocks * nrhs * 3;
+  double* partial = (double*)ws_get(c, "partial", npart * sizeof(double));
+  double* b2 = (double*)ws_get(c, "o_b2", nsys * sizeof(double));
+  double* r2 = (double*)ws_get(c, "o_r2", nsys * sizeof(double));
+  double* delta = (double*)ws_get(c, "o_delta", nsys * sizeof(double));
+  double* scale = (double*)ws_get(c, "o_scale", nsys * sizeof(double));
+  double* iscale = (double*)ws_get(c, "o_iscale", nsys * sizeof(double));
+  double* rel = (double*)ws_get(c, "o_rel", nsys * sizeof(double));
+  int* oact = (int*)ws_get(c, "o_active", nsys * sizeof(int));
+  // inner fields (precision P)
+  void* rin = ws_get(c, "i_rin", 2 * sbP);  // scaled residual, full lattice
+  void* ein = ws_get(c, "i_ein", 2 * sbP);  // correction, full lattice (even part = inner x)
+  Inner in;
+  in.prec = P;
+  in.nrhs = nrhs;
+  in.nseg = nseg;
+  in.vg = vgH;
+  in.si = si;
+  in.tc = tc;
+  in.U = P == P64 ? c->U64 : (P == P32 ? c->U32 : c->U16);
+  const void* Ainv = P == P64 ? c->Ainv64 : (P == P32 ? c->Ainv32 : c->Ainv16);
+  in.Ainv_e = off(Ainv, cbP, 0);
+  in.Ainv_o = off(Ainv, cbP, 1);
+  void* bhat = ws_get(c, "i_bhat", sbP);
+  in.b = bhat;
+  in.x = ein;  // even half of the full correction field
+  in.r = ws_get(c, "i_r", sbP);
+  in.p = ws_get(c, "i_p", sbP);
+  in.v = ws_get(c, "i_v", sbP);
+  in.s = ws_get(c, "i_s", sbP);
+  in.t = ws_get(c, "i_t", sbP);
+  in.tmp = ws_get(c, "i_tmp", sbP);
+  in.kappa = c->kappa;
+  in.threads = 0;
+  {
+    auto it = c->tuned_threads.find((long)P * 100000 + nrhs);
+    if (it != c->tuned_threads.end()) in.threads = it->second;
+  }
+  char* ksb = (char*)ws_get(c, "kstate", (size_t)nsys * (4 * 16 + 3 * 8 + 3 * 4) + 64);
+  in.ks.rho = (double2*)ksb;
+  in.ks.alpha = in.ks.rho + nsys;
+  in.ks.omega = in.ks.alpha + nsys;
+  in.ks.beta = in.ks.omega + nsys;
+  in.ks.r2 = (double*)(in.ks.beta + nsys);
+  in.ks.b2 = in.ks.r2 + nsys;
+  in.ks.stop2 = in.ks.b2 + nsys;
+  in.ks.active = (int*)(in.ks.stop2 + nsys);
+  in.ks.iters = in.ks.active + nsys;
+  in.ks.flag = in.ks.iters + nsys;
+  in.ks.count = (int*)ws_get(c, "kcount", 64);
+  in.partial = partial;
+  int* count_host = (int*)pinned_get(c, 64);
+  cudaMemsetAsync(in.ks.iters, 0, nsys * sizeof(int), st);
+
+  // x = 0, r = b, |b|^2
+  v_zero(P64, x, vgF, st);
+  cudaMemcpyAsync(r64, b, 2 * sb64, cudaMemcpyDeviceToDevice, st);
+  v_norm2(P64, b, vgF, si, nseg, partial, b2, st);
+  outer_update(b2, b2, nsys, tol, inner_tol, oact, delta, scale, rel, 1, st);
+
+  bs.cycles = 0;
+  bs.dslash = 0;
+  int total_iters = 0;
+  for (int cyc = 0; cyc < max_outer; cyc++) {
+    count_active(oact, nsys, in.ks.count, st);
+    cudaMemcpyAsync(count_host, in.ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (*count_host == 0 || total_iters >= max_iter) break;
+    bs.cycles++;
+    // scaled residual in the inner precision, Schur right-hand side
+    v_convert(P64, P, r64, rin, vgF, si, nseg, scale, st);
+    launch_clover_only(g, P, in.Ainv_o, off(rin, sbP, 1), in.tmp, nrhs, st);
+    DslashCall kp{P, EPI_C_YH, 0, in.tmp, off(rin, sbP, 0), nullptr, bhat, in.U, in.Ainv_e, 0, nrhs, 1.0,
+                  c->kappa, tc};
+    launch_dslash(g, kp, st, in.threads);
+    bs.dslash += 1;
+    // inner BiCGStab
+    bicg_init(P, bhat, in.r, in.p, in.x, vgH, si, nseg, partial, in.ks, delta, oact, st);
+    total_iters += run_bicg(c, in, max_iter - total_iters, chunk, prm.use_graph != 0, count_host, bs.dslash);
+    // odd half of the correction, then x += e / scale
+    DslashCall kr{P, EPI_C_YH, 0, in.x, off(rin, sbP, 1), nullptr, off(ein, sbP, 1), in.U, in.Ainv_o, 1, nrhs, 1.0,
+                  c->kappa, tc};
+    launch_dslash(g, kr, st, in.threads);
+    bs.dslash += 1;
+    recip(scale, iscale, nsys, st);
+    v_axpy_mixed(P, x, ein, vgF, si, nseg, iscale, oact, st);
+    // FP64 true residual r = b - D x
+    const size_t cb64 = clover_bytes(g, P64);
+    for (int p = 0; p < 2; p++) {
+      DslashCall k{P64, EPI_RES, 0, off(x, sb64, 1 - p), off(x, sb64, p), off(b, sb64, p), off(r64, sb64, p),
+                   c->U64, off(c->A64, cb64, p), p, nrhs, 1.0, -c->kappa, tc};
+      launch_dslash(g, k, st);
+    }
+    bs.dslash += 2;
+    v_norm2(P64, r64, vgF, si, nseg, partial, r2, st);
+    outer_update(r2, b2, nsys, tol, inner_tol, oact, delta, scale, rel, 0, st);
+  }
+  bs.rel.resize(nsys);
+  bs.iters.resize(nsys);
+  cudaMemcpyAsync(bs.rel.data(), rel, nsys * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(bs.iters.data(), in.ks.iters, nsys * sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e));
+  for (int i = 0; i < nsys; i++) {
+    if (!std::isfinite(bs.rel[i])) return set_error(c, LQCD_ERR_NAN, "solve: non-finite residual");
+    if (bs.rel[i] > tol) return set_error(c, LQCD_ERR_NOT_CONVERGED, "solve: tolerance not reached");
+  }
+  return LQCD_OK;
+}
+
+}  // namespace lqcd

@@ -1,0 +1,255 @@
+"""ctypes binding of the lqcd C ABI (include/lqcd.h): the same entry-point names, argument
+marshalling only.  Arrays may be numpy arrays (host memory, LQCD_HOST) or torch CUDA tensors
+(device memory, LQCD_DEVICE); complex arrays must be complex128 and C-contiguous.
+
+Importing this module loads liblqcd.so from the package directory and raises if it is missing:
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblqcd.so")
+
+LQCD_OK = 0
+LQCD_ERR_INVALID_ARG = 1
+LQCD_ERR_NOT_CONVERGED = 2
+LQCD_ERR_CUDA = 3
+LQCD_ERR_OOM = 4
+LQCD_ERR_TIMEOUT = 5
+LQCD_ERR_NAN = 6
+LQCD_ERR_STATE = 7
+LQCD_BC_PERIODIC, LQCD_BC_ANTIPERIODIC, LQCD_BC_OPEN = 0, 1, 2
+LQCD_HOST, LQCD_DEVICE = 0, 1
+LQCD_MODE_FULL, LQCD_MODE_DOMAIN = 0, 1
+LQCD_SINKS_DIAG, LQCD_SINKS_ALL = 0, 1
+LQCD_SOLVER_BICGSTAB64, LQCD_SOLVER_MIXED, LQCD_SOLVER_FGCR_NN = 0, 1, 2
+LQCD_PREC_F64, LQCD_PREC_F32, LQCD_PREC_F16 = 0, 1, 2
+
+EXPORTED = [
+    "lqcd_default_params", "lqcd_create", "lqcd_destroy", "lqcd_set_stream", "lqcd_last_error",
+    "lqcd_gauge_upload", "lqcd_set_domains", "lqcd_dirac_apply", "lqcd_solve_full",
+    "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
+    "lqcd_dslash_bench",
+]
+
+
+class lqcd_solve_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("solver", ctypes.c_int),
+                ("inner_prec", ctypes.c_int), ("rhs_block", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("gcr_nkrylov", ctypes.c_int),
+                ("precond_iters", ctypes.c_int)]
+
+
+class lqcd_solve_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.POINTER(ctypes.c_int)), ("true_resid", ctypes.POINTER(ctypes.c_double)),
+                ("n_seg", ctypes.c_int), ("outer_cycles", ctypes.c_int), ("total_iters", ctypes.c_longlong),
+                ("dslash_calls", ctypes.c_longlong), ("max_true_resid", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("fallback", ctypes.c_int)]
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lqcd error %d: %s" % (code, msg))
+        self.code = code
+
+
+def load_library(path=_LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("liblqcd.so not built (run python paper_2609_37049_b300/build.py): %s" % path)
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    c_int_p = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "lqcd_default_params": (None, [ctypes.POINTER(lqcd_solve_params)]),
+        "lqcd_create": (ip, [ctypes.POINTER(vp), c_int_p, ip, vp]),
+        "lqcd_destroy": (ip, [vp]),
+        "lqcd_set_stream": (ip, [vp, vp]),
+        "lqcd_last_error": (ctypes.c_char_p, [vp]),
+        "lqcd_gauge_upload": (ip, [vp, vp, ip, ctypes.c_double, ctypes.c_double]),
+        "lqcd_set_domains": (ip, [vp, c_int_p, ip]),
+        "lqcd_dirac_apply": (ip, [vp, vp, vp, ip, ip, ip]),
+        "lqcd_solve_full": (ip, [vp, vp, vp, ip, ip, ctypes.POINTER(lqcd_solve_params),
+                                 ctypes.POINTER(lqcd_solve_stats)]),
+        "lqcd_solve_domain": (ip, [vp, vp, vp, ip, ip, ctypes.POINTER(lqcd_solve_params),
+                                   ctypes.POINTER(lqcd_solve_stats)]),
+        "lqcd_perambulator": (ip, [vp, vp, ip, c_int_p, ip, ip, ip, ip, vp,
+                                   ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_stats)]),
+        "lqcd_loops": (ip, [vp, vp, ip, ip, c_int_p, ip, vp, vp, vp, ip]),
+        "lqcd_disc_correlator": (ip, [vp, vp, vp, vp, vp, ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, ip]),
+        "lqcd_dslash_bench": (ip, [vp, ip, ip, ip, ip, dp, dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def lib():
+    return _lib
+
+
+# ----------------------------------------------------------------------------- marshalling
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _where(*arrays):
+    kinds = {_is_torch(a) for a in arrays if a is not None}
+    if len(kinds) > 1:
+        raise TypeError("mix of host (numpy) and device (torch) arrays")
+    if kinds == {True}:
+        for a in arrays:
+            if a is not None and not a.is_cuda:
+                raise TypeError("torch tensors must live on the GPU")
+        return LQCD_DEVICE
+    return LQCD_HOST
+
+
+def _ptr(a, dtype=np.complex128):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous %s" % np.dtype(dtype).name)
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _int_array(vals):
+    arr = (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def default_params(**kw):
+    p = lqcd_solve_params()
+    _lib.lqcd_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Stats:
+    """Host-side holder for lqcd_solve_stats plus its per-RHS arrays."""
+
+    def __init__(self, nrhs, nseg):
+        self.iters = np.zeros(nrhs, dtype=np.int32)
+        self.true_resid = np.zeros(nrhs * nseg, dtype=np.float64)
+        self.c = lqcd_solve_stats()
+        self.c.iters = self.iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        self.c.true_resid = self.true_resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def __getattr__(self, k):
+        return getattr(self.c, k)
+
+
+class Context:
+    """One lqcd context: a lattice of extents dims = (Lx, Ly, Lz, Lt) on the current GPU."""
+
+    def __init__(self, dims, bc_t=LQCD_BC_ANTIPERIODIC, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.h = ctypes.c_void_p()
+        L = _int_array(self.dims)
+        rc = _lib.lqcd_create(ctypes.byref(self.h), L, int(bc_t), stream or _current_stream())
+        if rc != LQCD_OK:
+            raise LqcdError(rc, _lib.lqcd_last_error(None).decode())
+        self.extents = [self.dims[3]]
+
+    @property
+    def volume(self):
+        Lx, Ly, Lz, Lt = self.dims
+        return Lx * Ly * Lz * Lt
+
+    def close(self):
+        if self.h:
+            _lib.lqcd_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != LQCD_OK and rc not in allow:
+            raise LqcdError(rc, _lib.lqcd_last_error(self.h).decode())
+        return rc
+
+    def set_stream(self, stream=None):
+        return self._check(_lib.lqcd_set_stream(self.h, stream or _current_stream()))
+
+    def gauge_upload(self, links, kappa, c_sw):
+        return self._check(_lib.lqcd_gauge_upload(self.h, _ptr(links), _where(links), float(kappa),
+                                                  float(c_sw)))
+
+    def set_domains(self, extents):
+        rc = self._check(_lib.lqcd_set_domains(self.h, _int_array(extents), len(extents)))
+        self.extents = [int(e) for e in extents]
+        return rc
+
+    def dirac_apply(self, psi, out, domain_restricted=False):
+        nrhs = psi.shape[0]
+        return self._check(_lib.lqcd_dirac_apply(self.h, _ptr(psi), _ptr(out), nrhs, int(domain_restricted),
+                                                 _where(psi, out)))
+
+    def solve(self, b, x, params=None, domain=False, stats=None, allow_not_converged=False):
+        nrhs = b.shape[0]
+        p = params or default_params()
+        f = _lib.lqcd_solve_domain if domain else _lib.lqcd_solve_full
+        st = stats.c if stats is not None else None
+        if stats is not None:
+            nseg = len(self.extents) if domain else 1
+            if stats.iters.size < nrhs or stats.true_resid.size < nrhs * nseg:
+                raise ValueError("Stats arrays too small for %d right-hand sides x %d segments" % (nrhs, nseg))
+        rc = f(self.h, _ptr(b), _ptr(x), nrhs, _where(b, x), ctypes.byref(p),
+               ctypes.byref(st) if st is not None else None)
+        return self._check(rc, allow=(LQCD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+
+    def perambulator(self, Vt, n_ev, t_src, tau, mode=LQCD_MODE_FULL, sinks=LQCD_SINKS_DIAG, params=None,
+                     stats=None):
+        p = params or default_params()
+        st = stats.c if stats is not None else None
+        rc = _lib.lqcd_perambulator(self.h, _ptr(Vt), int(n_ev), _int_array(t_src), len(t_src), int(mode),
+                                    int(sinks), _where(Vt, tau), _ptr(tau), ctypes.byref(p),
+                                    ctypes.byref(st) if st is not None else None)
+        return self._check(rc)
+
+    def loops(self, tau, n_ev, n_t, gamma_ids, L, Lt, weights=None):
+        return self._check(_lib.lqcd_loops(self.h, _ptr(tau), int(n_ev), int(n_t), _int_array(gamma_ids),
+                                           len(gamma_ids), _ptr(weights, np.float64), _ptr(L), _ptr(Lt),
+                                           _where(tau, L, Lt, weights)))
+
+    def disc_correlator(self, L, Lt, Ld, Ltd, vev, out, terms=None):
+        """out: dict with C, Cdd, dC, C_avg, dC_avg (complex), valid, n_valid (int32)."""
+        n_cfg, n_g = L.shape[0], L.shape[1]
+        w = _where(L, Lt, Ld, Ltd, out["C"])
+        return self._check(_lib.lqcd_disc_correlator(
+            self.h, _ptr(L), _ptr(Lt), _ptr(Ld), _ptr(Ltd), n_cfg, n_g, int(vev), _ptr(out["C"]),
+            _ptr(out["Cdd"]), _ptr(out["dC"]), _ptr(out["C_avg"]), _ptr(out["dC_avg"]),
+            _ptr(out["valid"], np.int32), _ptr(out["n_valid"], np.int32), _ptr(terms), w))
+
+    def dslash_bench(self, prec, nrhs, n_iter=20, flush_l2=True):
+        """(ms per launch, algorithmic bytes per launch) of the eo hopping + clover-inverse kernel."""
+        ms, by = ctypes.c_double(), ctypes.c_double()
+        self._check(_lib.lqcd_dslash_bench(self.h, int(prec), int(nrhs), int(n_iter), int(flush_l2),
+                                           ctypes.byref(ms), ctypes.byref(by)))
+        return ms.value, by.value

@@ -1,0 +1,128 @@
+"""GPU parity of the operator and the solvers against the FP64 oracle (Sec. 2.1, Sec. 3).
+
+The operator is compared element by element (FP64 round-off); every solve is checked by the
+ORACLE's operator: ||b - D x_gpu|| / ||b|| <= 1e-10 per right-hand side (and per domain for the
+Dirichlet domain operator), and x_gpu against the oracle's own solution."""
+import numpy as np
+import pytest
+
+from lqcd_inputs import gauge_field, random_spinors
+from oracle.dirac import WilsonClover, BC_ANTIPERIODIC, BC_PERIODIC, BC_OPEN
+from oracle.solve import cgnr
+from tests.lattice_cases import ROUGH, gauge, rel_max, per_domain_resid
+
+pytestmark = pytest.mark.gpu
+
+lqcd_pkg = pytest.importorskip("paper_2609_37049_b300")
+from paper_2609_37049_b300 import Context, Stats, default_params, lqcd  # noqa: E402
+
+
+@pytest.mark.parametrize("dims,bc,ext", [
+    ((4, 4, 4, 8), BC_ANTIPERIODIC, [4, 4]),
+    ((6, 4, 2, 8), BC_PERIODIC, [2, 3, 3]),
+    ((4, 2, 4, 6), BC_OPEN, [6]),
+    ((2, 2, 2, 4), BC_ANTIPERIODIC, [1, 3]),
+])
+def test_dirac_apply_parity(dims, bc, ext):
+    U = gauge_field(dims, 0.5, 1234)
+    op = WilsonClover(U, 0.125, 1.6, bc)
+    psi = random_spinors(dims, 3, 7)
+    ctx = Context(dims, bc)
+    ctx.gauge_upload(U, 0.125, 1.6)
+    out = np.zeros_like(psi)
+    ctx.dirac_apply(psi, out)
+    assert rel_max(out, op.apply(psi)) < 1e-14
+    ctx.set_domains(ext)
+    ctx.dirac_apply(psi, out, domain_restricted=True)
+    assert rel_max(out, op.restricted(ext).apply(psi)) < 1e-14
+
+
+def test_dirac_apply_device_pointers():
+    torch = pytest.importorskip("torch")
+    dims = (4, 4, 4, 8)
+    U = gauge_field(dims, 0.5, 99)
+    psi = random_spinors(dims, 2, 5)
+    ctx = Context(dims)
+    ctx.gauge_upload(torch.from_numpy(U).cuda(), 0.125, 1.6)
+    out = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda")
+    ctx.dirac_apply(torch.from_numpy(psi).cuda(), out)
+    torch.cuda.synchronize()
+    assert rel_max(out.cpu().numpy(), WilsonClover(U, 0.125, 1.6).apply(psi)) < 1e-14
+
+
+SOLVERS = [
+    ("bicgstab64", dict(solver=lqcd.LQCD_SOLVER_BICGSTAB64)),
+    ("mixed32", dict(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F32)),
+    ("mixed16", dict(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F16)),
+    ("nograph", dict(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F32, use_graph=0)),
+]
+
+
+@pytest.mark.parametrize("name,kw", SOLVERS)
+@pytest.mark.parametrize("domain", [False, True])
+def test_solve_true_residual(name, kw, domain):
+    case = ROUGH
+    U = gauge(case, 2024)
+    op = WilsonClover(U, case["kappa"], case["c_sw"])
+    ext = case["extents"]
+    b = random_spinors(case["dims"], 5, 11)
+    ctx = Context(case["dims"])
+    ctx.gauge_upload(U, case["kappa"], case["c_sw"])
+    ctx.set_domains(ext)
+    x = np.zeros_like(b)
+    st = Stats(5, len(ext) if domain else 1)
+    ctx.solve(b, x, default_params(rhs_block=3, **kw), domain=domain, stats=st)
+    ref_op = op.restricted(ext) if domain else op
+    r = b - ref_op.apply(x)
+    res = per_domain_resid(b, r, ext if domain else [case["dims"][3]])
+    assert res.max() <= 1.02e-10, res
+    assert st.max_true_resid <= 1e-10 and np.all(st.true_resid <= 1e-10)
+    assert np.all(st.iters > 0)
+    xo, _ = cgnr(ref_op, b, tol=1e-13)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-8
+
+
+def test_domain_solve_with_empty_domain_and_one_domain_equals_full():
+    case = ROUGH
+    U = gauge(case, 7)
+    ctx = Context(case["dims"])
+    ctx.gauge_upload(U, case["kappa"], case["c_sw"])
+    b = random_spinors(case["dims"], 2, 3)
+    b[:, 4:] = 0  # nothing in the second domain
+    ctx.set_domains([4, 4])
+    x = np.zeros_like(b)
+    st = Stats(2, 2)
+    ctx.solve(b, x, default_params(), domain=True, stats=st)
+    assert np.abs(x[:, 4:]).max() == 0
+    assert np.all(st.true_resid.reshape(2, 2)[:, 1] == 0)
+    # a single domain covering the whole time axis is the full operator
+    ctx.set_domains([8])
+    xd, xf = np.zeros_like(b), np.zeros_like(b)
+    ctx.solve(b, xd, default_params(), domain=True)
+    ctx.solve(b, xf, default_params(), domain=False)
+    assert np.array_equal(xd, xf)
+
+
+def test_invalid_arguments_do_nothing():
+    ctx = Context((4, 4, 4, 8))
+    with pytest.raises(lqcd.LqcdError) as e:
+        ctx.set_domains([4, 3])
+    assert e.value.code == lqcd.LQCD_ERR_INVALID_ARG
+    b = np.zeros((1, 8, 4, 4, 4, 4, 3), dtype=complex)
+    with pytest.raises(lqcd.LqcdError) as e:
+        ctx.solve(b, b.copy())
+    assert e.value.code == lqcd.LQCD_ERR_STATE
+
+
+def test_not_converged_reports_partial_result():
+    case = ROUGH
+    U = gauge(case, 5)
+    ctx = Context(case["dims"])
+    ctx.gauge_upload(U, case["kappa"], case["c_sw"])
+    b = random_spinors(case["dims"], 1, 3)
+    x = np.zeros_like(b)
+    st = Stats(1, 1)
+    rc = ctx.solve(b, x, default_params(max_iter=8, max_outer=1, check_every=4), stats=st,
+                   allow_not_converged=True)
+    assert rc == lqcd.LQCD_ERR_NOT_CONVERGED
+    assert 1e-10 < st.max_true_resid < 1.0
