@@ -173,6 +173,15 @@ int lqcd_disc_correlator(lqcd_ctx* ctx, const double* L, const double* Lt, const
                          double* dC, double* C_avg, double* dC_avg, int* valid, int* n_valid,
                          double* terms, int where);
 
+/* Distillation vectors (Sec. 3.1, 3.2): the n_ev lowest eigenpairs of the gauge-covariant 3D
+ * Laplacian  (-Lap phi)(x) = sum_k [2 phi(x) - U_k(x) phi(x+k) - U_k(x-k)^dag phi(x-k)]  on every
+ * timeslice of the uploaded gauge field, to residual ||(-Lap) v - lambda v|| <= tol (0 -> 1e-10).
+ *   V:      [Lt][n_ev][Lx Ly Lz][3] complex, unit norm, largest-modulus component (first on ties)
+ *           made real positive;   lambda: [Lt][n_ev] real, ascending per timeslice.
+ *   iters (may be NULL): filter iterations of the slowest timeslice chunk.
+ * Errors: INVALID_ARG (n_ev < 1 or > 3 Lx Ly Lz), STATE (no gauge field), NOT_CONVERGED. */
+int lqcd_laplace_eigs(lqcd_ctx* ctx, int n_ev, double* V, double* lambda, int where, double tol, int* iters);
+
 /* Time the even-odd hopping kernel with the fused inverse-clover epilogue,
  * out_o = A_oo^{-1} H_oe in_e (one half of the Schur operator of Sec. 2.1's block form), on
  * nrhs right-hand sides in precision prec (LQCD_PREC_*), over n_iter launches on the context's
@@ -184,6 +193,10 @@ int lqcd_disc_correlator(lqcd_ctx* ctx, const double* L, const double* Lt, const
  * Fills the input with deterministic non-zero data.  Needs a gauge field.  Errors: INVALID_ARG. */
 int lqcd_dslash_bench(lqcd_ctx* ctx, int prec, int nrhs, int n_iter, int flush_l2, double* ms_per_launch,
                       double* algo_bytes_per_launch);
+
+/* Number of CUDA kernels this library has put on GPU queues in this process (all contexts):
+ * direct launches plus the kernel nodes of every replayed CUDA graph.  For accounting only. */
+long long lqcd_kernel_launches(void);
 
 #ifdef __cplusplus
 }

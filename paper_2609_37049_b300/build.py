@@ -24,7 +24,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblqcd.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fopenmp", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
 
 
@@ -58,7 +58,7 @@ def build(force=False, verbose=False):
     if changed or force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
             os.path.getmtime(o) for o in objs):
         cmd = [NVCC] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker",
-                               "-rpath,/usr/local/cuda/lib64", "-o", LIB] + objs
+                               "-rpath,/usr/local/cuda/lib64", "-Xcompiler", "-fopenmp", "-o", LIB] + objs
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,6 +1,8 @@
 // extern "C" entry points declared in include/lqcd.h: argument checks, host/device staging,
 // stream ordering, batching of right-hand sides.  All arithmetic runs in the CUDA kernels of
 // this library.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -13,8 +15,15 @@
 using namespace lqcd;
 
 static std::string g_create_error;
+static std::atomic<long long> g_launches{0};
+static thread_local bool g_capturing = false;
 
 namespace lqcd {
+
+void count_launch(long long n) {
+  if (!g_capturing) g_launches += n;
+}
+void set_capturing(bool on) { g_capturing = on; }
 
 int set_error(lqcd_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -31,6 +40,7 @@ void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes) {
     // graphs captured on the old buffer are stale
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
+    c->graph_kernels.clear();
   }
   void* p = nullptr;
   if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
@@ -253,6 +263,8 @@ __global__ void k_scatter_tau(const double2* C, int nsinks, int n_ev, int nrhs, 
 }  // namespace
 
 extern "C" {
+
+long long lqcd_kernel_launches(void) { return g_launches.load(); }
 
 void lqcd_default_params(lqcd_solve_params* p) {
   if (!p) return;
@@ -566,7 +578,7 @@ int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src,
       project(g, dV, n_ev, ex, d_z, nz, C, nb, c->work);
       long n = (long)nz * n_ev * 4 * nb;
       k_scatter_tau<<<(n + 255) / 256, 256, 0, c->work>>>(C, nz, n_ev, nb, r0, d_z + LQCD_MAXT, d_z,
-                                                          sinks == LQCD_SINKS_ALL, g.Lt, dtau);
+                                                          sinks == LQCD_SINKS_ALL, g.Lt, dtau); lqcd::count_launch();
       if (int e = cuda_check(c, "perambulator")) return e;
     }
   }
@@ -657,6 +669,27 @@ int lqcd_disc_correlator(lqcd_ctx* c, const double* L, const double* Lt, const d
 
 }  // extern "C"
 
+extern "C" int lqcd_laplace_eigs(lqcd_ctx* c, int n_ev, double* V, double* lambda, int where, double tol,
+                                 int* iters) {
+  if (!c || !V || !lambda) return set_error(c, LQCD_ERR_INVALID_ARG, "laplace_eigs: NULL argument");
+  const Geom& g = c->g;
+  const long L3 = (long)g.Lx * g.Ly * g.Lz;
+  if (n_ev < 1 || n_ev > 3 * L3) return set_error(c, LQCD_ERR_INVALID_ARG, "laplace_eigs: bad n_ev");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "laplace_eigs: no gauge field uploaded");
+  Scope sc(c);
+  size_t vb = (size_t)g.Lt * n_ev * L3 * 3 * sizeof(double2), lb = (size_t)g.Lt * n_ev * sizeof(double);
+  double2* dV = (double2*)stage_out(c, V, vb, where, "e_V");
+  double* dl = (double*)stage_out(c, lambda, lb, where, "e_lam");
+  if (!dV || !dl) return set_error(c, LQCD_ERR_OOM, "laplace_eigs: OOM");
+  int it = 0;
+  int rc = laplace_eigs(c, n_ev, dV, dl, tol > 0 ? tol : 1e-10, 500, &it);
+  if (iters) *iters = it;
+  if (rc != LQCD_OK) return rc;
+  if (int e = cuda_check(c, "laplace_eigs")) return e;
+  if (int e = finish_out(c, V, dV, vb, where)) return e;
+  return finish_out(c, lambda, dl, lb, where);
+}
+
 namespace {
 __global__ void k_fill_pattern(float* p, long n, unsigned seed) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -694,7 +727,7 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
     cudaMemsetAsync(in, 0x3c, sb, c->work);  // every half = 1.0 + tiny mantissa pattern
   } else {
     long nf = (long)(sb / sizeof(float));
-    k_fill_pattern<<<(nf + 255) / 256, 256, 0, c->work>>>((float*)in, nf, 12345u);
+    k_fill_pattern<<<(nf + 255) / 256, 256, 0, c->work>>>((float*)in, nf, 12345u); lqcd::count_launch();
     if (P == P64) cudaMemsetAsync(in, 0, 0, c->work);
   }
   if (P == P64) {
@@ -720,7 +753,10 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
   cudaEventCreate(&e1);
   double total = 0;
   for (int i = 0; i < n_iter; i++) {
-    if (fl) k_flush<<<(flush_n + 255) / 256, 256, 0, c->work>>>(fl, (long)flush_n);
+    if (fl) {
+      k_flush<<<(flush_n + 255) / 256, 256, 0, c->work>>>(fl, (long)flush_n);
+      lqcd::count_launch();
+    }
     cudaEventRecord(e0, c->work);
     launch_dslash(g, k, c->work, threads);
     cudaEventRecord(e1, c->work);

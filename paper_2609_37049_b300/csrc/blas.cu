@@ -449,17 +449,22 @@ static inline dim3 fin_grid(const VGeom& vg, int nseg) { return dim3(vg.nrhs, ns
     if ((prec) == P64) KERNEL<P64> __VA_ARGS__;  \
     else if ((prec) == P32) KERNEL<P32> __VA_ARGS__; \
     else KERNEL<P16> __VA_ARGS__;                \
+    lqcd::count_launch();                        \
   } while (0)
 
 void v_norm2(int prec, const void* x, const VGeom& vg, const SegInfo* si, int nseg, double* partial, double* out,
              cudaStream_t st) {
   DISPATCH_P(prec, k_norm2, <<<vg.blocks, vg.threads(), shm(vg, 1), st>>>(x, vg, si, partial));
-  k_fin_sum1<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, out);
+  k_fin_sum1<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, out); lqcd::count_launch();
 }
 
 void v_convert(int pin, int pout, const void* in, void* out, const VGeom& vg, const SegInfo* si, int nseg,
                const double* scale, cudaStream_t st) {
-#define CONV(A, B) k_convert<A, B><<<vg.blocks, vg.threads(), 0, st>>>(in, out, vg, si, nseg, scale)
+#define CONV(A, B)                                                                    \
+  do {                                                                                \
+    k_convert<A, B><<<vg.blocks, vg.threads(), 0, st>>>(in, out, vg, si, nseg, scale); \
+    lqcd::count_launch();                                                             \
+  } while (0)
   if (pin == P64 && pout == P32) CONV(P64, P32);
   else if (pin == P64 && pout == P16) CONV(P64, P16);
   else if (pin == P32 && pout == P64) CONV(P32, P64);
@@ -488,13 +493,13 @@ void v_copy(int prec, const void* a, void* b, const VGeom& vg, cudaStream_t st) 
 void bicg_init(int prec, const void* b, void* r, void* p, void* x, const VGeom& vg, const SegInfo* si, int nseg,
                double* partial, const KState& ks, const double* delta, const int* outer_active, cudaStream_t st) {
   DISPATCH_P(prec, k_bicg_init, <<<vg.blocks, vg.threads(), shm(vg, 1), st>>>(b, r, p, x, vg, si, partial));
-  k_bicg_fin_init<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks, delta, outer_active);
+  k_bicg_fin_init<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks, delta, outer_active); lqcd::count_launch();
 }
 
 void bicg_alpha(int prec, const void* r0, const void* v, const VGeom& vg, const SegInfo* si, int nseg,
                 double* partial, const KState& ks, cudaStream_t st) {
   DISPATCH_P(prec, k_dot, <<<vg.blocks, vg.threads(), shm(vg, 2), st>>>(r0, v, vg, si, partial));
-  k_bicg_fin_alpha<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+  k_bicg_fin_alpha<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
 }
 
 void bicg_s(int prec, const void* r, const void* v, void* s, const VGeom& vg, const SegInfo* si, int nseg,
@@ -505,14 +510,14 @@ void bicg_s(int prec, const void* r, const void* v, void* s, const VGeom& vg, co
 void bicg_omega(int prec, const void* t, const void* s, const VGeom& vg, const SegInfo* si, int nseg,
                 double* partial, const KState& ks, cudaStream_t st) {
   DISPATCH_P(prec, k_dot_ts, <<<vg.blocks, vg.threads(), shm(vg, 3), st>>>(t, s, vg, si, partial));
-  k_bicg_fin_omega<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+  k_bicg_fin_omega<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
 }
 
 void bicg_xr(int prec, void* x, const void* p, const void* s, const void* t, void* r, const void* r0,
              const VGeom& vg, const SegInfo* si, int nseg, double* partial, const KState& ks, cudaStream_t st) {
   DISPATCH_P(prec, k_bicg_xr,
              <<<vg.blocks, vg.threads(), shm(vg, 3), st>>>(x, p, s, t, r, r0, vg, si, nseg, ks, partial));
-  k_bicg_fin_beta<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+  k_bicg_fin_beta<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
 }
 
 void bicg_p(int prec, void* p, const void* r, const void* v, const VGeom& vg, const SegInfo* si, int nseg,
@@ -521,17 +526,17 @@ void bicg_p(int prec, void* p, const void* r, const void* v, const VGeom& vg, co
 }
 
 void count_active(const int* active, int n, int* count, cudaStream_t st) {
-  k_count_active<<<1, 256, 0, st>>>(active, n, count);
+  k_count_active<<<1, 256, 0, st>>>(active, n, count); lqcd::count_launch();
 }
 
 void outer_update(const double* r2, const double* b2, int nsys, double tol, double inner_tol, int* active,
                   double* delta, double* scale, double* rel, int first, cudaStream_t st) {
   k_outer_update<<<(nsys + 127) / 128, 128, 0, st>>>(r2, b2, nsys, tol, inner_tol, active, delta, scale, rel,
-                                                     first);
+                                                     first); lqcd::count_launch();
 }
 
 void recip(const double* a, double* b, int n, cudaStream_t st) {
-  k_recip<<<(n + 127) / 128, 128, 0, st>>>(a, b, n);
+  k_recip<<<(n + 127) / 128, 128, 0, st>>>(a, b, n); lqcd::count_launch();
 }
 
 }  // namespace lqcd

@@ -240,10 +240,10 @@ void build_gauge(lqcd_ctx* c, const double2* links_dev, int* bad_dev) {
   long V = 2 * g.Vh;
   int tpb = 128;
   long blocks = (V + tpb - 1) / tpb;
-  k_pack_links<<<blocks, tpb, 0, c->work>>>(links_dev, g, (double2*)c->U64, (float4*)c->U32, (uint2*)c->U16);
+  k_pack_links<<<blocks, tpb, 0, c->work>>>(links_dev, g, (double2*)c->U64, (float4*)c->U32, (uint2*)c->U16); lqcd::count_launch();
   k_clover_build<<<(V + 63) / 64, 64, 0, c->work>>>(links_dev, g, c->kappa, c->csw, (double2*)c->A64,
                                                     (double2*)c->Ainv64, (float4*)c->A32, (float4*)c->Ainv32,
-                                                    (uint2*)c->Ainv16, bad_dev);
+                                                    (uint2*)c->Ainv16, bad_dev); lqcd::count_launch();
 }
 
 }  // namespace lqcd

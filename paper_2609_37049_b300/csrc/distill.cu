@@ -34,11 +34,11 @@ __global__ void k_pack_spinor(const double2* in, double2* out, Geom g, int nrhs,
 
 void pack_spinor(const Geom& g, const double2* lex, double2* eo, int nrhs, cudaStream_t st) {
   long n = 2 * g.Vh * (long)nrhs;
-  k_pack_spinor<<<(n + 255) / 256, 256, 0, st>>>(lex, eo, g, nrhs, 1);
+  k_pack_spinor<<<(n + 255) / 256, 256, 0, st>>>(lex, eo, g, nrhs, 1); lqcd::count_launch();
 }
 void unpack_spinor(const Geom& g, const double2* eo, double2* lex, int nrhs, cudaStream_t st) {
   long n = 2 * g.Vh * (long)nrhs;
-  k_pack_spinor<<<(n + 255) / 256, 256, 0, st>>>(eo, lex, g, nrhs, 0);
+  k_pack_spinor<<<(n + 255) / 256, 256, 0, st>>>(eo, lex, g, nrhs, 0); lqcd::count_launch();
 }
 
 // ------------------------------------------------------------------ sources
@@ -70,7 +70,7 @@ __global__ void k_sources(const double2* Vt, int n_ev, const int* jr, const int*
 void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, const int* br,
                   const unsigned char* srcmask, double2* b, int nrhs, cudaStream_t st) {
   long n = 2 * g.Vh * (long)nrhs;
-  k_sources<<<(n + 255) / 256, 256, 0, st>>>(Vt, n_ev, jr, br, srcmask, b, g, nrhs);
+  k_sources<<<(n + 255) / 256, 256, 0, st>>>(Vt, n_ev, jr, br, srcmask, b, g, nrhs); lqcd::count_launch();
 }
 
 // ------------------------------------------------------------------ projection
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_project(const double2* Vt, int n_ev, co
 void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, int nsinks, double2* C,
              int nrhs, cudaStream_t st) {
   dim3 grid((4 * nrhs + PBN - 1) / PBN, (n_ev + PBM - 1) / PBM, nsinks);
-  k_project<<<grid, 256, 0, st>>>(Vt, n_ev, X, sinks, C, g, nrhs);
+  k_project<<<grid, 256, 0, st>>>(Vt, n_ev, X, sinks, C, g, nrhs); lqcd::count_launch();
 }
 
 // ------------------------------------------------------------------ loops
@@ -186,7 +186,7 @@ __global__ void k_loops(const double2* tau, int n_ev, int n_t, const double2* G,
 
 void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w, double2* L,
            double2* Lt, cudaStream_t st) {
-  k_loops<<<dim3(n_gamma, n_t), 128, 0, st>>>(tau, n_ev, n_t, G, n_gamma, w, L, Lt);
+  k_loops<<<dim3(n_gamma, n_t), 128, 0, st>>>(tau, n_ev, n_t, G, n_gamma, w, L, Lt); lqcd::count_launch();
 }
 
 // ------------------------------------------------------------------ correlators
@@ -265,12 +265,12 @@ void correlators(const double2* L, const double2* Lt, const double2* Ld, const d
                  cudaStream_t st) {
   long n = (long)n_cfg * n_g * T;
   if (terms) {
-    k_diff<<<(n + 255) / 256, 256, 0, st>>>(L, Ld, dL, n);
-    k_diff<<<(n + 255) / 256, 256, 0, st>>>(Lt, Ltd, dLt, n);
+    k_diff<<<(n + 255) / 256, 256, 0, st>>>(L, Ld, dL, n); lqcd::count_launch();
+    k_diff<<<(n + 255) / 256, 256, 0, st>>>(Lt, Ltd, dLt, n); lqcd::count_launch();
   }
   k_corr<<<dim3(n_g, T), ((T + 31) / 32) * 32, 0, st>>>(L, Lt, Ld, Ltd, n_cfg, n_g, T, vev, dom, C, Cdd, dC, valid,
-                                                        terms, dL, dLt);
-  k_corr_avg<<<n_g, ((T + 31) / 32) * 32, 0, st>>>(C, dC, dom, n_g, T, C_avg, dC_avg, n_valid);
+                                                        terms, dL, dLt); lqcd::count_launch();
+  k_corr_avg<<<n_g, ((T + 31) / 32) * 32, 0, st>>>(C, dC, dom, n_g, T, C_avg, dC_avg, n_valid); lqcd::count_launch();
 }
 
 }  // namespace lqcd

@@ -242,6 +242,7 @@ static void launch_p_e(const DslashParams& pr, bool dag, long nthreads, int tpb,
     dslash_kernel<P, EPI, true><<<blocks, tpb, 0, st>>>(pr);
   else
     dslash_kernel<P, EPI, false><<<blocks, tpb, 0, st>>>(pr);
+  lqcd::count_launch();
 }
 
 template <int P>
@@ -292,6 +293,7 @@ void launch_clover_only(const Geom& g, int prec, const void* C, const void* in, 
     clover_only_kernel<P32><<<blocks, tpb, 0, st>>>(C, in, out, g.Vh, nrhs);
   else
     clover_only_kernel<P16><<<blocks, tpb, 0, st>>>(C, in, out, g.Vh, nrhs);
+  lqcd::count_launch();
 }
 
 }  // namespace lqcd

@@ -30,6 +30,10 @@ struct BatchStats {
 // the full even-odd FP64 layout on the device.  Returns LQCD_OK or LQCD_ERR_NOT_CONVERGED.
 int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain, const lqcd_solve_params& p,
                 BatchStats& bs);
+// Lowest n_ev eigenpairs of the covariant 3D Laplacian on every timeslice (laplace.cu);
+// Vout [Lt][n_ev][L3][3] and lam_out [Lt][n_ev] are device pointers.
+int laplace_eigs(lqcd_ctx* c, int n_ev, double2* Vout, double* lam_out_dev, double tol, int max_iter,
+                 int* iters_out);
 // out = D in (or D_Lambda in), full even-odd FP64 layout.
 void apply_D(lqcd_ctx* c, const double2* in, double2* out, int nrhs, int domain, cudaStream_t st);
 }  // namespace lqcd

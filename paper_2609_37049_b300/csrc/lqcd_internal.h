@@ -123,11 +123,17 @@ struct lqcd_ctx {
   std::map<long, int> tuned_threads;
   // instantiated CUDA graphs of Krylov iteration chunks, keyed by buffers and shape
   std::map<std::string, cudaGraphExec_t> graphs;
+  std::map<cudaGraphExec_t, long long> graph_kernels;  // kernel nodes per instantiated graph
   // Clifford table on the device: [16][2][4][4] complex (Gamma, Gamma-tilde)
   double2* d_gamma = nullptr;
 };
 
 namespace lqcd {
+// Process-wide count of kernels this library has put on a GPU queue: every launch site calls
+// count_launch(); launches recorded while a stream is being captured are not counted, a graph
+// replay adds the number of kernel nodes of the graph instead.
+void count_launch(long long n = 1);
+void set_capturing(bool on);
 void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes);
 void* pinned_get(lqcd_ctx* c, size_t bytes);
 int set_error(lqcd_ctx* c, int code, const std::string& msg);

@@ -107,13 +107,26 @@ static int run_bicg(lqcd_ctx* c, const Inner& in, int max_iter, int chunk, bool 
       exec = f->second;
     } else {
       cudaGraph_t graph;
+      set_capturing(true);
       cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
       for (int k = 0; k < chunk; k++) bicg_iteration(c, in, st);
       count_active(in.ks.active, nsys, in.ks.count, st);
       cudaMemcpyAsync(count_host, in.ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
-      if (cudaStreamEndCapture(st, &graph) == cudaSuccess &&
-          cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+      cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      set_capturing(false);
+      if (ce == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
         c->graphs[key] = exec;
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(graph, nodes.data(), &nn);
+        long long nk = 0;
+        for (auto nd : nodes) {
+          cudaGraphNodeType ty;
+          cudaGraphNodeGetType(nd, &ty);
+          nk += ty == cudaGraphNodeTypeKernel;
+        }
+        c->graph_kernels[exec] = nk;
       } else {
         exec = nullptr;
         cudaGetLastError();
@@ -124,6 +137,7 @@ static int run_bicg(lqcd_ctx* c, const Inner& in, int max_iter, int chunk, bool 
   while (it < max_iter) {
     if (exec) {
       cudaGraphLaunch(exec, st);
+      count_launch(c->graph_kernels[exec]);
     } else {
       for (int k = 0; k < chunk; k++) bicg_iteration(c, in, st);
       count_active(in.ks.active, nsys, in.ks.count, st);

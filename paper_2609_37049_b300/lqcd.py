@@ -31,8 +31,13 @@ EXPORTED = [
     "lqcd_default_params", "lqcd_create", "lqcd_destroy", "lqcd_set_stream", "lqcd_last_error",
     "lqcd_gauge_upload", "lqcd_set_domains", "lqcd_dirac_apply", "lqcd_solve_full",
     "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
-    "lqcd_dslash_bench",
+    "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs",
 ]
+
+
+def kernel_launches():
+    """Kernels this library has queued in this process (direct launches + graph kernel nodes)."""
+    return int(_lib.lqcd_kernel_launches())
 
 
 class lqcd_solve_params(ctypes.Structure):
@@ -80,6 +85,8 @@ def load_library(path=_LIB_PATH):
         "lqcd_loops": (ip, [vp, vp, ip, ip, c_int_p, ip, vp, vp, vp, ip]),
         "lqcd_disc_correlator": (ip, [vp, vp, vp, vp, vp, ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, ip]),
         "lqcd_dslash_bench": (ip, [vp, ip, ip, ip, ip, dp, dp]),
+        "lqcd_kernel_launches": (ctypes.c_longlong, []),
+        "lqcd_laplace_eigs": (ip, [vp, ip, vp, vp, ip, ctypes.c_double, c_int_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -246,6 +253,13 @@ class Context:
             self.h, _ptr(L), _ptr(Lt), _ptr(Ld), _ptr(Ltd), n_cfg, n_g, int(vev), _ptr(out["C"]),
             _ptr(out["Cdd"]), _ptr(out["dC"]), _ptr(out["C_avg"]), _ptr(out["dC_avg"]),
             _ptr(out["valid"], np.int32), _ptr(out["n_valid"], np.int32), _ptr(terms), w))
+
+    def laplace_eigs(self, n_ev, V, lam, tol=1e-10):
+        """Lowest n_ev Laplacian eigenpairs per timeslice into V [Lt][n_ev][L3][3], lam [Lt][n_ev]."""
+        it = ctypes.c_int()
+        self._check(_lib.lqcd_laplace_eigs(self.h, int(n_ev), _ptr(V), _ptr(lam, np.float64), _where(V, lam),
+                                           float(tol), ctypes.byref(it)))
+        return it.value
 
     def dslash_bench(self, prec, nrhs, n_iter=20, flush_l2=True):
         """(ms per launch, algorithmic bytes per launch) of the eo hopping + clover-inverse kernel."""
