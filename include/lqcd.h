@@ -111,7 +111,8 @@ void lqcd_default_params(lqcd_solve_params* p);
 int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream);
 int lqcd_destroy(lqcd_ctx* ctx);
 int lqcd_set_stream(lqcd_ctx* ctx, void* stream);
-/* Message of the last error on this context (or of the last failed lqcd_create if ctx is NULL). */
+/* Message of the last error on this context; with ctx = NULL, of the last failed call that takes
+ * no context (lqcd_create, lqcd_disc_correlator_noalloc). */
 const char* lqcd_last_error(const lqcd_ctx* ctx);
 
 /* Upload gauge links and set kappa, c_sw (Sec. 3: Wilson-clover).  Builds the clover term A and
@@ -193,6 +194,28 @@ int lqcd_laplace_eigs(lqcd_ctx* ctx, int n_ev, double* V, double* lambda, int wh
  * Fills the input with deterministic non-zero data.  Needs a gauge field.  Errors: INVALID_ARG. */
 int lqcd_dslash_bench(lqcd_ctx* ctx, int prec, int nrhs, int n_iter, int flush_l2, double* ms_per_launch,
                       double* algo_bytes_per_launch);
+
+/* lqcd_disc_correlator without any GPU memory allocation, for callers that cannot allocate:
+ * code being captured into a CUDA graph, hosts that reserve all device memory up front, or loops
+ * where an allocation would synchronise the device.  (The paper has no counterpart; this is an
+ * interface for such callers.)  Same results as lqcd_disc_correlator for the same inputs.
+ *   All array arguments are DEVICE pointers on the current device, owned by the caller, with
+ *   the layouts of lqcd_disc_correlator; T = Lt; dom_of_t: [T] int domain index of each
+ *   timeslice (the tiling of lqcd_set_domains); stream: cudaStream_t the work is queued on
+ *   (the call returns once it is queued).
+ *   Scratch: the differences L - Ld and Lt - Ltd needed for `terms` live in a fixed 2 MiB
+ *   device array compiled into the library (held on every GPU that loads the library until the
+ *   process exits), so n_cfg * n_gamma * T must not exceed 65536 when terms != NULL
+ *   (INVALID_ARG otherwise, with a message for lqcd_last_error(NULL)).  Every call shares that
+ *   array: calls whose GPU work overlaps (different streams, or threads) race on it; each call
+ *   writes all the scratch it reads, so nothing needs clearing between calls.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *   make that first call before any stream capture.
+ * Errors: INVALID_ARG (NULL, sizes, vev with n_cfg = 1, T > 256), CUDA. */
+int lqcd_disc_correlator_noalloc(const double* L, const double* Lt, const double* Ld, const double* Ltd, int n_cfg,
+                                 int n_gamma, int T, const int* dom_of_t, int vev, double* C, double* Cdd, double* dC,
+                                 double* C_avg, double* dC_avg, int* valid, int* n_valid, double* terms,
+                                 void* stream);
 
 /* Number of CUDA kernels this library has put on GPU queues in this process (all contexts):
  * direct launches plus the kernel nodes of every replayed CUDA graph.  For accounting only. */

@@ -30,6 +30,9 @@ int set_error(lqcd_ctx* c, int code, const std::string& msg) {
   return code;
 }
 
+// Message for lqcd_last_error(NULL): failures of calls that take no context.
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+
 void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes) {
   auto it = c->ws.find(name);
   if (it != c->ws.end() && it->second.second >= bytes) return it->second.first;

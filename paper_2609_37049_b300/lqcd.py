@@ -31,7 +31,7 @@ EXPORTED = [
     "lqcd_default_params", "lqcd_create", "lqcd_destroy", "lqcd_set_stream", "lqcd_last_error",
     "lqcd_gauge_upload", "lqcd_set_domains", "lqcd_dirac_apply", "lqcd_solve_full",
     "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
-    "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs",
+    "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
 ]
 
 
@@ -87,6 +87,8 @@ def load_library(path=_LIB_PATH):
         "lqcd_dslash_bench": (ip, [vp, ip, ip, ip, ip, dp, dp]),
         "lqcd_kernel_launches": (ctypes.c_longlong, []),
         "lqcd_laplace_eigs": (ip, [vp, ip, vp, vp, ip, ctypes.c_double, c_int_p]),
+        "lqcd_disc_correlator_noalloc": (ip, [vp, vp, vp, vp, ip, ip, ip, vp, ip, vp, vp, vp, vp, vp, vp, vp, vp,
+                                              vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
