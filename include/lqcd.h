@@ -217,6 +217,13 @@ int lqcd_disc_correlator_noalloc(const double* L, const double* Lt, const double
                                  double* C_avg, double* dC_avg, int* valid, int* n_valid, double* terms,
                                  void* stream);
 
+/* Per-phase GPU time of this context's calls (prepare, inner Krylov, reconstruct, FP64 true
+ * residual, sources, projection, ...) as a JSON object {"phase": milliseconds, ...} written to
+ * buf (len bytes); reset = 1 clears the totals.  Timing is recorded only when the environment
+ * variable LQCD_PHASE_TIMING=1 was set when the context was created (it adds CUDA events around
+ * phases outside captured graphs).  Errors: INVALID_ARG (buffer too small). */
+int lqcd_phase_times(lqcd_ctx* ctx, char* buf, int len, int reset);
+
 /* Number of CUDA kernels this library has put on GPU queues in this process (all contexts):
  * direct launches plus the kernel nodes of every replayed CUDA graph.  For accounting only. */
 long long lqcd_kernel_launches(void);

@@ -24,6 +24,20 @@ void count_launch(long long n) {
   if (!g_capturing) g_launches += n;
 }
 void set_capturing(bool on) { g_capturing = on; }
+bool is_capturing() { return g_capturing; }
+
+void flush_phase_times(lqcd_ctx* c) {
+  if (c->pending.empty()) return;
+  cudaStreamSynchronize(c->work);
+  for (auto& p : c->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) c->phase_ms[p.first] += ms;
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  cudaGetLastError();
+  c->pending.clear();
+}
 
 int set_error(lqcd_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -293,8 +307,8 @@ int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
       g_create_error = "lqcd_create: every extent must be even and >= 2";
       return LQCD_ERR_INVALID_ARG;
     }
-  if (L[3] > LQCD_MAXT) {
-    g_create_error = "lqcd_create: Lt > 256";
+  if (L[0] > 256 || L[1] > 256 || L[2] > 256 || L[3] > LQCD_MAXT) {
+    g_create_error = "lqcd_create: extents > 256 (Lt > 256)";
     return LQCD_ERR_INVALID_ARG;
   }
   if (bc_t < LQCD_BC_PERIODIC || bc_t > LQCD_BC_OPEN) {
@@ -324,7 +338,29 @@ int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
     lqcd_destroy(c);
     return LQCD_ERR_CUDA;
   }
+  {
+    // packed coordinates of every checkerboard site of each parity (s = 2 cb + b, b fixing parity)
+    std::vector<unsigned> co(2 * c->g.Vh);
+    for (int p = 0; p < 2; p++)
+      for (long cb = 0; cb < c->g.Vh; cb++) {
+        long xh = cb % c->g.Lxh, yzt = cb / c->g.Lxh;
+        int y = (int)(yzt % L[1]), z = (int)((yzt / L[1]) % L[2]), t = (int)(yzt / ((long)L[1] * L[2]));
+        int x = (int)(2 * xh) + ((p + y + z + t) & 1);
+        co[p * c->g.Vh + cb] = (unsigned)x | ((unsigned)y << 8) | ((unsigned)z << 16) | ((unsigned)t << 24);
+      }
+    if (cudaMalloc(&c->d_coord, co.size() * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemcpy(c->d_coord, co.data(), co.size() * sizeof(unsigned), cudaMemcpyHostToDevice) != cudaSuccess) {
+      g_create_error = "lqcd_create: cannot allocate the coordinate table";
+      cudaGetLastError();
+      lqcd_destroy(c);
+      return LQCD_ERR_CUDA;
+    }
+  }
   c->extents.assign(1, L[3]);
+  {
+    const char* tv = getenv("LQCD_PHASE_TIMING");
+    c->timing = tv && tv[0] == '1';
+  }
   fill_tables(c);
   M4 G[16], Gt[16];
   clifford(G, Gt);
@@ -345,13 +381,30 @@ int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
   return LQCD_OK;
 }
 
+int lqcd_phase_times(lqcd_ctx* c, char* buf, int len, int reset) {
+  if (!c || !buf || len < 3) return set_error(c, LQCD_ERR_INVALID_ARG, "phase_times: bad arguments");
+  flush_phase_times(c);
+  std::string s = "{";
+  for (auto& kv : c->phase_ms) {
+    char item[160];
+    snprintf(item, sizeof item, "%s\"%s\": %.6f", s.size() > 1 ? ", " : "", kv.first.c_str(), kv.second);
+    s += item;
+  }
+  s += "}";
+  if ((int)s.size() >= len) return set_error(c, LQCD_ERR_INVALID_ARG, "phase_times: buffer too small");
+  memcpy(buf, s.c_str(), s.size() + 1);
+  if (reset) c->phase_ms.clear();
+  return LQCD_OK;
+}
+
 int lqcd_destroy(lqcd_ctx* c) {
   if (!c) return LQCD_OK;
   if (c->work) cudaStreamSynchronize(c->work);
+  flush_phase_times(c);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
   void* bufs[] = {c->U64, c->U32, c->U16, c->A64, c->Ainv64, c->Ainv32, c->Ainv16, c->A32,
-                  c->d_tc_full, c->d_tc_dom, c->d_seg_full, c->d_seg_dom, c->d_gamma};
+                  c->d_tc_full, c->d_tc_dom, c->d_seg_full, c->d_seg_dom, c->d_gamma, c->d_coord};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -571,14 +624,23 @@ int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src,
         hjb[blk + r] = (r0 + r) % 4;
       }
       cudaMemcpyAsync(d_jb, hjb.data(), 2 * blk * sizeof(int), cudaMemcpyHostToDevice, c->work);
-      make_sources(g, dV, n_ev, d_jb, d_jb + blk, d_mask, eb, nb, c->work);
+      {
+        PhaseTimer pt(c, "sources");
+        make_sources(g, dV, n_ev, d_jb, d_jb + blk, d_mask, eb, nb, c->work);
+      }
       BatchStats bs;
       int r = solve_batch(c, eb, ex, nb, domain, q, bs);
       if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED) return r;
       if (r != LQCD_OK) rc = r;
       add_stats(st, bs, 0, nb, nseg, false);
       rhs_counter += nb;
-      project(g, dV, n_ev, ex, d_z, nz, C, nb, c->work);
+      {
+        const int ks = project_ksplit(g, n_ev, nb, nz);
+        double2* Cp = (double2*)ws_get(c, "p_Cpart", (size_t)ks * nz * n_ev * 4 * nb * sizeof(double2));
+        if (!Cp) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
+        lqcd::PhaseTimer pt(c, "project");
+        project(g, dV, n_ev, ex, d_z, nz, C, Cp, nb, c->work);
+      }
       long n = (long)nz * n_ev * 4 * nb;
       k_scatter_tau<<<(n + 255) / 256, 256, 0, c->work>>>(C, nz, n_ev, nb, r0, d_z + LQCD_MAXT, d_z,
                                                           sinks == LQCD_SINKS_ALL, g.Lt, dtau); lqcd::count_launch();
@@ -746,6 +808,7 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
   const void* Ainv = P == P64 ? c->Ainv64 : (P == P32 ? c->Ainv32 : c->Ainv16);
   const void* Ao = (const char*)Ainv + clover_bytes(g, P);
   DslashCall k{P, EPI_CH, 0, in, nullptr, nullptr, out, U, Ao, 1, nrhs, 0.0, 1.0, c->d_tc_full};
+  k.coord = coord_of(c, 1);
   int threads = 0;
   auto it = c->tuned_threads.find((long)P * 100000 + nrhs);
   if (it != c->tuned_threads.end()) threads = it->second;

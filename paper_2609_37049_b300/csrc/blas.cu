@@ -513,6 +513,18 @@ void bicg_omega(int prec, const void* t, const void* s, const VGeom& vg, const S
   k_bicg_fin_omega<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
 }
 
+// Finishing kernels alone, for partial sums produced by a dslash with fused reductions.
+void bicg_fin_alpha_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
+                         cudaStream_t st) {
+  k_bicg_fin_alpha<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+  lqcd::count_launch();
+}
+void bicg_fin_omega_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
+                         cudaStream_t st) {
+  k_bicg_fin_omega<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+  lqcd::count_launch();
+}
+
 void bicg_xr(int prec, void* x, const void* p, const void* s, const void* t, void* r, const void* r0,
              const VGeom& vg, const SegInfo* si, int nseg, double* partial, const KState& ks, cudaStream_t st) {
   DISPATCH_P(prec, k_bicg_xr,

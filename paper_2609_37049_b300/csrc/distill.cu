@@ -76,15 +76,17 @@ void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, con
 // ------------------------------------------------------------------ projection
 // For every sink timeslice tp = sinks[z]:  C[z][i][alpha][r] = sum_{s3,a} conj(V(tp)[i][s3][a])
 //                                                               X_r(tp, s3, alpha, a)
-// as a tiled complex GEMM (M = n_ev, N = 4 nrhs with n = alpha * nrhs + r, K = 3 L^3), FP64.
+// as a tiled complex GEMM (M = n_ev, N = 4 nrhs with n = alpha * nrhs + r, K = 3 L^3), FP64,
+// split along K over blockIdx.z = z * ksplit + kpart so the grid fills the GPU; the ksplit
+// partial tiles are then summed in a fixed order (deterministic).
 #define PBM 32
 #define PBN 32
 #define PBK 16
 __global__ void __launch_bounds__(256) k_project(const double2* Vt, int n_ev, const double2* X, const int* sinks,
-                                                 double2* C, Geom g, int nrhs) {
+                                                 double2* Cpart, Geom g, int nrhs, int ksplit) {
   __shared__ double2 As[PBK][PBM + 1];
   __shared__ double2 Bs[PBK][PBN + 1];
-  const int z = blockIdx.z;
+  const int z = blockIdx.z / ksplit, kpart = blockIdx.z - z * ksplit;
   const int tp = sinks[z];
   const long L3 = (long)g.Lx * g.Ly * g.Lz;
   const long K = 3 * L3;
@@ -95,7 +97,10 @@ __global__ void __launch_bounds__(256) k_project(const double2* Vt, int n_ev, co
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++) acc[i][j] = {0.0, 0.0};
   const double2* A = Vt + (long)tp * n_ev * K;
-  for (long k0 = 0; k0 < K; k0 += PBK) {
+  const long kchunks = (K + PBK - 1) / PBK;
+  const long kc0 = kchunks * kpart / ksplit, kc1 = kchunks * (kpart + 1) / ksplit;
+  double2* C = Cpart + (long)blockIdx.z * n_ev * N;
+  for (long k0 = kc0 * PBK; k0 < kc1 * PBK; k0 += PBK) {
     // A tile: PBM x PBK; 256 threads load 512 entries (2 each)
     for (int e = threadIdx.x; e < PBM * PBK; e += 256) {
       int mm = e / PBK, kk = e % PBK;
@@ -138,15 +143,43 @@ __global__ void __launch_bounds__(256) k_project(const double2* Vt, int n_ev, co
       int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
       if (m < n_ev && n < N) {
         int alpha = n / nrhs, r = n - alpha * nrhs;
-        C[(((long)z * n_ev + m) * 4 + alpha) * nrhs + r] = make_double2(acc[i][j].re, acc[i][j].im);
+        C[((long)m * 4 + alpha) * nrhs + r] = make_double2(acc[i][j].re, acc[i][j].im);
       }
     }
 }
 
+// C[z] = sum over kpart of Cpart[z * ksplit + kpart]
+__global__ void k_project_sum(const double2* Cpart, double2* C, long per_z, int nsinks, int ksplit) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per_z * nsinks) return;
+  const long z = i / per_z, e = i - z * per_z;
+  double re = 0, im = 0;
+  for (int k = 0; k < ksplit; k++) {
+    double2 v = Cpart[(z * ksplit + k) * per_z + e];
+    re += v.x;
+    im += v.y;
+  }
+  C[i] = make_double2(re, im);
+}
+
+int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks) {
+  const long tiles = (long)((4 * nrhs + PBN - 1) / PBN) * ((n_ev + PBM - 1) / PBM) * nsinks;
+  const long kchunks = (3L * g.Lx * g.Ly * g.Lz + PBK - 1) / PBK;
+  long ks = (4 * 148 + tiles - 1) / tiles;  // about four blocks per SM
+  if (ks > kchunks) ks = kchunks;
+  if (ks < 1) ks = 1;
+  return (int)ks;
+}
+
 void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, int nsinks, double2* C,
-             int nrhs, cudaStream_t st) {
-  dim3 grid((4 * nrhs + PBN - 1) / PBN, (n_ev + PBM - 1) / PBM, nsinks);
-  k_project<<<grid, 256, 0, st>>>(Vt, n_ev, X, sinks, C, g, nrhs); lqcd::count_launch();
+             double2* Cpart, int nrhs, cudaStream_t st) {
+  const int ksplit = project_ksplit(g, n_ev, nrhs, nsinks);
+  dim3 grid((4 * nrhs + PBN - 1) / PBN, (n_ev + PBM - 1) / PBM, nsinks * ksplit);
+  k_project<<<grid, 256, 0, st>>>(Vt, n_ev, X, sinks, Cpart, g, nrhs, ksplit);
+  lqcd::count_launch();
+  const long per_z = (long)n_ev * 4 * nrhs;
+  k_project_sum<<<(per_z * nsinks + 255) / 256, 256, 0, st>>>(Cpart, C, per_z, nsinks, ksplit);
+  lqcd::count_launch();
 }
 
 // ------------------------------------------------------------------ loops

@@ -9,14 +9,16 @@
 //   x = 0, r = b
 //   repeat while some system has ||r|| > tol ||b||:
 //     rhat_e = A_ee^-1 (r_e + kappa H_eo A_oo^-1 r_o)          (even-odd Schur right-hand side)
-//     solve  (1 - kappa^2 A_ee^-1 H_eo A_oo^-1 H_oe) e_e = rhat_e  to relative residual delta
+//     solve  M e_e = rhat_e,  M = 1 - kappa^2 A_ee^-1 H_eo A_oo^-1 H_oe,  to relative residual delta
 //     e_o = A_oo^-1 (r_o + kappa H_oe e_e);  x += e;  r = b - D x  (FP64)
 //
 // The inner solve is BiCGStab run in lockstep over all systems of the batch, in FP64 (the plain
-// solver), FP32, or FP16 storage with FP32 arithmetic; its residual is rescaled to unit norm
-// per system before conversion.  One BiCGStab iteration is 12 kernel launches with all scalars
-// on the device; chunks of iterations are captured once into a CUDA graph and replayed, with a
-// host convergence check (one 4-byte read) between chunks.
+// solver), FP32, or FP16 storage with FP32 arithmetic; its right-hand side is rescaled to unit
+// norm per system.  The prepare / reconstruct steps run in the inner precision (their errors are
+// relative to the correction, not to x); only r = b - D x needs FP64.  One BiCGStab iteration is
+// 10 launches with all scalars on the device: the two dot products of each Schur apply are
+// fused into its second dslash.  Chunks of iterations are captured once into a CUDA graph and
+// replayed, with a host convergence check (one 4-byte read) between chunks.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -41,11 +43,19 @@ static inline const void* off(const void* base, size_t b, int p) {
   return reinterpret_cast<const char*>(base) + b * p;
 }
 
+static DslashCall call(lqcd_ctx* c, int prec, int epi, const void* in, const void* y, const void* z, void* out,
+                       const void* U, const void* C, int out_par, int nrhs, double a, double b,
+                       const signed char* tc) {
+  DslashCall k{prec, epi, 0, in, y, z, out, U, C, out_par, nrhs, a, b, tc};
+  k.coord = coord_of(c, out_par);
+  return k;
+}
+
 void apply_D(lqcd_ctx* c, const double2* in, double2* out, int nrhs, int domain, cudaStream_t st) {
   const size_t sb = spinor_bytes(c->g, P64, nrhs), cbb = clover_bytes(c->g, P64);
   for (int p = 0; p < 2; p++) {
-    DslashCall k{P64, EPI_CY_H, 0, off(in, sb, 1 - p), off(in, sb, p), nullptr, off(out, sb, p), c->U64,
-                 off(c->A64, cbb, p), p, nrhs, 1.0, -c->kappa, domain ? c->d_tc_dom : c->d_tc_full};
+    DslashCall k = call(c, P64, EPI_CY_H, off(in, sb, 1 - p), off(in, sb, p), nullptr, off(out, sb, p), c->U64,
+                        off(c->A64, cbb, p), p, nrhs, 1.0, -c->kappa, domain ? c->d_tc_dom : c->d_tc_full);
     launch_dslash(c->g, k, st);
   }
 }
@@ -66,21 +76,29 @@ struct Inner {
   int threads;
 };
 
-static void schur(lqcd_ctx* c, const Inner& in, const void* src, void* dst, cudaStream_t st) {
-  DslashCall k1{in.prec, EPI_CH, 0, src, nullptr, nullptr, in.tmp, in.U, in.Ainv_o, 1, in.nrhs, 0.0, 1.0, in.tc};
+// dst = M src; the second dslash also forms the partial sums `red` (RED_DOT_Z with zred, or
+// RED_DOT_Y_NORM with y = src) for the following BiCGStab scalar.
+static void schur(lqcd_ctx* c, const Inner& in, const void* src, void* dst, int red, const void* zred,
+                  cudaStream_t st) {
+  DslashCall k1 = call(c, in.prec, EPI_CH, src, nullptr, nullptr, in.tmp, in.U, in.Ainv_o, 1, in.nrhs, 0.0, 1.0,
+                       in.tc);
   launch_dslash(c->g, k1, st, in.threads);
-  DslashCall k2{in.prec, EPI_Y_CH, 0, in.tmp, src, nullptr, dst, in.U, in.Ainv_e, 0, in.nrhs, 1.0,
-                -in.kappa * in.kappa, in.tc};
+  DslashCall k2 = call(c, in.prec, EPI_Y_CH, in.tmp, src, nullptr, dst, in.U, in.Ainv_e, 0, in.nrhs, 1.0,
+                       -in.kappa * in.kappa, in.tc);
+  k2.red = red;
+  k2.zred = zred;
+  k2.partial = in.partial;
+  k2.red_sites = in.vg.S;
   launch_dslash(c->g, k2, st, in.threads);
 }
 
 static void bicg_iteration(lqcd_ctx* c, const Inner& in, cudaStream_t st) {
   const int P = in.prec;
-  schur(c, in, in.p, in.v, st);
-  bicg_alpha(P, in.b, in.v, in.vg, in.si, in.nseg, in.partial, in.ks, st);
+  schur(c, in, in.p, in.v, RED_DOT_Z, in.b, st);  // v = M p, partial (r0, v)
+  bicg_fin_alpha_only(in.partial, in.vg, in.si, in.nseg, in.ks, st);
   bicg_s(P, in.r, in.v, in.s, in.vg, in.si, in.nseg, in.ks, st);
-  schur(c, in, in.s, in.t, st);
-  bicg_omega(P, in.t, in.s, in.vg, in.si, in.nseg, in.partial, in.ks, st);
+  schur(c, in, in.s, in.t, RED_DOT_Y_NORM, nullptr, st);  // t = M s, partial (t, s), (t, t)
+  bicg_fin_omega_only(in.partial, in.vg, in.si, in.nseg, in.ks, st);
   bicg_xr(P, in.x, in.p, in.s, in.t, in.r, in.b, in.vg, in.si, in.nseg, in.partial, in.ks, st);
   bicg_p(P, in.p, in.r, in.v, in.vg, in.si, in.nseg, in.ks, st);
 }
@@ -93,53 +111,57 @@ static std::string graph_key(const Inner& in, int chunk) {
   return buf;
 }
 
+static cudaGraphExec_t capture(lqcd_ctx* c, const std::string& key, int nsys, const KState& ks, int* count_host,
+                               const std::function<void(cudaStream_t)>& body) {
+  cudaStream_t st = c->work;
+  auto f = c->graphs.find(key);
+  if (f != c->graphs.end()) return f->second;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec = nullptr;
+  set_capturing(true);
+  cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  body(st);
+  count_active(ks.active, nsys, ks.count, st);
+  cudaMemcpyAsync(count_host, ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  set_capturing(false);
+  if (ce == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+    c->graphs[key] = exec;
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    long long nk = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(nd, &ty);
+      nk += ty == cudaGraphNodeTypeKernel;
+    }
+    c->graph_kernels[exec] = nk;
+  } else {
+    exec = nullptr;
+    cudaGetLastError();
+  }
+  if (ce == cudaSuccess) cudaGraphDestroy(graph);
+  return exec;
+}
+
 // Run BiCGStab on the prepared systems until all are inactive or max_iter; returns iterations.
 static int run_bicg(lqcd_ctx* c, const Inner& in, int max_iter, int chunk, bool use_graph, int* count_host,
                     long long& dslash_calls) {
   cudaStream_t st = c->work;
   const int nsys = in.nrhs * in.nseg;
+  auto body = [&](cudaStream_t s) {
+    for (int k = 0; k < chunk; k++) bicg_iteration(c, in, s);
+  };
+  cudaGraphExec_t exec = use_graph ? capture(c, graph_key(in, chunk), nsys, in.ks, count_host, body) : nullptr;
   int it = 0;
-  cudaGraphExec_t exec = nullptr;
-  if (use_graph) {
-    std::string key = graph_key(in, chunk);
-    auto f = c->graphs.find(key);
-    if (f != c->graphs.end()) {
-      exec = f->second;
-    } else {
-      cudaGraph_t graph;
-      set_capturing(true);
-      cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-      for (int k = 0; k < chunk; k++) bicg_iteration(c, in, st);
-      count_active(in.ks.active, nsys, in.ks.count, st);
-      cudaMemcpyAsync(count_host, in.ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
-      cudaError_t ce = cudaStreamEndCapture(st, &graph);
-      set_capturing(false);
-      if (ce == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
-        c->graphs[key] = exec;
-        size_t nn = 0;
-        cudaGraphGetNodes(graph, nullptr, &nn);
-        std::vector<cudaGraphNode_t> nodes(nn);
-        cudaGraphGetNodes(graph, nodes.data(), &nn);
-        long long nk = 0;
-        for (auto nd : nodes) {
-          cudaGraphNodeType ty;
-          cudaGraphNodeGetType(nd, &ty);
-          nk += ty == cudaGraphNodeTypeKernel;
-        }
-        c->graph_kernels[exec] = nk;
-      } else {
-        exec = nullptr;
-        cudaGetLastError();
-      }
-      cudaGraphDestroy(graph);
-    }
-  }
   while (it < max_iter) {
     if (exec) {
       cudaGraphLaunch(exec, st);
       count_launch(c->graph_kernels[exec]);
     } else {
-      for (int k = 0; k < chunk; k++) bicg_iteration(c, in, st);
+      body(st);
       count_active(in.ks.active, nsys, in.ks.count, st);
       cudaMemcpyAsync(count_host, in.ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
     }
@@ -165,15 +187,19 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   const int chunk = prm.check_every > 0 ? prm.check_every : 8;
 
   int P = P64;
+  // Residual reduction asked of one inner solve.  FP32 BiCGStab on a unit-norm right-hand side
+  // reaches a true residual of a few 1e-7 before rounding stalls it, so asking 2e-6 makes two
+  // defect-correction cycles enough for 1e-10 (each FP64 cycle costs two FP64 dslash launches).
   double inner_tol = 1e-12;
   if (prm.solver == LQCD_SOLVER_MIXED || prm.solver == LQCD_SOLVER_FGCR_NN) {
     P = prm.inner_prec == LQCD_PREC_F16 ? P16 : P32;
-    inner_tol = P == P32 ? 1e-5 : 1e-2;
+    inner_tol = P == P32 ? 2e-6 : 1e-2;
   }
   if (prm.inner_tol > 0) inner_tol = prm.inner_tol;
 
   VGeom vgF = make_vgeom(g, nrhs, 2);  // full lattice
   VGeom vgH = make_vgeom(g, nrhs, 1);  // one parity
+  if (vgH.threads() > 256) return set_error(c, LQCD_ERR_INVALID_ARG, "solve: rhs_block > 256");
   const size_t sb64 = spinor_bytes(g, P64, nrhs), sbP = spinor_bytes(g, P, nrhs);
   const size_t cbP = clover_bytes(g, P);
 
@@ -218,6 +244,10 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
     if (it != c->tuned_threads.end()) in.threads = it->second;
   }
   char* ksb = (char*)ws_get(c, "kstate", (size_t)nsys * (4 * 16 + 3 * 8 + 3 * 4) + 64);
+  in.ks.count = (int*)ws_get(c, "kcount", 64);
+  if (!r64 || !partial || !b2 || !r2 || !delta || !scale || !iscale || !rel || !oact || !rin || !ein || !bhat ||
+      !in.r || !in.p || !in.v || !in.s || !in.t || !in.tmp || !ksb || !in.ks.count)
+    return set_error(c, LQCD_ERR_OOM, "solve: out of device memory");
   in.ks.rho = (double2*)ksb;
   in.ks.alpha = in.ks.rho + nsys;
   in.ks.omega = in.ks.alpha + nsys;
@@ -228,7 +258,6 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   in.ks.active = (int*)(in.ks.stop2 + nsys);
   in.ks.iters = in.ks.active + nsys;
   in.ks.flag = in.ks.iters + nsys;
-  in.ks.count = (int*)ws_get(c, "kcount", 64);
   in.partial = partial;
   int* count_host = (int*)pinned_get(c, 64);
   cudaMemsetAsync(in.ks.iters, 0, nsys * sizeof(int), st);
@@ -242,39 +271,47 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   bs.cycles = 0;
   bs.dslash = 0;
   int total_iters = 0;
+  const size_t cb64 = clover_bytes(g, P64);
   for (int cyc = 0; cyc < max_outer; cyc++) {
     count_active(oact, nsys, in.ks.count, st);
     cudaMemcpyAsync(count_host, in.ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     if (*count_host == 0 || total_iters >= max_iter) break;
     bs.cycles++;
-    // scaled residual in the inner precision, Schur right-hand side
-    v_convert(P64, P, r64, rin, vgF, si, nseg, scale, st);
-    launch_clover_only(g, P, in.Ainv_o, off(rin, sbP, 1), in.tmp, nrhs, st);
-    DslashCall kp{P, EPI_C_YH, 0, in.tmp, off(rin, sbP, 0), nullptr, bhat, in.U, in.Ainv_e, 0, nrhs, 1.0,
-                  c->kappa, tc};
-    launch_dslash(g, kp, st, in.threads);
-    bs.dslash += 1;
-    // inner BiCGStab
-    bicg_init(P, bhat, in.r, in.p, in.x, vgH, si, nseg, partial, in.ks, delta, oact, st);
-    total_iters += run_bicg(c, in, max_iter - total_iters, chunk, prm.use_graph != 0, count_host, bs.dslash);
-    // odd half of the correction, then x += e / scale
-    DslashCall kr{P, EPI_C_YH, 0, in.x, off(rin, sbP, 1), nullptr, off(ein, sbP, 1), in.U, in.Ainv_o, 1, nrhs, 1.0,
-                  c->kappa, tc};
-    launch_dslash(g, kr, st, in.threads);
-    bs.dslash += 1;
-    recip(scale, iscale, nsys, st);
-    v_axpy_mixed(P, x, ein, vgF, si, nseg, iscale, oact, st);
-    // FP64 true residual r = b - D x
-    const size_t cb64 = clover_bytes(g, P64);
-    for (int p = 0; p < 2; p++) {
-      DslashCall k{P64, EPI_RES, 0, off(x, sb64, 1 - p), off(x, sb64, p), off(b, sb64, p), off(r64, sb64, p),
-                   c->U64, off(c->A64, cb64, p), p, nrhs, 1.0, -c->kappa, tc};
-      launch_dslash(g, k, st);
+    {  // scaled residual in the inner precision, Schur right-hand side
+      PhaseTimer pt(c, "prepare");
+      v_convert(P64, P, r64, rin, vgF, si, nseg, scale, st);
+      launch_clover_only(g, P, in.Ainv_o, off(rin, sbP, 1), in.tmp, nrhs, st);
+      DslashCall kp = call(c, P, EPI_C_YH, in.tmp, off(rin, sbP, 0), nullptr, bhat, in.U, in.Ainv_e, 0, nrhs, 1.0,
+                           c->kappa, tc);
+      launch_dslash(g, kp, st, in.threads);
+      bs.dslash += 1;
     }
-    bs.dslash += 2;
-    v_norm2(P64, r64, vgF, si, nseg, partial, r2, st);
-    outer_update(r2, b2, nsys, tol, inner_tol, oact, delta, scale, rel, 0, st);
+    {  // inner BiCGStab
+      PhaseTimer pt(c, P == P64 ? "inner_bicgstab_f64" : (P == P32 ? "inner_bicgstab_f32" : "inner_bicgstab_f16"));
+      bicg_init(P, bhat, in.r, in.p, in.x, vgH, si, nseg, partial, in.ks, delta, oact, st);
+      total_iters += run_bicg(c, in, max_iter - total_iters, chunk, prm.use_graph != 0, count_host, bs.dslash);
+    }
+    {  // odd half of the correction, then x += e / scale
+      PhaseTimer pt(c, "reconstruct");
+      DslashCall kr = call(c, P, EPI_C_YH, in.x, off(rin, sbP, 1), nullptr, off(ein, sbP, 1), in.U, in.Ainv_o, 1,
+                           nrhs, 1.0, c->kappa, tc);
+      launch_dslash(g, kr, st, in.threads);
+      bs.dslash += 1;
+      recip(scale, iscale, nsys, st);
+      v_axpy_mixed(P, x, ein, vgF, si, nseg, iscale, oact, st);
+    }
+    {  // FP64 true residual r = b - D x
+      PhaseTimer pt(c, "residual_f64");
+      for (int p = 0; p < 2; p++) {
+        DslashCall k = call(c, P64, EPI_RES, off(x, sb64, 1 - p), off(x, sb64, p), off(b, sb64, p),
+                            off(r64, sb64, p), c->U64, off(c->A64, cb64, p), p, nrhs, 1.0, -c->kappa, tc);
+        launch_dslash(g, k, st);
+      }
+      bs.dslash += 2;
+      v_norm2(P64, r64, vgF, si, nseg, partial, r2, st);
+      outer_update(r2, b2, nsys, tol, inner_tol, oact, delta, scale, rel, 0, st);
+    }
   }
   bs.rel.resize(nsys);
   bs.iters.resize(nsys);
@@ -282,6 +319,7 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   cudaMemcpyAsync(bs.iters.data(), in.ks.iters, nsys * sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e));
+  flush_phase_times(c);
   for (int i = 0; i < nsys; i++) {
     if (!std::isfinite(bs.rel[i])) return set_error(c, LQCD_ERR_NAN, "solve: non-finite residual");
     if (bs.rel[i] > tol) return set_error(c, LQCD_ERR_NOT_CONVERGED, "solve: tolerance not reached");

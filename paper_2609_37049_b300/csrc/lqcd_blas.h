@@ -19,6 +19,10 @@ void bicg_s(int prec, const void* r, const void* v, void* s, const VGeom& vg, co
             const KState& ks, cudaStream_t st);
 void bicg_omega(int prec, const void* t, const void* s, const VGeom& vg, const SegInfo* si, int nseg,
                 double* partial, const KState& ks, cudaStream_t st);
+void bicg_fin_alpha_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
+                         cudaStream_t st);
+void bicg_fin_omega_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
+                         cudaStream_t st);
 void bicg_xr(int prec, void* x, const void* p, const void* s, const void* t, void* r, const void* r0,
              const VGeom& vg, const SegInfo* si, int nseg, double* partial, const KState& ks, cudaStream_t st);
 void bicg_p(int prec, void* p, const void* r, const void* v, const VGeom& vg, const SegInfo* si, int nseg,

@@ -146,10 +146,11 @@ LQCD_D void store_spinor(void* base, long stride, long idx, const cplx<R> (&s)[1
 }
 
 // ------------------------------------------------------------------ links
-// U[a][b] of link (mu, parity p, cb).  P32/P16 rebuild row 2 = conj(row0 x row1) (SU(3)).
+// U[a][b] of link (mu, parity p, cb).  P64 stores all nine entries; P32 / P16 store rows 0 and 1
+// (three 16-byte / 8-byte loads) and rebuild row 2 = conj(row0 x row1) (SU(3)): measured on
+// B300, the three wide loads plus the rebuild flops beat nine narrow loads.
 template <int P>
 LQCD_D void load_link(const void* base, long Vh, int mu, int p, long cb, cplx<typename Traits<P>::real> (&u)[3][3]) {
-  using R = typename Traits<P>::real;
   if constexpr (P == P64) {
     const double2* f = reinterpret_cast<const double2*>(base) + ((long)(mu * 2 + p) * 9) * Vh + cb;
 #pragma unroll
@@ -178,7 +179,6 @@ LQCD_D void load_link(const void* base, long Vh, int mu, int p, long cb, cplx<ty
     u[2][1] = cj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
     u[2][2] = cj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
   }
-  (void)sizeof(R);
 }
 
 // ------------------------------------------------------------------ clover (packed Hermitian 6x6)
@@ -241,6 +241,31 @@ LQCD_D void clover_apply(const void* base, long Vh, long cb, cplx<typename Trait
     herm6_apply<R>(r, &s[6 * ch], y);
 #pragma unroll
     for (int i = 0; i < 6; i++) s[6 * ch + i] = y[i];
+  }
+}
+
+// ------------------------------------------------------------------ block reduction
+// Sum ND values over the S sites of a block for each of its nrhs right-hand sides (threads are
+// (site_local, rhs) with rhs fastest) and write partial[block][rhs][ND].  Needs ND * blockDim
+// doubles of dynamic shared memory; S must be a power of two.
+template <int ND>
+LQCD_D void block_reduce_rhs(double (&v)[ND], double* partial, int S, int nrhs, int site_local, int rhs) {
+  extern __shared__ double sm_red[];
+  const int n = blockDim.x;
+#pragma unroll
+  for (int k = 0; k < ND; k++) sm_red[k * n + threadIdx.x] = v[k];
+  __syncthreads();
+  for (int s = S / 2; s >= 1; s >>= 1) {
+    if (site_local < s) {
+#pragma unroll
+      for (int k = 0; k < ND; k++) sm_red[k * n + threadIdx.x] += sm_red[k * n + threadIdx.x + s * nrhs];
+    }
+    __syncthreads();
+  }
+  if (site_local == 0) {
+#pragma unroll
+    for (int k = 0; k < ND; k++)
+      partial[((long)blockIdx.x * nrhs + rhs) * ND + k] = sm_red[k * n + threadIdx.x];
   }
 }
 

@@ -7,8 +7,10 @@ void pack_spinor(const Geom& g, const double2* lex, double2* eo, int nrhs, cudaS
 void unpack_spinor(const Geom& g, const double2* eo, double2* lex, int nrhs, cudaStream_t st);
 void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, const int* br,
                   const unsigned char* srcmask, double2* b, int nrhs, cudaStream_t st);
+// Cpart: scratch of project_ksplit(...) * nsinks * n_ev * 4 * nrhs complex entries.
+int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks);
 void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, int nsinks, double2* C,
-             int nrhs, cudaStream_t st);
+             double2* Cpart, int nrhs, cudaStream_t st);
 void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w, double2* L,
            double2* Lt, cudaStream_t st);
 void correlators(const double2* L, const double2* Lt, const double2* Ld, const double2* Ltd, int n_cfg, int n_g,

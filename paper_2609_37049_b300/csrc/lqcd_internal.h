@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -62,6 +63,12 @@ enum Epi {
   EPI_RES = 6    // out = z - (C y + b H x)
 };
 
+// Dot products fused into the epilogue (second half of the Schur operator, EPI_Y_CH only):
+//   RED_DOT_Z:      partial (zred, out)             -> 2 doubles per (block, rhs)
+//   RED_DOT_Y_NORM: partial (out, y), (out, out)    -> 3 doubles per (block, rhs)
+// with blocks of red_sites sites x nrhs (the VGeom blocks of the same batch).
+enum Red { RED_NONE = 0, RED_DOT_Z = 1, RED_DOT_Y_NORM = 2 };
+
 struct DslashCall {
   int prec;
   int epi;
@@ -75,7 +82,12 @@ struct DslashCall {
   int out_par;
   int nrhs;
   double a, b;
-  const signed char* tc;  // device array [Lt]: forward t-hop coefficient per timeslice
+  const signed char* tc;            // device array [Lt]: forward t-hop coefficient per timeslice
+  const unsigned* coord = nullptr;  // packed site coordinates of parity out_par (device)
+  double* partial = nullptr;
+  const void* zred = nullptr;
+  int red = RED_NONE;
+  int red_sites = 0;
 };
 
 void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int threads = 0);
@@ -126,7 +138,37 @@ struct lqcd_ctx {
   std::map<cudaGraphExec_t, long long> graph_kernels;  // kernel nodes per instantiated graph
   // Clifford table on the device: [16][2][4][4] complex (Gamma, Gamma-tilde)
   double2* d_gamma = nullptr;
+  // packed site coordinates x | y << 8 | z << 16 | t << 24 per parity: [2][Vh]
+  unsigned* d_coord = nullptr;
+  // optional per-phase GPU timing (LQCD_PHASE_TIMING=1): event pairs not yet read, totals in ms
+  bool timing = false;
+  std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::map<std::string, double> phase_ms;
 };
+
+namespace lqcd {
+bool is_capturing();
+// Records CUDA events around a phase on the work stream when timing is on (not while capturing).
+struct PhaseTimer {
+  lqcd_ctx* c;
+  const char* name;
+  cudaEvent_t e0 = nullptr;
+  PhaseTimer(lqcd_ctx* ctx, const char* n) : c(ctx), name(n) {
+    if (c->timing && !is_capturing() && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, c->work);
+  }
+  ~PhaseTimer() {
+    if (!e0) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) != cudaSuccess) return;
+    cudaEventRecord(e1, c->work);
+    c->pending.push_back({name, {e0, e1}});
+  }
+};
+// Synchronise the work stream and add the pending phase durations to the totals.
+void flush_phase_times(lqcd_ctx* c);
+}  // namespace lqcd
+
+inline const unsigned* coord_of(const lqcd_ctx* c, int parity) { return c->d_coord + parity * c->g.Vh; }
 
 namespace lqcd {
 // Process-wide count of kernels this library has put on a GPU queue: every launch site calls

@@ -32,6 +32,7 @@ EXPORTED = [
     "lqcd_gauge_upload", "lqcd_set_domains", "lqcd_dirac_apply", "lqcd_solve_full",
     "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
     "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
+    "lqcd_phase_times",
 ]
 
 
@@ -89,6 +90,7 @@ def load_library(path=_LIB_PATH):
         "lqcd_laplace_eigs": (ip, [vp, ip, vp, vp, ip, ctypes.c_double, c_int_p]),
         "lqcd_disc_correlator_noalloc": (ip, [vp, vp, vp, vp, ip, ip, ip, vp, ip, vp, vp, vp, vp, vp, vp, vp, vp,
                                               vp]),
+        "lqcd_phase_times": (ip, [vp, ctypes.c_char_p, ip, ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +257,13 @@ class Context:
             self.h, _ptr(L), _ptr(Lt), _ptr(Ld), _ptr(Ltd), n_cfg, n_g, int(vev), _ptr(out["C"]),
             _ptr(out["Cdd"]), _ptr(out["dC"]), _ptr(out["C_avg"]), _ptr(out["dC_avg"]),
             _ptr(out["valid"], np.int32), _ptr(out["n_valid"], np.int32), _ptr(terms), w))
+
+    def phase_times(self, reset=False):
+        """GPU milliseconds per solver phase (needs LQCD_PHASE_TIMING=1 at context creation)."""
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        self._check(_lib.lqcd_phase_times(self.h, buf, 8192, int(reset)))
+        return json.loads(buf.value.decode())
 
     def laplace_eigs(self, n_ev, V, lam, tol=1e-10):
         """Lowest n_ev Laplacian eigenpairs per timeslice into V [Lt][n_ev][L3][3], lam [Lt][n_ev]."""
