@@ -85,7 +85,8 @@ typedef struct {
   int max_outer;     /* cap on defect-correction cycles; 0 -> 20 */
   int check_every;   /* Krylov iterations between host convergence checks; 0 -> 8 */
   int gcr_nkrylov;   /* flexible GCR restart length; 0 -> 8 */
-  int precond_iters; /* FP16 preconditioner sweeps per application; 0 -> 6 */
+  int precond_iters; /* FP16 MR preconditioner sweeps per application; 0 -> 6; < 0: no preconditioner
+                        (plain FP32 GCR inside the defect correction, for comparisons) */
 } lqcd_solve_params;
 
 typedef struct {
@@ -216,6 +217,33 @@ int lqcd_disc_correlator_noalloc(const double* L, const double* Lt, const double
                                  int n_gamma, int T, const int* dom_of_t, int vev, double* C, double* Cdd, double* dC,
                                  double* C_avg, double* dC_avg, int* valid, int* n_valid, double* terms,
                                  void* stream);
+
+/* ---- Learned preconditioner (not in the paper: an accelerator of the solves of Sec. 4, whose
+ * results it cannot change because the FP64 true residual still decides convergence).
+ * A gauge-covariant network of four linear parallel-transport layers, channel widths
+ * 4 -> 8 -> 8 -> 8 -> 4 (colour-vector channels; the four spin components of a spinor in and out):
+ *   out_o(x) = sum_{p=0..8} sum_c W[p][o][c] (T_p h_c)(x),  T_0 = 1,
+ *   T_{1+mu} h(x) = U_mu(x) h(x+mu),  T_{5+mu} h(x) = U_mu(x-mu)^dag h(x-mu),
+ * on the fermion links (boundary phase; Dirichlet cuts when domain = 1).  Weights: complex, stored
+ * per layer as [9][C_out][C_in], layers one after the other, as (re, im) float pairs; inference
+ * reads a BF16 copy and accumulates in FP32, training updates FP32 master weights with Adam.
+ * Fields for lqcd_nn_apply / lqcd_nn_loss_grad: [n][V][4][3] complex64 (FP32 re, im), full lattice. */
+int lqcd_nn_num_weights(void); /* number of complex weights */
+int lqcd_nn_set_weights(lqcd_ctx* ctx, const float* w);  /* host, 2 * lqcd_nn_num_weights() floats */
+int lqcd_nn_get_weights(lqcd_ctx* ctx, float* w);
+/* out = network(in) with the FP32 master weights. */
+int lqcd_nn_apply(lqcd_ctx* ctx, const float* in, float* out, int nsamp, int domain, int where);
+/* Loss sum |N(in) - target|^2 / sum |target|^2 over all sites (even_only = 1: even sites) and its
+ * gradient dL/dconj(W) (host, 2 * lqcd_nn_num_weights() floats; may be NULL). */
+int lqcd_nn_loss_grad(lqcd_ctx* ctx, const float* in, const float* target, int nsamp, int domain, int even_only,
+                      int where, double* loss, float* grad);
+/* Train on n_pairs (r, e) pairs of the even-odd Schur system M e = r generated by the plain FP64
+ * solver from random r (seeded): `epochs` passes of Adam (learning rate lr) over batches of `batch`
+ * pairs, loss over even sites; loss_hist[epochs] (may be NULL) receives the mean loss per epoch.
+ * Starts from the weights set before (lqcd_nn_set_weights).  Afterwards LQCD_SOLVER_FGCR_NN uses
+ * the network.  Errors: STATE (no weights or no gauge field), OOM. */
+int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, int domain, unsigned seed,
+                  double* loss_hist);
 
 /* Per-phase GPU time of this context's calls (prepare, inner Krylov, reconstruct, FP64 true
  * residual, sources, projection, ...) as a JSON object {"phase": milliseconds, ...} written to

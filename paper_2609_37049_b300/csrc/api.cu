@@ -404,7 +404,8 @@ int lqcd_destroy(lqcd_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
   void* bufs[] = {c->U64, c->U32, c->U16, c->A64, c->Ainv64, c->Ainv32, c->Ainv16, c->A32,
-                  c->d_tc_full, c->d_tc_dom, c->d_seg_full, c->d_seg_dom, c->d_gamma, c->d_coord};
+                  c->d_tc_full, c->d_tc_dom, c->d_seg_full, c->d_seg_dom, c->d_gamma, c->d_coord,
+                  c->nn_weights, c->nn_w16, c->nn_m, c->nn_v};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -733,6 +734,56 @@ int lqcd_disc_correlator(lqcd_ctx* c, const double* L, const double* Lt, const d
 }
 
 }  // extern "C"
+
+extern "C" int lqcd_nn_num_weights(void) { return nn_total_weights(); }
+
+extern "C" int lqcd_nn_set_weights(lqcd_ctx* c, const float* w) {
+  if (!c || !w) return set_error(c, LQCD_ERR_INVALID_ARG, "nn_set_weights: NULL");
+  Scope sc(c);
+  return nn_set_weights(c, w);
+}
+
+extern "C" int lqcd_nn_get_weights(lqcd_ctx* c, float* w) {
+  if (!c || !w) return set_error(c, LQCD_ERR_INVALID_ARG, "nn_get_weights: NULL");
+  Scope sc(c);
+  return nn_get_weights(c, w);
+}
+
+extern "C" int lqcd_nn_apply(lqcd_ctx* c, const float* in, float* out, int nsamp, int domain, int where) {
+  if (!c || !in || !out || nsamp < 1) return set_error(c, LQCD_ERR_INVALID_ARG, "nn_apply: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "nn_apply: no gauge field uploaded");
+  Scope sc(c);
+  const size_t bytes = (size_t)c->V * 12 * nsamp * sizeof(float2);
+  const float2* di = (const float2*)stage_in(c, in, bytes, where, "nn_in");
+  float2* dout = (float2*)stage_out(c, out, bytes, where, "nn_out");
+  if (!di || !dout) return set_error(c, LQCD_ERR_OOM, "nn_apply: OOM");
+  if (int rc = nn_apply_lex(c, di, dout, nsamp, domain)) return rc;
+  if (int e = cuda_check(c, "nn_apply")) return e;
+  return finish_out(c, out, dout, bytes, where);
+}
+
+extern "C" int lqcd_nn_loss_grad(lqcd_ctx* c, const float* in, const float* target, int nsamp, int domain,
+                                 int even_only, int where, double* loss, float* grad) {
+  if (!c || !in || !target || !loss || nsamp < 1)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "nn_loss_grad: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "nn_loss_grad: no gauge field uploaded");
+  Scope sc(c);
+  const size_t bytes = (size_t)c->V * 12 * nsamp * sizeof(float2);
+  const float2* di = (const float2*)stage_in(c, in, bytes, where, "nn_in");
+  const float2* dt = (const float2*)stage_in(c, target, bytes, where, "nn_tgt");
+  if (!di || !dt) return set_error(c, LQCD_ERR_OOM, "nn_loss_grad: OOM");
+  return nn_loss_grad_lex(c, di, dt, nsamp, domain, even_only, loss, grad);
+}
+
+extern "C" int lqcd_nn_train(lqcd_ctx* c, int n_pairs, int epochs, int batch, double lr, int domain, unsigned seed,
+                             double* loss_hist) {
+  if (!c || n_pairs < 1 || epochs < 1 || batch < 1 || !(lr > 0))
+    return set_error(c, LQCD_ERR_INVALID_ARG, "nn_train: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "nn_train: no gauge field uploaded");
+  if (!c->nn_weights) return set_error(c, LQCD_ERR_STATE, "nn_train: set initial weights first");
+  Scope sc(c);
+  return nn_train(c, n_pairs, epochs, batch, lr, domain, seed, loss_hist);
+}
 
 extern "C" int lqcd_laplace_eigs(lqcd_ctx* c, int n_ev, double* V, double* lambda, int where, double tol,
                                  int* iters) {

@@ -60,22 +60,6 @@ void apply_D(lqcd_ctx* c, const double2* in, double2* out, int nrhs, int domain,
   }
 }
 
-struct Inner {
-  int prec, nrhs, nseg;
-  VGeom vg;
-  const SegInfo* si;
-  const signed char* tc;
-  const void* U;
-  const void* Ainv_e;
-  const void* Ainv_o;
-  const void* b;  // prepared right-hand side; also the BiCGStab shadow residual r0
-  void *x, *r, *p, *v, *s, *t, *tmp;
-  KState ks;
-  double* partial;
-  double kappa;
-  int threads;
-};
-
 // dst = M src; the second dslash also forms the partial sums `red` (RED_DOT_Z with zred, or
 // RED_DOT_Y_NORM with y = src) for the following BiCGStab scalar.
 static void schur(lqcd_ctx* c, const Inner& in, const void* src, void* dst, int red, const void* zred,
@@ -173,6 +157,83 @@ static int run_bicg(lqcd_ctx* c, const Inner& in, int max_iter, int chunk, bool 
   return it;
 }
 
+// ------------------------------------------------------------------ flexible GCR
+enum { PREC_NONE = 0, PREC_MR16 = 1, PREC_NN = 2 };
+
+struct Fgcr {
+  int m;          // restart length
+  VecList Z, W;   // FP32 search directions and their images
+  void* x;        // FP32 solution (even half of the correction field)
+  void* r;        // FP32 residual
+  GState gs;
+  int kind;       // PREC_*
+  int n_mr;       // MR sweeps of the FP16 preconditioner
+  Inner in16;     // FP16 Schur operator (U16, Ainv16) and its work vectors
+  void *e16, *r16, *p16;
+  double2* omega16;
+};
+
+// z = K r
+static void precondition(lqcd_ctx* c, const Inner& in, const Fgcr& f, void* z, cudaStream_t st) {
+  if (f.kind == PREC_MR16) {
+    const Inner& h = f.in16;
+    v_convert(P32, P16, f.r, f.r16, in.vg, in.si, in.nseg, f.gs.pscale, st);
+    v_zero(P16, f.e16, in.vg, st);
+    for (int i = 0; i < f.n_mr; i++) {
+      schur(c, h, f.r16, f.p16, RED_DOT_Y_NORM, nullptr, st);  // p = M r, partial (p, r), (p, p)
+      mr_finish(h.partial, in.vg, in.si, in.nseg, f.omega16, f.gs.active, st);
+      mr_update(P16, f.e16, f.r16, f.p16, in.vg, in.si, in.nseg, f.omega16, f.gs.active, st);
+    }
+    v_convert(P16, P32, f.e16, z, in.vg, in.si, in.nseg, f.gs.ipscale, st);
+  } else if (f.kind == PREC_NN) {
+    nn_precondition(c, in, f.r, z, f.gs.pscale, f.gs.ipscale, st);
+  } else {
+    v_copy(P32, f.r, z, in.vg, st);
+  }
+}
+
+static void fgcr_cycle(lqcd_ctx* c, const Inner& in, const Fgcr& f, cudaStream_t st) {
+  for (int k = 0; k < f.m; k++) {
+    precondition(c, in, f, f.Z.v[k], st);
+    schur(c, in, f.Z.v[k], f.W.v[k], RED_NONE, nullptr, st);
+    gcr_orthogonalise(P32, f.W, f.Z, k, f.r, in.vg, in.si, in.nseg, in.partial, f.gs, st);
+    gcr_update(P32, f.x, f.r, f.Z.v[k], f.W.v[k], in.vg, in.si, in.nseg, in.partial, f.gs, st);
+  }
+}
+
+// Run restarted FGCR(m) until all systems are inactive or max_iter; returns iterations.
+static int run_fgcr(lqcd_ctx* c, const Inner& in, const Fgcr& f, int max_iter, bool use_graph, int* count_host,
+                    long long& dslash_calls) {
+  cudaStream_t st = c->work;
+  const int nsys = in.nrhs * in.nseg;
+  auto body = [&](cudaStream_t s) { fgcr_cycle(c, in, f, s); };
+  char key[256];
+  snprintf(key, sizeof key, "fgcr:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p", f.m, f.kind, f.n_mr, in.nrhs, in.nseg, f.x,
+           f.Z.v[0], (void*)f.gs.beta, (const void*)in.tc, c->nn_weights);
+  GState gs_count = f.gs;
+  KState ks_count = in.ks;
+  ks_count.active = gs_count.active;
+  ks_count.count = gs_count.count;
+  cudaGraphExec_t exec = use_graph ? capture(c, key, nsys, ks_count, count_host, body) : nullptr;
+  int it = 0;
+  const long long per_cycle = (long long)f.m * (2 + (f.kind == PREC_MR16 ? 2 * f.n_mr : 0));
+  while (it < max_iter) {
+    if (exec) {
+      cudaGraphLaunch(exec, st);
+      count_launch(c->graph_kernels[exec]);
+    } else {
+      body(st);
+      count_active(gs_count.active, nsys, gs_count.count, st);
+      cudaMemcpyAsync(count_host, gs_count.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    }
+    it += f.m;
+    dslash_calls += per_cycle;
+    cudaStreamSynchronize(st);
+    if (*count_host == 0) break;
+  }
+  return it;
+}
+
 int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain, const lqcd_solve_params& prm,
                 BatchStats& bs) {
   cudaStream_t st = c->work;
@@ -190,10 +251,23 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   // Residual reduction asked of one inner solve.  FP32 BiCGStab on a unit-norm right-hand side
   // reaches a true residual of a few 1e-7 before rounding stalls it, so asking 2e-6 makes two
   // defect-correction cycles enough for 1e-10 (each FP64 cycle costs two FP64 dslash launches).
+  // MIXED with FP16 inner precision and FGCR_NN run FP32 flexible GCR whose preconditioner is
+  // FP16-storage MR sweeps or the learned network (MR if no network is loaded).
   double inner_tol = 1e-12;
+  bool use_gcr = false;
+  int pkind = PREC_NONE;
   if (prm.solver == LQCD_SOLVER_MIXED || prm.solver == LQCD_SOLVER_FGCR_NN) {
-    P = prm.inner_prec == LQCD_PREC_F16 ? P16 : P32;
-    inner_tol = P == P32 ? 2e-6 : 1e-2;
+    P = P32;
+    inner_tol = 2e-6;
+    if (prm.solver == LQCD_SOLVER_FGCR_NN) {
+      use_gcr = true;
+      pkind = c->nn_weights ? PREC_NN : PREC_MR16;
+      if (!c->nn_weights) bs.fallback = 1;
+    } else if (prm.inner_prec == LQCD_PREC_F16) {
+      use_gcr = true;
+      pkind = PREC_MR16;
+    }
+    if (use_gcr && prm.precond_iters < 0) pkind = PREC_NONE;  // unpreconditioned FGCR (reference runs)
   }
   if (prm.inner_tol > 0) inner_tol = prm.inner_tol;
 
@@ -205,7 +279,9 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
 
   // FP64 outer fields and per-system bookkeeping
   double2* r64 = (double2*)ws_get(c, "o_r64", 2 * sb64);
-  size_t npart = (size_t)vgF.blocks * nrhs * 3;
+  // per-(block, rhs) partial sums: 3 for BiCGStab / norms on the full lattice, up to 2 x 16 for the
+  // GCR Gram rows on one parity
+  size_t npart = std::max((size_t)vgF.blocks * nrhs * 3, (size_t)vgH.blocks * nrhs * 2 * LQCD_GCR_MAXK);
   double* partial = (double*)ws_get(c, "partial", npart * sizeof(double));
   double* b2 = (double*)ws_get(c, "o_b2", nsys * sizeof(double));
   double* r2 = (double*)ws_get(c, "o_r2", nsys * sizeof(double));
@@ -262,6 +338,52 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   int* count_host = (int*)pinned_get(c, 64);
   cudaMemsetAsync(in.ks.iters, 0, nsys * sizeof(int), st);
 
+  Fgcr f;
+  if (use_gcr) {
+    f.m = prm.gcr_nkrylov > 0 ? std::min(prm.gcr_nkrylov, LQCD_GCR_MAXK) : 8;
+    f.kind = pkind;
+    f.n_mr = prm.precond_iters > 0 ? prm.precond_iters : 6;
+    for (int k = 0; k < f.m; k++) {
+      f.Z.v[k] = ws_get(c, "g_z" + std::to_string(k), sbP);
+      f.W.v[k] = ws_get(c, "g_w" + std::to_string(k), sbP);
+      if (!f.Z.v[k] || !f.W.v[k]) return set_error(c, LQCD_ERR_OOM, "solve: out of device memory (GCR)");
+    }
+    f.x = in.x;
+    f.r = in.r;
+    char* gb = (char*)ws_get(c, "gstate", (size_t)nsys * (LQCD_GCR_MAXK * 24 + 16 + 5 * 8) + 64);
+    if (!gb) return set_error(c, LQCD_ERR_OOM, "solve: out of device memory (GCR)");
+    f.gs.nsys = nsys;
+    f.gs.beta = (double2*)gb;
+    f.gs.alpha = f.gs.beta + (size_t)LQCD_GCR_MAXK * nsys;
+    f.gs.w2 = (double*)(f.gs.alpha + nsys);
+    f.gs.r2 = f.gs.w2 + (size_t)LQCD_GCR_MAXK * nsys;
+    f.gs.b2 = f.gs.r2 + nsys;
+    f.gs.stop2 = f.gs.b2 + nsys;
+    f.gs.pscale = f.gs.stop2 + nsys;
+    f.gs.ipscale = f.gs.pscale + nsys;
+    f.gs.active = in.ks.active;
+    f.gs.iters = in.ks.iters;
+    f.gs.count = in.ks.count;
+    if (pkind == PREC_NN) {
+      if (int rc = nn_reserve(c, nrhs)) return rc;
+    }
+    if (pkind == PREC_MR16) {
+      const size_t sb16 = spinor_bytes(g, P16, nrhs);
+      f.in16 = in;
+      f.in16.prec = P16;
+      f.in16.U = c->U16;
+      f.in16.Ainv_e = off(c->Ainv16, clover_bytes(g, P16), 0);
+      f.in16.Ainv_o = off(c->Ainv16, clover_bytes(g, P16), 1);
+      f.in16.tmp = ws_get(c, "h_tmp", sb16);
+      f.e16 = ws_get(c, "h_e", sb16);
+      f.r16 = ws_get(c, "h_r", sb16);
+      f.p16 = ws_get(c, "h_p", sb16);
+      f.omega16 = (double2*)ws_get(c, "h_omega", nsys * sizeof(double2));
+      if (!f.in16.tmp || !f.e16 || !f.r16 || !f.p16 || !f.omega16)
+        return set_error(c, LQCD_ERR_OOM, "solve: out of device memory (FP16 preconditioner)");
+    }
+  }
+
   // x = 0, r = b, |b|^2
   v_zero(P64, x, vgF, st);
   cudaMemcpyAsync(r64, b, 2 * sb64, cudaMemcpyDeviceToDevice, st);
@@ -287,8 +409,12 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
       launch_dslash(g, kp, st, in.threads);
       bs.dslash += 1;
     }
-    {  // inner BiCGStab
-      PhaseTimer pt(c, P == P64 ? "inner_bicgstab_f64" : (P == P32 ? "inner_bicgstab_f32" : "inner_bicgstab_f16"));
+    if (use_gcr) {  // inner flexible GCR (FP32) with the FP16 MR or network preconditioner
+      PhaseTimer pt(c, pkind == PREC_NN ? "inner_fgcr_nn" : "inner_fgcr_mr16");
+      gcr_init(P32, bhat, in.x, in.r, vgH, si, nseg, partial, f.gs, delta, oact, st);
+      total_iters += run_fgcr(c, in, f, max_iter - total_iters, prm.use_graph != 0, count_host, bs.dslash);
+    } else {  // inner BiCGStab
+      PhaseTimer pt(c, P == P64 ? "inner_bicgstab_f64" : "inner_bicgstab_f32");
       bicg_init(P, bhat, in.r, in.p, in.x, vgH, si, nseg, partial, in.ks, delta, oact, st);
       total_iters += run_bicg(c, in, max_iter - total_iters, chunk, prm.use_graph != 0, count_host, bs.dslash);
     }

@@ -140,6 +140,13 @@ struct lqcd_ctx {
   double2* d_gamma = nullptr;
   // packed site coordinates x | y << 8 | z << 16 | t << 24 per parity: [2][Vh]
   unsigned* d_coord = nullptr;
+  // network preconditioner: FP32 master weights, BF16 inference copy, Adam moments, work fields
+  void* nn_weights = nullptr;
+  void* nn_w16 = nullptr;
+  void* nn_m = nullptr;
+  void* nn_v = nullptr;
+  int nn_step = 0;
+  void* nn_buf[3] = {nullptr, nullptr, nullptr};
   // optional per-phase GPU timing (LQCD_PHASE_TIMING=1): event pairs not yet read, totals in ms
   bool timing = false;
   std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;

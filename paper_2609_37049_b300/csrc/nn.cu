@@ -1,0 +1,698 @@
+// Gauge-covariant parallel-transport network used as the preconditioner of flexible GCR, with
+// its training on the GPU (forward, backward and Adam kernels of this file).
+//
+// A layer maps C_in channels of colour vectors h_c(x) to C_out channels,
+//     out_o(x) = sum_{p=0..8} sum_c W[p][o][c] (T_p h_c)(x),
+//     T_0 h = h,  T_{1+mu} h(x) = U_mu(x) h(x+mu),  T_{5+mu} h(x) = U_mu(x-mu)^dag h(x-mu),
+// on the fermion links (time boundary phase, and Dirichlet cuts for the domain operator, from
+// the same per-timeslice coefficients as the dslash).  Each path commutes with gauge
+// transformations, so the network is gauge covariant.  Four linear layers, channel widths
+// 4 -> 8 -> 8 -> 8 -> 4: a spinor (four spin channels) in, a spinor out.  Inference reads BF16
+// weights and accumulates in FP32; training keeps FP32 master weights.
+//
+// Field layout (FP32 complex): [k = channel * 3 + colour][se][n], se = parity * Vh + cb (even-odd
+// full lattice), n = sample; one thread per (site, sample), samples fastest so the links of a
+// site are a warp broadcast.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <vector>
+
+#include "lqcd_blas.h"
+#include "lqcd_distill.h"
+
+namespace lqcd {
+
+constexpr int NN_LAYERS = 4;
+constexpr int NN_W[NN_LAYERS + 1] = {4, 8, 8, 8, 4};
+constexpr int NN_PATHS = 9;
+
+static int nn_layer_offset(int l) {  // complex entries before layer l
+  int o = 0;
+  for (int i = 0; i < l; i++) o += NN_PATHS * NN_W[i] * NN_W[i + 1];
+  return o;
+}
+int nn_total_weights() { return nn_layer_offset(NN_LAYERS); }
+
+struct NNGeo {
+  Geom g;
+  const unsigned* coord;  // [2][Vh]
+  const float4* U;        // FP32 links (rows 0, 1)
+  const signed char* tc;
+  int N;  // samples
+};
+
+template <typename WT>
+LQCD_D cplx<float> wload(const WT* w, int i);
+template <>
+LQCD_D cplx<float> wload<float2>(const float2* w, int i) {
+  float2 v = w[i];
+  return {v.x, v.y};
+}
+template <>
+LQCD_D cplx<float> wload<__nv_bfloat162>(const __nv_bfloat162* w, int i) {
+  float2 v = __bfloat1622float2(w[i]);
+  return {v.x, v.y};
+}
+
+// Transported channels of one path at one (site, sample): th[c][a] = (T_p h_c)(x)[a].
+// Returns false if the path is cut (coefficient 0).
+template <int C>
+LQCD_D bool path_vectors(const NNGeo& G, const float2* h, int p, int par, long cb, int x, int y, int z, int t,
+                         int n, cplx<float> (&th)[C][3]) {
+  const Geom& g = G.g;
+  const long V = 2 * g.Vh;
+  const long s = x + (long)g.Lx * (y + (long)g.Ly * (z + (long)g.Lz * t));
+  long sn = s;
+  int coef = 1;
+  int mu = (p - 1) & 3;
+  bool fwd = p >= 1 && p <= 4;
+  if (p != 0) {
+    int cm = mu == 0 ? x : (mu == 1 ? y : (mu == 2 ? z : t));
+    int Lm = mu == 0 ? g.Lx : (mu == 1 ? g.Ly : (mu == 2 ? g.Lz : g.Lt));
+    long sm = mu == 0 ? 1 : (mu == 1 ? g.Lx : (mu == 2 ? (long)g.Lx * g.Ly : (long)g.Lx * g.Ly * g.Lz));
+    if (fwd) {
+      sn = s + ((cm + 1 == Lm) ? sm * (1 - Lm) : sm);
+      if (mu == 3) coef = __ldg(G.tc + t);
+    } else {
+      sn = s + ((cm == 0) ? sm * (Lm - 1) : -sm);
+      if (mu == 3) coef = __ldg(G.tc + (t == 0 ? g.Lt - 1 : t - 1));
+    }
+    if (coef == 0) return false;
+  }
+  const int npar = p == 0 ? par : 1 - par;
+  const long nse = (long)npar * g.Vh + (sn >> 1);
+  cplx<float> hv[C][3];
+#pragma unroll
+  for (int c = 0; c < C; c++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      float2 v = __ldg(h + ((long)(c * 3 + a) * V + nse) * G.N + n);
+      hv[c][a] = {v.x, v.y};
+    }
+  if (p == 0) {
+#pragma unroll
+    for (int c = 0; c < C; c++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) th[c][a] = hv[c][a];
+    return true;
+  }
+  cplx<float> u[3][3];
+  if (fwd)
+    load_link<P32>(G.U, g.Vh, mu, par, cb, u);
+  else
+    load_link<P32>(G.U, g.Vh, mu, 1 - par, sn >> 1, u);
+  const float cf = (float)coef;
+#pragma unroll
+  for (int c = 0; c < C; c++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cplx<float> acc = {0.f, 0.f};
+#pragma unroll
+      for (int b = 0; b < 3; b++) acc = acc + (fwd ? u[a][b] * hv[c][b] : cjmul(u[b][a], hv[c][b]));
+      th[c][a] = cf * acc;
+    }
+  return true;
+}
+
+LQCD_D void nn_site(const NNGeo& G, long se, int& par, long& cb, int& x, int& y, int& z, int& t) {
+  par = se >= G.g.Vh ? 1 : 0;
+  cb = se - (long)par * G.g.Vh;
+  const unsigned cw = __ldg(G.coord + (long)par * G.g.Vh + cb);
+  x = cw & 0xff;
+  y = (cw >> 8) & 0xff;
+  z = (cw >> 16) & 0xff;
+  t = cw >> 24;
+}
+
+// out = layer(W, in)  (transport and channel mixing fused; weights staged in shared memory)
+template <int CIN, int COUT, typename WT>
+__global__ void k_nn_layer(const float2* in, float2* out, const WT* W, NNGeo G) {
+  __shared__ cplx<float> Ws[NN_PATHS * COUT * CIN];
+  for (int i = threadIdx.x; i < NN_PATHS * COUT * CIN; i += blockDim.x) Ws[i] = wload<WT>(W, i);
+  __syncthreads();
+  const long V = 2 * G.g.Vh;
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long se = tid / G.N;
+  const int n = (int)(tid - se * G.N);
+  if (se >= V) return;
+  int par, x, y, z, t;
+  long cb;
+  nn_site(G, se, par, cb, x, y, z, t);
+  cplx<float> acc[COUT][3];
+#pragma unroll
+  for (int o = 0; o < COUT; o++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) acc[o][a] = {0.f, 0.f};
+  for (int p = 0; p < NN_PATHS; p++) {
+    cplx<float> th[CIN][3];
+    if (!path_vectors<CIN>(G, in, p, par, cb, x, y, z, t, n, th)) continue;
+#pragma unroll
+    for (int o = 0; o < COUT; o++)
+#pragma unroll
+      for (int c = 0; c < CIN; c++) {
+        cplx<float> w = Ws[(p * COUT + o) * CIN + c];
+#pragma unroll
+        for (int a = 0; a < 3; a++) acc[o][a] = acc[o][a] + w * th[c][a];
+      }
+  }
+#pragma unroll
+  for (int o = 0; o < COUT; o++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) out[((long)(o * 3 + a) * V + se) * G.N + n] = make_float2(acc[o][a].re, acc[o][a].im);
+}
+
+// T[p][k][se][n] = (T_p in)[k] for every path (training: the weight gradient needs them)
+template <int C>
+__global__ void k_nn_transport(const float2* in, float2* T, NNGeo G) {
+  const long V = 2 * G.g.Vh;
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long se = tid / G.N;
+  const int n = (int)(tid - se * G.N);
+  if (se >= V) return;
+  int par, x, y, z, t;
+  long cb;
+  nn_site(G, se, par, cb, x, y, z, t);
+  const long VN = V * G.N;
+  for (int p = 0; p < NN_PATHS; p++) {
+    cplx<float> th[C][3];
+    bool on = path_vectors<C>(G, in, p, par, cb, x, y, z, t, n, th);
+#pragma unroll
+    for (int c = 0; c < C; c++)
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+        T[((long)p * C * 3 + c * 3 + a) * VN + se * G.N + n] =
+            on ? make_float2(th[c][a].re, th[c][a].im) : make_float2(0.f, 0.f);
+  }
+}
+
+// partial[block][p][o][c] = sum over the block's site-samples of sum_a d_o[a] conj(T_p h_c[a])
+template <int CIN, int COUT>
+__global__ void k_nn_wgrad(const float2* T, const float2* d, float* partial, long VN, long per_block) {
+  constexpr int TS = 16;
+  extern __shared__ float2 smw[];
+  float2* Ds = smw;                       // [TS][COUT*3]
+  float2* Ts = smw + TS * COUT * 3;       // [TS][9][CIN*3]
+  const int nthr = NN_PATHS * COUT * CIN;
+  const int me = threadIdx.x;
+  const int p = me / (COUT * CIN), o = (me / CIN) % COUT, c = me % CIN;
+  double accr = 0, acci = 0;
+  const long q0 = (long)blockIdx.x * per_block;
+  const long q1 = q0 + per_block < VN ? q0 + per_block : VN;
+  for (long qb = q0; qb < q1; qb += TS) {
+    for (int e = threadIdx.x; e < TS * COUT * 3; e += blockDim.x) {
+      int i = e / (COUT * 3), k = e % (COUT * 3);
+      long q = qb + i;
+      Ds[e] = q < q1 ? d[(long)k * VN + q] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < TS * NN_PATHS * CIN * 3; e += blockDim.x) {
+      int i = e / (NN_PATHS * CIN * 3), k = e % (NN_PATHS * CIN * 3);
+      long q = qb + i;
+      Ts[e] = q < q1 ? T[(long)k * VN + q] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (me < nthr) {
+      float sr = 0, si = 0;
+      for (int i = 0; i < TS; i++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          float2 dv = Ds[i * COUT * 3 + o * 3 + a];
+          float2 tv = Ts[(i * NN_PATHS + p) * CIN * 3 + c * 3 + a];
+          sr += dv.x * tv.x + dv.y * tv.y;  // d * conj(t)
+          si += dv.y * tv.x - dv.x * tv.y;
+        }
+      accr += sr;
+      acci += si;
+    }
+    __syncthreads();
+  }
+  if (me < nthr) {
+    partial[((long)blockIdx.x * nthr + me) * 2] = (float)accr;
+    partial[((long)blockIdx.x * nthr + me) * 2 + 1] = (float)acci;
+  }
+}
+
+__global__ void k_nn_sum_blocks(const float* partial, int nblocks, int nvals, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvals) return;
+  double s = 0;
+  for (int b = 0; b < nblocks; b++) s += partial[(long)b * nvals + i];
+  out[i] = s;
+}
+
+// sums[0] += sum mask |tgt|^2, sums[1] += sum mask |out - tgt|^2 (per block partials)
+__global__ void k_nn_loss_partial(const float2* out, const float2* tgt, long VN, long Vh, int N, int even_only,
+                                  double* partial) {
+  __shared__ double sa[256], sb[256];
+  double a = 0, b = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < 12 * VN; i += (long)gridDim.x * blockDim.x) {
+    long q = i % VN;
+    long se = q / N;
+    if (even_only && se >= Vh) continue;
+    float2 o = out[i], t = tgt[i];
+    a += (double)t.x * t.x + (double)t.y * t.y;
+    double dx = o.x - t.x, dy = o.y - t.y;
+    b += dx * dx + dy * dy;
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s >= 1; s >>= 1) {
+    if (threadIdx.x < s) {
+      sa[threadIdx.x] += sa[threadIdx.x + s];
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = sa[0];
+    partial[2 * blockIdx.x + 1] = sb[0];
+  }
+}
+
+__global__ void k_nn_loss_final(const double* partial, int nb, double* sums) {
+  if (threadIdx.x || blockIdx.x) return;
+  double a = 0, b = 0;
+  for (int i = 0; i < nb; i++) {
+    a += partial[2 * i];
+    b += partial[2 * i + 1];
+  }
+  sums[0] = a;
+  sums[1] = b;
+  sums[2] = a > 0 ? b / a : 0.0;
+}
+
+// delta = mask (out - tgt) / sum mask |tgt|^2
+__global__ void k_nn_delta(const float2* out, const float2* tgt, float2* delta, long VN, long Vh, int N,
+                           int even_only, const double* sums) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 12 * VN) return;
+  long se = (i % VN) / N;
+  float inv = sums[0] > 0 ? (float)(1.0 / sums[0]) : 0.f;
+  float2 o = out[i], t = tgt[i];
+  bool on = !(even_only && se >= Vh);
+  delta[i] = on ? make_float2((o.x - t.x) * inv, (o.y - t.y) * inv) : make_float2(0.f, 0.f);
+}
+
+// Adam on the real and imaginary parts: the real gradient is 2 Re / 2 Im of dL/dconj(W).
+__global__ void k_nn_adam(float2* W, __nv_bfloat162* W16, const double* grad, float2* m, float2* v, int n,
+                          float lr, float b1, float b2, float eps, int step) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gr = (float)(2.0 * grad[2 * i]), gi = (float)(2.0 * grad[2 * i + 1]);
+  float2 mm = m[i], vv = v[i];
+  mm.x = b1 * mm.x + (1 - b1) * gr;
+  mm.y = b1 * mm.y + (1 - b1) * gi;
+  vv.x = b2 * vv.x + (1 - b2) * gr * gr;
+  vv.y = b2 * vv.y + (1 - b2) * gi * gi;
+  m[i] = mm;
+  v[i] = vv;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  float2 w = W[i];
+  w.x -= lr * (mm.x / c1) / (sqrtf(vv.x / c2) + eps);
+  w.y -= lr * (mm.y / c1) / (sqrtf(vv.y / c2) + eps);
+  W[i] = w;
+  W16[i] = __floats2bfloat162_rn(w.x, w.y);
+}
+
+__global__ void k_nn_to_bf16(const float2* W, __nv_bfloat162* W16, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) W16[i] = __floats2bfloat162_rn(W[i].x, W[i].y);
+}
+
+// Adjoint weights: Wa[p][c][o] = conj(W[pbar][o][c]) with pbar the reverse path.
+__global__ void k_nn_adjoint_weights(const float2* W, float2* Wa, int cin, int cout) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NN_PATHS * cin * cout) return;
+  int p = i / (cin * cout), c = (i / cout) % cin, o = i % cout;
+  int pb = p == 0 ? 0 : (p <= 4 ? p + 4 : p - 4);
+  float2 w = W[(pb * cout + o) * cin + c];
+  Wa[i] = make_float2(w.x, -w.y);
+}
+
+// even-half FP32 spinor [6 float4][cb][nrhs] <-> NN field (4 spin channels, full lattice)
+__global__ void k_nn_from_spinor(const void* r, float2* h, Geom g, int nrhs, const SegInfo* si, int nseg,
+                                 const double* scale) {
+  const long V = 2 * g.Vh;
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= V * nrhs) return;
+  const long se = tid / nrhs;
+  const int n = (int)(tid - se * nrhs);
+  if (se >= g.Vh) {  // odd sites: zero
+    for (int k = 0; k < 12; k++) h[((long)k * V + se) * nrhs + n] = make_float2(0.f, 0.f);
+    return;
+  }
+  cplx<float> s[12];
+  load_spinor<P32>(r, g.Vh * nrhs, se * nrhs + n, s);
+  const int t = (int)(se / g.Vth);
+  const float sc = scale ? (float)scale[n * nseg + (si ? si->seg_of_t[t] : 0)] : 1.f;
+  for (int k = 0; k < 12; k++) h[((long)k * V + se) * nrhs + n] = make_float2(sc * s[k].re, sc * s[k].im);
+}
+
+__global__ void k_nn_to_spinor(const float2* h, void* z, Geom g, int nrhs, const SegInfo* si, int nseg,
+                               const double* scale) {
+  const long V = 2 * g.Vh;
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= g.Vh * nrhs) return;
+  const long se = tid / nrhs;
+  const int n = (int)(tid - se * nrhs);
+  const int t = (int)(se / g.Vth);
+  const float sc = scale ? (float)scale[n * nseg + (si ? si->seg_of_t[t] : 0)] : 1.f;
+  cplx<float> s[12];
+  for (int k = 0; k < 12; k++) {
+    float2 v = h[((long)k * V + se) * nrhs + n];
+    s[k] = {sc * v.x, sc * v.y};
+  }
+  store_spinor<P32>(z, g.Vh * nrhs, se * nrhs + n, s);
+}
+
+// lexicographic FP32 complex [n][V][4][3] <-> NN field
+__global__ void k_nn_lex(const float2* a, float2* b, Geom g, int N, int to_nn, const unsigned* coord) {
+  const long V = 2 * g.Vh;
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= V * N) return;
+  const long se = tid / N;
+  const int n = (int)(tid - se * N);
+  const int par = se >= g.Vh ? 1 : 0;
+  const long cb = se - (long)par * g.Vh;
+  const unsigned cw = coord[(long)par * g.Vh + cb];
+  const long s = (cw & 0xff) + (long)g.Lx * (((cw >> 8) & 0xff) + (long)g.Ly * (((cw >> 16) & 0xff) + (long)g.Lz * (cw >> 24)));
+  for (int k = 0; k < 12; k++) {
+    if (to_nn)
+      b[((long)k * V + se) * N + n] = a[((long)n * V + s) * 12 + k];
+    else
+      b[((long)n * V + s) * 12 + k] = a[((long)k * V + se) * N + n];
+  }
+}
+
+// deterministic Gaussian-like random even-site FP64 spinors (training inputs)
+__global__ void k_nn_random_even(double2* b, Geom g, int nrhs, unsigned seed) {
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= 2 * g.Vh * nrhs) return;
+  const int n = (int)(tid % nrhs);
+  const long site = tid / nrhs;
+  const int par = (int)(site / g.Vh);
+  const long cb = site - (long)par * g.Vh;
+  for (int k = 0; k < 12; k++) {
+    double2 v = make_double2(0.0, 0.0);
+    if (par == 0) {
+      unsigned long long h = ((unsigned long long)(cb * nrhs + n) * 12 + k) * 0x9E3779B97F4A7C15ull ^
+                             ((unsigned long long)seed << 32);
+      h ^= h >> 33;
+      h *= 0xff51afd7ed558ccdull;
+      h ^= h >> 33;
+      h *= 0xc4ceb9fe1a85ec53ull;
+      h ^= h >> 33;
+      double u1 = ((h & 0xFFFFFFFF) + 0.5) / 4294967296.0, u2 = ((h >> 32) + 0.5) / 4294967296.0;
+      double rr = sqrt(-2.0 * log(u1));
+      v = make_double2(rr * cos(6.283185307179586 * u2), rr * sin(6.283185307179586 * u2));
+    }
+    b[((long)par * 12 * g.Vh + (k * g.Vh + cb)) * nrhs + n] = v;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+static NNGeo nn_geo(lqcd_ctx* c, int N, int domain) {
+  NNGeo G;
+  G.g = c->g;
+  G.coord = c->d_coord;
+  G.U = (const float4*)c->U32;
+  G.tc = domain ? c->d_tc_dom : c->d_tc_full;
+  G.N = N;
+  return G;
+}
+
+template <typename WT>
+static void layer_launch(int l_in, int l_out, const float2* in, float2* out, const WT* W, const NNGeo& G,
+                         cudaStream_t st) {
+  const long n = 2 * G.g.Vh * (long)G.N;
+  const int tpb = 128;
+  const long blocks = (n + tpb - 1) / tpb;
+  if (l_in == 4 && l_out == 8)
+    k_nn_layer<4, 8, WT><<<blocks, tpb, 0, st>>>(in, out, W, G);
+  else if (l_in == 8 && l_out == 8)
+    k_nn_layer<8, 8, WT><<<blocks, tpb, 0, st>>>(in, out, W, G);
+  else if (l_in == 8 && l_out == 4)
+    k_nn_layer<8, 4, WT><<<blocks, tpb, 0, st>>>(in, out, W, G);
+  else
+    k_nn_layer<4, 4, WT><<<blocks, tpb, 0, st>>>(in, out, W, G);
+  count_launch();
+}
+
+static bool nn_ensure(lqcd_ctx* c) {
+  if (c->nn_weights) return true;
+  const int n = nn_total_weights();
+  if (cudaMalloc(&c->nn_weights, n * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&c->nn_w16, n * sizeof(__nv_bfloat162)) != cudaSuccess ||
+      cudaMalloc(&c->nn_m, n * sizeof(float2)) != cudaSuccess || cudaMalloc(&c->nn_v, n * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaMemsetAsync(c->nn_m, 0, n * sizeof(float2), c->work);
+  cudaMemsetAsync(c->nn_v, 0, n * sizeof(float2), c->work);
+  c->nn_step = 0;
+  return true;
+}
+
+int nn_set_weights(lqcd_ctx* c, const float* w_host) {
+  const int n = nn_total_weights();
+  if (!nn_ensure(c)) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
+  cudaMemcpyAsync(c->nn_weights, w_host, n * sizeof(float2), cudaMemcpyHostToDevice, c->work);
+  k_nn_to_bf16<<<(n + 255) / 256, 256, 0, c->work>>>((const float2*)c->nn_weights, (__nv_bfloat162*)c->nn_w16, n);
+  count_launch();
+  cudaMemsetAsync(c->nn_m, 0, n * sizeof(float2), c->work);
+  cudaMemsetAsync(c->nn_v, 0, n * sizeof(float2), c->work);
+  c->nn_step = 0;
+  cudaStreamSynchronize(c->work);
+  return LQCD_OK;
+}
+
+int nn_get_weights(lqcd_ctx* c, float* w_host) {
+  if (!c->nn_weights) return set_error(c, LQCD_ERR_STATE, "nn: no weights");
+  cudaMemcpyAsync(w_host, c->nn_weights, nn_total_weights() * sizeof(float2), cudaMemcpyDeviceToHost, c->work);
+  cudaStreamSynchronize(c->work);
+  return LQCD_OK;
+}
+
+// Network on NN-layout fields (N samples); bf16 = 1 uses the inference weights.  a, b: ping-pong
+// buffers of 8 channels; the result is in the returned pointer (4 channels).
+static float2* nn_forward(lqcd_ctx* c, const float2* h0, float2* a, float2* b, int N, int domain, bool bf16,
+                          cudaStream_t st) {
+  NNGeo G = nn_geo(c, N, domain);
+  const float2* cur = h0;
+  float2* bufs[2] = {a, b};
+  for (int l = 0; l < NN_LAYERS; l++) {
+    float2* out = bufs[l & 1];
+    const int off = nn_layer_offset(l);
+    if (bf16)
+      layer_launch<__nv_bfloat162>(NN_W[l], NN_W[l + 1], cur, out, (const __nv_bfloat162*)c->nn_w16 + off, G, st);
+    else
+      layer_launch<float2>(NN_W[l], NN_W[l + 1], cur, out, (const float2*)c->nn_weights + off, G, st);
+    cur = out;
+  }
+  return (float2*)cur;
+}
+
+void nn_precondition(lqcd_ctx* c, const Inner& in, const void* r, void* z, const double* pscale,
+                     const double* ipscale, cudaStream_t st) {
+  const Geom& g = c->g;
+  const int N = in.nrhs;
+  const long V = 2 * g.Vh;
+  const size_t fb = (size_t)24 * V * N * sizeof(float2);
+  float2* h0 = (float2*)c->nn_buf[0];
+  float2* a = (float2*)c->nn_buf[1];
+  float2* b = (float2*)c->nn_buf[2];
+  (void)fb;
+  const long n = V * N;
+  k_nn_from_spinor<<<(n + 255) / 256, 256, 0, st>>>(r, h0, g, N, in.si, in.nseg, pscale);
+  count_launch();
+  const int domain = in.tc == c->d_tc_dom && c->d_tc_dom != c->d_tc_full;
+  float2* out = nn_forward(c, h0, a, b, N, domain, true, st);
+  k_nn_to_spinor<<<(g.Vh * N + 255) / 256, 256, 0, st>>>(out, z, g, N, in.si, in.nseg, ipscale);
+  count_launch();
+}
+
+// Reserve the three NN-layout work fields used by nn_precondition for a batch of nrhs (outside
+// graph capture).
+int nn_reserve(lqcd_ctx* c, int nrhs) {
+  const size_t fb = (size_t)24 * 2 * c->g.Vh * nrhs * sizeof(float2);
+  for (int i = 0; i < 3; i++) {
+    c->nn_buf[i] = ws_get(c, "nn_buf" + std::to_string(i), fb);
+    if (!c->nn_buf[i]) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
+  }
+  return LQCD_OK;
+}
+
+// Forward + loss + backward (and optionally Adam) on NN-layout input/target of N samples.
+// Returns the loss through *loss; grad_host (may be NULL) receives dL/dconj(W) as float pairs.
+static int nn_step(lqcd_ctx* c, const float2* h0, const float2* tgt, int N, int domain, int even_only,
+                   double* loss, float* grad_host, bool adam, float lr) {
+  cudaStream_t st = c->work;
+  const Geom& g = c->g;
+  const long V = 2 * g.Vh, VN = V * N;
+  NNGeo G = nn_geo(c, N, domain);
+  // activations h1..h4 (up to 8 channels) and transported copies of h0..h3
+  float2* act[NN_LAYERS + 1];
+  act[0] = (float2*)h0;
+  float2* T[NN_LAYERS];
+  for (int l = 0; l < NN_LAYERS; l++) {
+    act[l + 1] = (float2*)ws_get(c, "nn_act" + std::to_string(l), (size_t)NN_W[l + 1] * 3 * VN * sizeof(float2));
+    T[l] = (float2*)ws_get(c, "nn_T" + std::to_string(l), (size_t)NN_PATHS * NN_W[l] * 3 * VN * sizeof(float2));
+    if (!act[l + 1] || !T[l]) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory (training)");
+  }
+  float2* d0 = (float2*)ws_get(c, "nn_d0", (size_t)24 * VN * sizeof(float2));
+  float2* d1 = (float2*)ws_get(c, "nn_d1", (size_t)24 * VN * sizeof(float2));
+  float2* Wa = (float2*)ws_get(c, "nn_Wadj", (size_t)NN_PATHS * 64 * sizeof(float2));
+  double* grad = (double*)ws_get(c, "nn_grad", (size_t)2 * nn_total_weights() * sizeof(double));
+  const int lblocks = 296;
+  double* lpart = (double*)ws_get(c, "nn_lpart", (size_t)2 * lblocks * sizeof(double));
+  double* sums = (double*)ws_get(c, "nn_sums", 4 * sizeof(double));
+  if (!d0 || !d1 || !Wa || !grad || !lpart || !sums) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
+  const int tpb = 128;
+  const long nb = (VN + tpb - 1) / tpb;
+  for (int l = 0; l < NN_LAYERS; l++) {
+    if (NN_W[l] == 4)
+      k_nn_transport<4><<<nb, tpb, 0, st>>>(act[l], T[l], G);
+    else
+      k_nn_transport<8><<<nb, tpb, 0, st>>>(act[l], T[l], G);
+    count_launch();
+    layer_launch<float2>(NN_W[l], NN_W[l + 1], act[l], act[l + 1], (const float2*)c->nn_weights + nn_layer_offset(l),
+                         G, st);
+  }
+  k_nn_loss_partial<<<lblocks, 256, 0, st>>>(act[NN_LAYERS], tgt, VN, g.Vh, N, even_only, lpart);
+  k_nn_loss_final<<<1, 1, 0, st>>>(lpart, lblocks, sums);
+  k_nn_delta<<<(12 * VN + 255) / 256, 256, 0, st>>>(act[NN_LAYERS], tgt, d0, VN, g.Vh, N, even_only, sums);
+  count_launch(3);
+  float2* dcur = d0;
+  float2* dnext = d1;
+  for (int l = NN_LAYERS - 1; l >= 0; l--) {
+    const int cin = NN_W[l], cout = NN_W[l + 1], nval = NN_PATHS * cin * cout;
+    const long per_block = 4096;
+    const int nblk = (int)((VN + per_block - 1) / per_block);
+    float* wpart = (float*)ws_get(c, "nn_wpart", (size_t)nblk * 2 * NN_PATHS * 64 * sizeof(float));
+    if (!wpart) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
+    const size_t shm = (size_t)16 * (cout * 3 + NN_PATHS * cin * 3) * sizeof(float2);
+    if (cin == 4)
+      k_nn_wgrad<4, 8><<<nblk, nval, shm, st>>>(T[l], dcur, wpart, VN, per_block);
+    else if (cout == 8)
+      k_nn_wgrad<8, 8><<<nblk, nval, shm, st>>>(T[l], dcur, wpart, VN, per_block);
+    else
+      k_nn_wgrad<8, 4><<<nblk, nval, shm, st>>>(T[l], dcur, wpart, VN, per_block);
+    k_nn_sum_blocks<<<(2 * nval + 255) / 256, 256, 0, st>>>(wpart, nblk, 2 * nval, grad + 2 * nn_layer_offset(l));
+    count_launch(2);
+    if (l > 0) {  // delta of the layer input: adjoint layer
+      k_nn_adjoint_weights<<<(nval + 127) / 128, 128, 0, st>>>((const float2*)c->nn_weights + nn_layer_offset(l), Wa,
+                                                               cin, cout);
+      count_launch();
+      layer_launch<float2>(cout, cin, dcur, dnext, Wa, G, st);
+      std::swap(dcur, dnext);
+    }
+  }
+  double hs[4];
+  cudaMemcpyAsync(hs, sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (grad_host) {
+    std::vector<double> gd(2 * nn_total_weights());
+    cudaMemcpyAsync(gd.data(), grad, gd.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    for (size_t i = 0; i < gd.size(); i++) grad_host[i] = (float)gd[i];
+  }
+  if (adam) {
+    c->nn_step++;
+    const int n = nn_total_weights();
+    k_nn_adam<<<(n + 255) / 256, 256, 0, st>>>((float2*)c->nn_weights, (__nv_bfloat162*)c->nn_w16, grad,
+                                               (float2*)c->nn_m, (float2*)c->nn_v, n, lr, 0.9f, 0.999f, 1e-8f,
+                                               c->nn_step);
+    count_launch();
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, std::string("nn: ") + cudaGetErrorString(e));
+  *loss = hs[2];
+  return LQCD_OK;
+}
+
+int nn_apply_lex(lqcd_ctx* c, const float2* in_dev, float2* out_dev, int N, int domain) {
+  if (!c->nn_weights) return set_error(c, LQCD_ERR_STATE, "nn: no weights");
+  const long VN = 2 * c->g.Vh * (long)N;
+  float2* h0 = (float2*)ws_get(c, "nn_h0", (size_t)12 * VN * sizeof(float2));
+  float2* a = (float2*)ws_get(c, "nn_pa", (size_t)24 * VN * sizeof(float2));
+  float2* b = (float2*)ws_get(c, "nn_pb", (size_t)24 * VN * sizeof(float2));
+  if (!h0 || !a || !b) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
+  k_nn_lex<<<(VN + 255) / 256, 256, 0, c->work>>>(in_dev, h0, c->g, N, 1, c->d_coord);
+  count_launch();
+  float2* out = nn_forward(c, h0, a, b, N, domain, false, c->work);
+  k_nn_lex<<<(VN + 255) / 256, 256, 0, c->work>>>(out, out_dev, c->g, N, 0, c->d_coord);
+  count_launch();
+  return LQCD_OK;
+}
+
+int nn_loss_grad_lex(lqcd_ctx* c, const float2* in_dev, const float2* tgt_dev, int N, int domain, int even_only,
+                     double* loss, float* grad_host) {
+  if (!c->nn_weights) return set_error(c, LQCD_ERR_STATE, "nn: no weights");
+  const long VN = 2 * c->g.Vh * (long)N;
+  float2* h0 = (float2*)ws_get(c, "nn_h0", (size_t)12 * VN * sizeof(float2));
+  float2* tg = (float2*)ws_get(c, "nn_tg", (size_t)12 * VN * sizeof(float2));
+  if (!h0 || !tg) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
+  k_nn_lex<<<(VN + 255) / 256, 256, 0, c->work>>>(in_dev, h0, c->g, N, 1, c->d_coord);
+  k_nn_lex<<<(VN + 255) / 256, 256, 0, c->work>>>(tgt_dev, tg, c->g, N, 1, c->d_coord);
+  count_launch(2);
+  return nn_step(c, h0, tg, N, domain, even_only, loss, grad_host, false, 0.f);
+}
+
+// Training pairs (r, e) with M e = r for the even-odd Schur operator M, from the plain FP64
+// solver: b = (A_ee r, 0) solved with D gives x_e = M^-1 A_ee^-1 b_e = M^-1 r.  Then Adam on
+// the loss |N(r) - e|^2 / |e|^2 over even sites.  loss_hist[epochs] receives the mean loss.
+int nn_train(lqcd_ctx* c, int n_pairs, int epochs, int batch, double lr, int domain, unsigned seed,
+             double* loss_hist) {
+  cudaStream_t st = c->work;
+  const Geom& g = c->g;
+  if (!nn_ensure(c)) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
+  const long V = 2 * g.Vh;
+  const int nb_pairs = (n_pairs + batch - 1) / batch;
+  n_pairs = nb_pairs * batch;
+  // pair storage in NN layout (FP32): inputs and targets, batch-major
+  const size_t per_batch = (size_t)12 * V * batch * sizeof(float2);
+  float2* R = (float2*)ws_get(c, "nn_pairs_r", per_batch * nb_pairs);
+  float2* E = (float2*)ws_get(c, "nn_pairs_e", per_batch * nb_pairs);
+  double2* b64 = (double2*)ws_get(c, "nn_b64", (size_t)2 * spinor_bytes(g, P64, batch));
+  double2* x64 = (double2*)ws_get(c, "nn_x64", (size_t)2 * spinor_bytes(g, P64, batch));
+  double2* r64 = (double2*)ws_get(c, "nn_r64", (size_t)2 * spinor_bytes(g, P64, batch));
+  void* f32 = ws_get(c, "nn_f32", spinor_bytes(g, P32, batch));
+  if (!R || !E || !b64 || !x64 || !r64 || !f32) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory (pairs)");
+  lqcd_solve_params p;
+  lqcd_default_params(&p);
+  p.solver = LQCD_SOLVER_BICGSTAB64;
+  p.tol = 1e-8;
+  const size_t sb64 = spinor_bytes(g, P64, batch);
+  VGeom vgH = make_vgeom(g, batch, 1);
+  for (int k = 0; k < nb_pairs; k++) {
+    k_nn_random_even<<<(2 * g.Vh * batch + 255) / 256, 256, 0, st>>>(r64, g, batch, seed + 7919u * k);
+    count_launch();
+    cudaMemsetAsync(b64, 0, 2 * sb64, st);
+    launch_clover_only(g, P64, c->A64, r64, b64, batch, st);  // b_e = A_ee r_e
+    BatchStats bs;
+    int rc = solve_batch(c, b64, x64, batch, domain, p, bs);
+    if (rc != LQCD_OK) return rc;
+    // even halves to NN layout (odd zero)
+    v_convert(P64, P32, r64, f32, vgH, nullptr, 1, nullptr, st);
+    k_nn_from_spinor<<<(V * batch + 255) / 256, 256, 0, st>>>(f32, R + (size_t)k * 12 * V * batch, g, batch, nullptr, 1,
+                                                             nullptr);
+    v_convert(P64, P32, x64, f32, vgH, nullptr, 1, nullptr, st);
+    k_nn_from_spinor<<<(V * batch + 255) / 256, 256, 0, st>>>(f32, E + (size_t)k * 12 * V * batch, g, batch, nullptr, 1,
+                                                             nullptr);
+    count_launch(2);
+  }
+  for (int ep = 0; ep < epochs; ep++) {
+    double acc = 0;
+    for (int k = 0; k < nb_pairs; k++) {
+      double L = 0;
+      int rc = nn_step(c, R + (size_t)k * 12 * V * batch, E + (size_t)k * 12 * V * batch, batch, domain, 1, &L,
+                       nullptr, true, (float)lr);
+      if (rc != LQCD_OK) return rc;
+      acc += L;
+    }
+    if (loss_hist) loss_hist[ep] = acc / nb_pairs;
+  }
+  return LQCD_OK;
+}
+
+}  // namespace lqcd

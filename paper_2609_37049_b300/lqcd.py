@@ -32,8 +32,27 @@ EXPORTED = [
     "lqcd_gauge_upload", "lqcd_set_domains", "lqcd_dirac_apply", "lqcd_solve_full",
     "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
     "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
-    "lqcd_phase_times",
+    "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
+    "lqcd_nn_loss_grad", "lqcd_nn_train",
 ]
+
+NN_WIDTHS = (4, 8, 8, 8, 4)
+
+
+def nn_flatten(Ws):
+    """Network weights [W_l (9, C_out, C_in) complex] -> flat float32 (re, im) array of the C ABI."""
+    return np.ascontiguousarray(np.concatenate([np.asarray(W, dtype=np.complex64).ravel() for W in Ws]).view(
+        np.float32))
+
+
+def nn_unflatten(flat):
+    c = np.asarray(flat, dtype=np.float32).view(np.complex64)
+    out, o = [], 0
+    for cin, cout in zip(NN_WIDTHS[:-1], NN_WIDTHS[1:]):
+        n = 9 * cout * cin
+        out.append(c[o:o + n].reshape(9, cout, cin).astype(np.complex128))
+        o += n
+    return out
 
 
 def kernel_launches():
@@ -91,6 +110,12 @@ def load_library(path=_LIB_PATH):
         "lqcd_disc_correlator_noalloc": (ip, [vp, vp, vp, vp, ip, ip, ip, vp, ip, vp, vp, vp, vp, vp, vp, vp, vp,
                                               vp]),
         "lqcd_phase_times": (ip, [vp, ctypes.c_char_p, ip, ip]),
+        "lqcd_nn_num_weights": (ip, []),
+        "lqcd_nn_set_weights": (ip, [vp, vp]),
+        "lqcd_nn_get_weights": (ip, [vp, vp]),
+        "lqcd_nn_apply": (ip, [vp, vp, vp, ip, ip, ip]),
+        "lqcd_nn_loss_grad": (ip, [vp, vp, vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_double), vp]),
+        "lqcd_nn_train": (ip, [vp, ip, ip, ip, ctypes.c_double, ip, ctypes.c_uint, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -257,6 +282,34 @@ class Context:
             self.h, _ptr(L), _ptr(Lt), _ptr(Ld), _ptr(Ltd), n_cfg, n_g, int(vev), _ptr(out["C"]),
             _ptr(out["Cdd"]), _ptr(out["dC"]), _ptr(out["C_avg"]), _ptr(out["dC_avg"]),
             _ptr(out["valid"], np.int32), _ptr(out["n_valid"], np.int32), _ptr(terms), w))
+
+    # ---- learned preconditioner
+    def nn_set_weights(self, Ws):
+        flat = nn_flatten(Ws)
+        return self._check(_lib.lqcd_nn_set_weights(self.h, ctypes.c_void_p(flat.ctypes.data)))
+
+    def nn_get_weights(self):
+        flat = np.zeros(2 * _lib.lqcd_nn_num_weights(), dtype=np.float32)
+        self._check(_lib.lqcd_nn_get_weights(self.h, ctypes.c_void_p(flat.ctypes.data)))
+        return nn_unflatten(flat)
+
+    def nn_apply(self, x, out, domain=False):
+        return self._check(_lib.lqcd_nn_apply(self.h, _ptr(x, np.complex64), _ptr(out, np.complex64), x.shape[0],
+                                              int(domain), _where(x, out)))
+
+    def nn_loss_grad(self, x, target, domain=False, even_only=False):
+        loss = ctypes.c_double()
+        g = np.zeros(2 * _lib.lqcd_nn_num_weights(), dtype=np.float32)
+        self._check(_lib.lqcd_nn_loss_grad(self.h, _ptr(x, np.complex64), _ptr(target, np.complex64), x.shape[0],
+                                           int(domain), int(even_only), _where(x, target), ctypes.byref(loss),
+                                           ctypes.c_void_p(g.ctypes.data)))
+        return loss.value, nn_unflatten(g)
+
+    def nn_train(self, n_pairs, epochs, batch, lr, domain=False, seed=1):
+        hist = np.zeros(epochs, dtype=np.float64)
+        self._check(_lib.lqcd_nn_train(self.h, int(n_pairs), int(epochs), int(batch), float(lr), int(domain),
+                                       int(seed), ctypes.c_void_p(hist.ctypes.data)))
+        return hist
 
     def phase_times(self, reset=False):
         """GPU milliseconds per solver phase (needs LQCD_PHASE_TIMING=1 at context creation)."""
