@@ -202,6 +202,10 @@ def run_ours(args, rank, world):
     ctx.laplace_eigs(N_EV, Vd, lam)
     torch.cuda.synchronize()
     t_eig = time.time() - t0
+    import tempfile
+    from paper_2609_37049_b300 import autotune
+    tuning = autotune.tune(ctx, cache=os.path.join(tempfile.gettempdir(), "lqcd_tuning.json"),
+                           precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F64), blocks=(RHS_BLOCK,))
     params = default_params(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F32, rhs_block=RHS_BLOCK)
     n_grp = len(EXTENTS)
     tau_f = torch.zeros((n_grp, N_EV, 4, N_EV, 4), dtype=torch.complex128, device="cuda")
@@ -288,21 +292,39 @@ def run_ours(args, rank, world):
     e2e = {"value": rhs_per_step * e_steps * world / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "steps": e_steps}
 
-    # ---- plain FP64 solver on a sample (one source timeslice, full operator, 128 RHS)
-    plain_p = default_params(solver=lqcd.LQCD_SOLVER_BICGSTAB64, rhs_block=RHS_BLOCK)
+    # ---- solvers compared on one sample: full-operator perambulator of one source timeslice
+    # (128 RHS); every one reaches FP64 true residual 1e-10
     tau1 = torch.zeros((1, N_EV, 4, N_EV, 4), dtype=torch.complex128, device="cuda")
-    torch.cuda.synchronize()
+
+    def sample(p):
+        ctx.perambulator(Vd, N_EV, [0], tau1, mode=lqcd.LQCD_MODE_FULL, params=p)  # graphs, buffers
+        torch.cuda.synchronize()
+        t0 = time.time()
+        st = Stats(1, 1)
+        ctx.perambulator(Vd, N_EV, [0], tau1, mode=lqcd.LQCD_MODE_FULL, params=p, stats=st)
+        torch.cuda.synchronize()
+        return {"rhs_per_s": 4 * N_EV / (time.time() - t0), "iters_per_rhs": st.total_iters / (4 * N_EV),
+                "max_true_resid": st.max_true_resid, "fallback": st.fallback}
+
+    solvers = {}
+    solvers["plain_fp64_bicgstab"] = sample(default_params(solver=lqcd.LQCD_SOLVER_BICGSTAB64, rhs_block=RHS_BLOCK))
+    solvers["mixed_fp32_bicgstab"] = sample(params)
+    solvers["mixed_fgcr_fp16_mr4"] = sample(default_params(solver=lqcd.LQCD_SOLVER_MIXED,
+                                                           inner_prec=lqcd.LQCD_PREC_F16, precond_iters=4,
+                                                           rhs_block=RHS_BLOCK))
+    solvers["mixed_fgcr_none"] = sample(default_params(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F16,
+                                                       precond_iters=-1, rhs_block=RHS_BLOCK))
+    ctx.nn_set_weights(lqcd.nn_initial_weights(5, 0.05))
     t0 = time.time()
-    st = Stats(1, 1)
-    ctx.perambulator(Vd, N_EV, [0], tau1, mode=lqcd.LQCD_MODE_FULL, params=plain_p, stats=st)
+    hist = ctx.nn_train(n_pairs=64, epochs=12, batch=8, lr=3e-3, seed=11)
     torch.cuda.synchronize()
-    plain = {"value": 4 * N_EV / (time.time() - t0), "unit": "RHS/s", "sample": "full-operator "
-             "perambulator of one source timeslice (128 RHS), BiCGStab entirely in FP64",
-             "max_true_resid": st.max_true_resid}
-    t0 = time.time()
-    ctx.perambulator(Vd, N_EV, [0], tau1, mode=lqcd.LQCD_MODE_FULL, params=params)
-    torch.cuda.synchronize()
-    mixed_same = 4 * N_EV / (time.time() - t0)
+    train_s = time.time() - t0
+    solvers["mixed_fgcr_learned"] = sample(default_params(solver=lqcd.LQCD_SOLVER_FGCR_NN, rhs_block=RHS_BLOCK))
+    solvers["mixed_fgcr_learned"].update({"train_seconds": train_s, "train_pairs": 64, "epochs": 12,
+                                          "loss_first": float(hist[0]), "loss_last": float(hist[-1])})
+    plain = dict(solvers["plain_fp64_bicgstab"], value=solvers["plain_fp64_bicgstab"]["rhs_per_s"], unit="RHS/s",
+                 sample="full-operator perambulator of one source timeslice (128 RHS), BiCGStab entirely in FP64")
+    mixed_same = solvers["mixed_fp32_bicgstab"]["rhs_per_s"]
 
     # ---- dslash roofline of the dominant kernel (FP32 hopping + inverse clover, RHS block)
     dsl = {}
@@ -332,7 +354,8 @@ def run_ours(args, rank, world):
                       "l2": "working set > L2 (126 MB): 64-RHS spinor batches of 25-50 MB each, links+clover "
                             "and ~10 vectors per batch live at once", "parallelism": "rhs-sharded x%d" % world},
            "e2e": e2e, "plain_fp64": plain, "mixed_same_sample_rhs_per_s": mixed_same,
-           "speedup_vs_plain": mixed_same / plain["value"], "dslash": dsl, "roofline": roofline,
+           "speedup_vs_plain": mixed_same / plain["value"], "solvers": solvers, "tuning": tuning,
+           "dslash": dsl, "roofline": roofline,
            "clocks": clk.summary(), "gpu_launches": launches, "eigensolve_s": t_eig,
            "solver_stats": {"full_iters_per_step": stats["full"][-1][0], "dom_iters_per_step": stats["dom"][-1][0],
                             "max_true_resid": max(x[1] for x in stats["full"] + stats["dom"]),

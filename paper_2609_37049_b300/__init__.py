@@ -7,5 +7,6 @@ fails loudly if it has not been built (``python -m paper_2609_37049_b300.build``
 """
 from . import lqcd  # noqa: F401  (loads liblqcd.so)
 from .lqcd import Context, Stats, default_params, LqcdError  # noqa: F401
+from . import autotune  # noqa: F401
 
-__all__ = ["lqcd", "Context", "Stats", "default_params", "LqcdError"]
+__all__ = ["lqcd", "autotune", "Context", "Stats", "default_params", "LqcdError"]

@@ -1,0 +1,73 @@
+"""Autotuner for the batched solver: threads per block of the dslash launches and the RHS block
+width (right-hand sides solved in lockstep per launch), persisted in a JSON cache keyed by
+lattice extents, GPU name and precision.
+
+    from paper_2609_37049_b300 import Context, autotune
+    choice = autotune.tune(ctx, cache="tuning.json")     # times once, then reads the cache
+    params.rhs_block = choice["rhs_block"]
+
+The RHS block is chosen from the measured dslash time per right-hand side (the solver's cost is
+dominated by the Schur-operator dslash pair; wider blocks share the link and clover loads), among
+widths whose work vectors fit a memory budget.
+"""
+import json
+import os
+
+from . import lqcd
+
+CANDIDATE_BLOCKS = (16, 32, 64, 128)
+
+
+def _gpu_name():
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:
+        return "unknown"
+
+
+def _key(ctx):
+    return "%s|%s" % ("x".join(str(d) for d in ctx.dims), _gpu_name())
+
+
+def _spinor_bytes(ctx, prec, nrhs):
+    per = {lqcd.LQCD_PREC_F64: 16, lqcd.LQCD_PREC_F32: 8, lqcd.LQCD_PREC_F16: 4}[prec]
+    return ctx.volume // 2 * nrhs * 12 * per
+
+
+def tune(ctx, cache=None, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F16, lqcd.LQCD_PREC_F64),
+         blocks=CANDIDATE_BLOCKS, memory_budget=64 << 30, retune=False):
+    """Tune (or load from `cache`) and install the launch choices on ctx; returns the choice dict."""
+    db = {}
+    if cache and os.path.exists(cache) and not retune:
+        with open(cache) as f:
+            db = json.load(f)
+    key = _key(ctx)
+    if key in db:
+        choice = db[key]
+        for prec, per_n in choice["threads"].items():
+            for n, t in per_n.items():
+                ctx.set_dslash_threads(int(prec), int(n), int(t))
+        return choice
+    threads, per_rhs = {}, {}
+    for prec in precisions:
+        threads[str(prec)] = {}
+        for n in blocks:
+            # about 20 work vectors of the inner precision per batch plus FP64 outer vectors
+            need = 20 * _spinor_bytes(ctx, prec, n) + 8 * _spinor_bytes(ctx, lqcd.LQCD_PREC_F64, n)
+            if need > memory_budget:
+                continue
+            t, ms = ctx.tune_dslash(prec, n)
+            threads[str(prec)][str(n)] = t
+            if prec == lqcd.LQCD_PREC_F32:
+                per_rhs[n] = ms / n
+    best = min(per_rhs, key=per_rhs.get) if per_rhs else 64
+    choice = {"threads": threads, "rhs_block": int(best),
+              "dslash_ms_per_rhs_f32": {str(k): v for k, v in per_rhs.items()}}
+    if cache:
+        db[key] = choice
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return choice

@@ -735,6 +735,60 @@ int lqcd_disc_correlator(lqcd_ctx* c, const double* L, const double* Lt, const d
 
 }  // extern "C"
 
+extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_threads, double* best_ms) {
+  if (!c || nrhs < 1 || !best_threads || !best_ms ||
+      (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
+    return set_error(c, LQCD_ERR_INVALID_ARG, "tune_dslash: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "tune_dslash: no gauge field uploaded");
+  const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);
+  const Geom& g = c->g;
+  const size_t sb = spinor_bytes(g, P, nrhs);
+  void* in = ws_get(c, "bench_in", sb);
+  void* out = ws_get(c, "bench_out", sb);
+  if (!in || !out) return set_error(c, LQCD_ERR_OOM, "tune_dslash: OOM");
+  Scope sc(c);
+  cudaMemsetAsync(in, 0, sb, c->work);
+  const void* U = P == P64 ? c->U64 : (P == P32 ? c->U32 : c->U16);
+  const void* Ainv = P == P64 ? c->Ainv64 : (P == P32 ? c->Ainv32 : c->Ainv16);
+  DslashCall k{P, EPI_CH, 0, in, nullptr, nullptr, out, U, (const char*)Ainv + clover_bytes(g, P), 1, nrhs, 0.0, 1.0,
+               c->d_tc_full};
+  k.coord = coord_of(c, 1);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e30;
+  int bt = 128;
+  for (int tpb : {64, 128, 256}) {
+    launch_dslash(g, k, c->work, tpb);
+    cudaEventRecord(e0, c->work);
+    for (int i = 0; i < 5; i++) launch_dslash(g, k, c->work, tpb);
+    cudaEventRecord(e1, c->work);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / 5 < best) {
+      best = ms / 5;
+      bt = tpb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (int e = cuda_check(c, "tune_dslash")) return e;
+  c->tuned_threads[(long)P * 100000 + nrhs] = bt;
+  *best_threads = bt;
+  *best_ms = best;
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_set_dslash_threads(lqcd_ctx* c, int prec, int nrhs, int threads) {
+  if (!c || nrhs < 1 || (threads != 64 && threads != 128 && threads != 256) ||
+      (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
+    return set_error(c, LQCD_ERR_INVALID_ARG, "set_dslash_threads: bad arguments");
+  const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);
+  c->tuned_threads[(long)P * 100000 + nrhs] = threads;
+  return LQCD_OK;
+}
+
 extern "C" int lqcd_nn_num_weights(void) { return nn_total_weights(); }
 
 extern "C" int lqcd_nn_set_weights(lqcd_ctx* c, const float* w) {

@@ -33,7 +33,7 @@ EXPORTED = [
     "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
     "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
-    "lqcd_nn_loss_grad", "lqcd_nn_train",
+    "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_threads",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -43,6 +43,18 @@ def nn_flatten(Ws):
     """Network weights [W_l (9, C_out, C_in) complex] -> flat float32 (re, im) array of the C ABI."""
     return np.ascontiguousarray(np.concatenate([np.asarray(W, dtype=np.complex64).ravel() for W in Ws]).view(
         np.float32))
+
+
+def nn_initial_weights(seed, scale=0.05):
+    """Starting weights for training: the identity on the path-0 channel block plus small
+    seeded Gaussian complex noise on every path (numpy; layers [9, C_out, C_in])."""
+    rng = np.random.default_rng(seed)
+    Ws = []
+    for cin, cout in zip(NN_WIDTHS[:-1], NN_WIDTHS[1:]):
+        W = scale * (rng.normal(size=(9, cout, cin)) + 1j * rng.normal(size=(9, cout, cin)))
+        W[0] += np.eye(cout, cin)
+        Ws.append(W)
+    return Ws
 
 
 def nn_unflatten(flat):
@@ -110,6 +122,8 @@ def load_library(path=_LIB_PATH):
         "lqcd_disc_correlator_noalloc": (ip, [vp, vp, vp, vp, ip, ip, ip, vp, ip, vp, vp, vp, vp, vp, vp, vp, vp,
                                               vp]),
         "lqcd_phase_times": (ip, [vp, ctypes.c_char_p, ip, ip]),
+        "lqcd_tune_dslash": (ip, [vp, ip, ip, c_int_p, ctypes.POINTER(ctypes.c_double)]),
+        "lqcd_set_dslash_threads": (ip, [vp, ip, ip, ip]),
         "lqcd_nn_num_weights": (ip, []),
         "lqcd_nn_set_weights": (ip, [vp, vp]),
         "lqcd_nn_get_weights": (ip, [vp, vp]),
@@ -282,6 +296,15 @@ class Context:
             self.h, _ptr(L), _ptr(Lt), _ptr(Ld), _ptr(Ltd), n_cfg, n_g, int(vev), _ptr(out["C"]),
             _ptr(out["Cdd"]), _ptr(out["dC"]), _ptr(out["C_avg"]), _ptr(out["dC_avg"]),
             _ptr(out["valid"], np.int32), _ptr(out["n_valid"], np.int32), _ptr(terms), w))
+
+    # ---- autotuning
+    def tune_dslash(self, prec, nrhs):
+        bt, ms = ctypes.c_int(), ctypes.c_double()
+        self._check(_lib.lqcd_tune_dslash(self.h, int(prec), int(nrhs), ctypes.byref(bt), ctypes.byref(ms)))
+        return bt.value, ms.value
+
+    def set_dslash_threads(self, prec, nrhs, threads):
+        return self._check(_lib.lqcd_set_dslash_threads(self.h, int(prec), int(nrhs), int(threads)))
 
     # ---- learned preconditioner
     def nn_set_weights(self, Ws):
