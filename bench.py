@@ -222,9 +222,11 @@ def run_ours(args, rank, world):
     corr["n_valid"] = torch.zeros(T, dtype=torch.int32, device="cuda")
     stats = {"full": [], "dom": []}
 
+    from paper_2609_37049_b300.shard import source_groups, units_for_step
+    groups = source_groups(T, EXTENTS)
+
     def step(s):
-        g = (s * world + rank) % EXTENTS[0]
-        t_src = [g + EXTENTS[0] * k for k in range(n_grp)]
+        t_src = units_for_step(groups, s, rank, world)
         for mode, tau, L, Lt, key in ((lqcd.LQCD_MODE_FULL, tau_f, loopsF, loopsFt, "full"),
                                       (lqcd.LQCD_MODE_DOMAIN, tau_d, loopsD, loopsDt, "dom")):
             st = Stats(1, 1)
@@ -266,8 +268,7 @@ def run_ours(args, rank, world):
     npy = lambda t: t.numpy()
 
     def step_e2e(s):
-        g = (s * world + rank) % EXTENTS[0]
-        t_src = [g + EXTENTS[0] * k for k in range(n_grp)]
+        t_src = units_for_step(groups, s, rank, world)
         ctx.gauge_upload(npy(U_h), KAPPA, CSW)
         for mode, (L, Lt) in ((lqcd.LQCD_MODE_FULL, lF_h[:2]), (lqcd.LQCD_MODE_DOMAIN, lF_h[2:])):
             ctx.perambulator(npy(V_h), N_EV, t_src, npy(tau_h), mode=mode, params=params)

@@ -1,0 +1,48 @@
+"""Work partition across ranks (one process per GPU).
+
+The distillation path shards without any exchange during the solves: a unit of work is a source
+group, i.e. one source timeslice per domain (t = g, g + e_0, ... for the tiling of the time axis),
+whose full-operator and domain-operator perambulators and loops are independent of every other
+group.  Units are dealt round-robin to ranks; the only collective is a gather of the per-group
+loops (a few kilobytes) to the rank that forms the correlators.
+"""
+import numpy as np
+
+
+def source_groups(Lt, extents):
+    """Source groups of a tiling of [0, Lt): group g holds t0(d) + g for every domain d wide enough,
+    g = 0 .. max(extents) - 1 (domains narrower than g + 1 drop out of group g)."""
+    extents = [int(e) for e in extents]
+    if sum(extents) != Lt or min(extents) < 1:
+        raise ValueError("extents must tile the time axis")
+    starts = np.cumsum([0] + extents[:-1])
+    return [[int(s + g) for s, e in zip(starts, extents) if g < e] for g in range(max(extents))]
+
+
+def shard(units, rank, world):
+    """Units of this rank: round-robin over the list."""
+    if not 0 <= rank < world:
+        raise ValueError("rank out of range")
+    return list(units)[rank::world]
+
+
+def units_for_step(units, step, rank, world):
+    """The unit a rank processes in bench step `step` (weak scaling: every rank one unit per step)."""
+    return units[(step * world + rank) % len(units)]
+
+
+def gather_loops(local, rank, world, dist=None):
+    """Gather {t: loop values} dictionaries of all ranks on every rank (torch.distributed object
+    gather; the identity when world == 1).  Raises if two ranks produced the same timeslice."""
+    if world == 1 or dist is None:
+        merged = dict(local)
+    else:
+        parts = [None] * world
+        dist.all_gather_object(parts, dict(local))
+        merged = {}
+        for p in parts:
+            for t, v in p.items():
+                if t in merged:
+                    raise RuntimeError("timeslice %d computed by two ranks" % t)
+                merged[t] = v
+    return dict(sorted(merged.items()))

@@ -1,0 +1,86 @@
+"""Multi-rank host logic with two gloo ranks on CPU: every source group is processed exactly once
+across ranks, and the gathered loops equal a single-process run (units are independent)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from paper_2609_37049_b300.shard import source_groups, shard, gather_loops, units_for_step
+
+
+def fake_loops(group):
+    """Stand-in for the per-group GPU work: deterministic values per timeslice."""
+    return {t: np.array([np.sin(t + 0.5), np.cos(3 * t)]) for t in group}
+
+
+def _worker(rank, world, port, groups, out_q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local = {}
+    for g in shard(groups, rank, world):
+        local.update(fake_loops(g))
+    merged = gather_loops(local, rank, world, dist)
+    if rank == 0:
+        out_q.put({t: v.tolist() for t, v in merged.items()})
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def test_source_groups_tile_every_timeslice_once():
+    for Lt, ext in ((32, [4] * 8), (48, [6, 8, 10, 6, 8, 10]), (8, [4, 4]), (8, [8])):
+        groups = source_groups(Lt, ext)
+        flat = sorted(t for g in groups for t in g)
+        assert flat == list(range(Lt))
+        starts = np.cumsum([0] + ext[:-1])
+        dom = np.repeat(np.arange(len(ext)), ext)
+        for g in groups:
+            assert len({int(dom[t]) for t in g}) == len(g)  # at most one timeslice per domain
+    with pytest.raises(ValueError):
+        source_groups(8, [4, 3])
+
+
+def test_units_for_step_cover_all_units_across_ranks():
+    units = source_groups(32, [4] * 8)
+    seen = [units_for_step(units, s, r, 2) for s in range(2) for r in range(2)]
+    assert sorted(map(tuple, seen)) == sorted(map(tuple, units))
+
+
+def test_two_gloo_ranks_gather_equals_single_process():
+    groups = source_groups(48, [6, 8, 10, 6, 8, 10])
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, groups, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    single = {}
+    for g in groups:
+        single.update(fake_loops(g))
+    assert sorted(int(t) for t in got) == list(range(48))
+    for t, v in single.items():
+        assert np.allclose(got[t], v)
+
+
+def test_duplicate_timeslice_is_an_error():
+    class FakeDist:
+        def all_gather_object(self, parts, obj):
+            parts[0] = {1: 1.0}
+            parts[1] = {1: 2.0}
+    with pytest.raises(RuntimeError):
+        gather_loops({1: 1.0}, 0, 2, FakeDist())
