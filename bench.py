@@ -54,12 +54,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-dslash", action="store_true",
                     help="only time the dslash kernels of the workload (small command for ncu captures)")
+    ap.add_argument("--dslash-variant", type=int, default=-1,
+                    help="with --profile-dslash: time only this launch variant (default: all)")
     return ap.parse_args()
 
 
-def profile_dslash():
+def profile_dslash(only_variant=-1):
     """The FP32 / FP16 / FP64 even-odd hopping + inverse-clover kernels of the workload, a few
-    launches each, L2 flushed between launches (inputs: 64-RHS FP32 batch = 400 MB > L2)."""
+    launches each per launch variant (register cap 128 / 80 / 64 per thread; FP64 has only the
+    first), L2 flushed between launches (inputs: 64-RHS FP32 batch = 400 MB > L2)."""
     import torch
     from lqcd_inputs import gauge_field
     from paper_2609_37049_b300 import Context, lqcd
@@ -69,8 +72,12 @@ def profile_dslash():
     out = {}
     for name, prec, nrhs in (("f32", lqcd.LQCD_PREC_F32, RHS_BLOCK), ("f16", lqcd.LQCD_PREC_F16, RHS_BLOCK),
                              ("f64", lqcd.LQCD_PREC_F64, 8)):
-        ms, by = ctx.dslash_bench(prec, nrhs, 3, True)
-        out[name] = {"nrhs": nrhs, "ms": ms, "GBs": by / ms / 1e6, "algo_bytes": by}
+        for v in ((0,) if prec == lqcd.LQCD_PREC_F64 else (0, 1, 2)):
+            if only_variant >= 0 and v != only_variant:
+                continue
+            ctx.set_dslash_variant(prec, nrhs, v)
+            ms, by = ctx.dslash_bench(prec, nrhs, 3, True)
+            out["%s_v%d" % (name, v)] = {"nrhs": nrhs, "ms": ms, "GBs": by / ms / 1e6, "algo_bytes": by}
     print(json.dumps(out), flush=True)
 
 
@@ -422,7 +429,7 @@ def dist_max(x, world):
 def main():
     args = parse()
     if args.profile_dslash:
-        profile_dslash()
+        profile_dslash(args.dslash_variant)
         return
     rank, world = dist_init()
     if args.impl == "reference":

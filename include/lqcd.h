@@ -246,12 +246,12 @@ int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, 
                   double* loss_hist);
 
 /* Autotuning of the dslash launch: time the hopping kernel of precision prec on nrhs right-hand
- * sides with 64, 128 and 256 threads per block and keep the fastest for this context (used by
- * every later launch of that precision and RHS count outside the fused-reduction kernels, whose
- * block shape is fixed by the reduction).  lqcd_set_dslash_threads installs a known choice
- * (e.g. from a cache) without timing.  Errors: INVALID_ARG, STATE (no gauge field). */
-int lqcd_tune_dslash(lqcd_ctx* ctx, int prec, int nrhs, int* best_threads, double* best_ms);
-int lqcd_set_dslash_threads(lqcd_ctx* ctx, int prec, int nrhs, int threads);
+ * sides in its compiled variants (register caps of 128 / 80 / 64 per thread, i.e. 4 / 6 / 8
+ * resident 128-thread blocks per SM; FP64 has one) and keep the fastest for this context; every
+ * later dslash launch of that precision and RHS count uses it.  lqcd_set_dslash_variant installs
+ * a known choice (e.g. from a cache) without timing.  Errors: INVALID_ARG, STATE (no gauge). */
+int lqcd_tune_dslash(lqcd_ctx* ctx, int prec, int nrhs, int* best_variant, double* best_ms);
+int lqcd_set_dslash_variant(lqcd_ctx* ctx, int prec, int nrhs, int variant);
 
 /* Per-phase GPU time of this context's calls (prepare, inner Krylov, reconstruct, FP64 true
  * residual, sources, projection, ...) as a JSON object {"phase": milliseconds, ...} written to

@@ -1,4 +1,4 @@
-"""Autotuner for the batched solver: threads per block of the dslash launches and the RHS block
+"""Autotuner for the batched solver: the dslash launch variant (register cap / resident blocks) and the RHS block
 width (right-hand sides solved in lockstep per launch), persisted in a JSON cache keyed by
 lattice extents, GPU name and precision.
 
@@ -45,24 +45,24 @@ def tune(ctx, cache=None, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F16, lq
     key = _key(ctx)
     if key in db:
         choice = db[key]
-        for prec, per_n in choice["threads"].items():
-            for n, t in per_n.items():
-                ctx.set_dslash_threads(int(prec), int(n), int(t))
+        for prec, per_n in choice["variant"].items():
+            for n, v in per_n.items():
+                ctx.set_dslash_variant(int(prec), int(n), int(v))
         return choice
-    threads, per_rhs = {}, {}
+    variants, per_rhs = {}, {}
     for prec in precisions:
-        threads[str(prec)] = {}
+        variants[str(prec)] = {}
         for n in blocks:
             # about 20 work vectors of the inner precision per batch plus FP64 outer vectors
             need = 20 * _spinor_bytes(ctx, prec, n) + 8 * _spinor_bytes(ctx, lqcd.LQCD_PREC_F64, n)
             if need > memory_budget:
                 continue
             t, ms = ctx.tune_dslash(prec, n)
-            threads[str(prec)][str(n)] = t
+            variants[str(prec)][str(n)] = t
             if prec == lqcd.LQCD_PREC_F32:
                 per_rhs[n] = ms / n
     best = min(per_rhs, key=per_rhs.get) if per_rhs else 64
-    choice = {"threads": threads, "rhs_block": int(best),
+    choice = {"variant": variants, "rhs_block": int(best),
               "dslash_ms_per_rhs_f32": {str(k): v for k, v in per_rhs.items()}}
     if cache:
         db[key] = choice

@@ -735,8 +735,8 @@ int lqcd_disc_correlator(lqcd_ctx* c, const double* L, const double* Lt, const d
 
 }  // extern "C"
 
-extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_threads, double* best_ms) {
-  if (!c || nrhs < 1 || !best_threads || !best_ms ||
+extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_variant, double* best_ms) {
+  if (!c || nrhs < 1 || !best_variant || !best_ms ||
       (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
     return set_error(c, LQCD_ERR_INVALID_ARG, "tune_dslash: bad arguments");
   if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "tune_dslash: no gauge field uploaded");
@@ -757,35 +757,36 @@ extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_threa
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = 1e30;
-  int bt = 128;
-  for (int tpb : {64, 128, 256}) {
-    launch_dslash(g, k, c->work, tpb);
+  int bt = 0;
+  const int nvar = P == P64 ? 1 : 3;  // FP64 has one variant (ALU bound)
+  for (int var = 0; var < nvar; var++) {
+    launch_dslash(g, k, c->work, var);
     cudaEventRecord(e0, c->work);
-    for (int i = 0; i < 5; i++) launch_dslash(g, k, c->work, tpb);
+    for (int i = 0; i < 5; i++) launch_dslash(g, k, c->work, var);
     cudaEventRecord(e1, c->work);
     cudaEventSynchronize(e1);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms / 5 < best) {
       best = ms / 5;
-      bt = tpb;
+      bt = var;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (int e = cuda_check(c, "tune_dslash")) return e;
-  c->tuned_threads[(long)P * 100000 + nrhs] = bt;
-  *best_threads = bt;
+  c->tuned_variant[(long)P * 100000 + nrhs] = bt;
+  *best_variant = bt;
   *best_ms = best;
   return LQCD_OK;
 }
 
-extern "C" int lqcd_set_dslash_threads(lqcd_ctx* c, int prec, int nrhs, int threads) {
-  if (!c || nrhs < 1 || (threads != 64 && threads != 128 && threads != 256) ||
+extern "C" int lqcd_set_dslash_variant(lqcd_ctx* c, int prec, int nrhs, int variant) {
+  if (!c || nrhs < 1 || variant < 0 || variant > 2 ||
       (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
-    return set_error(c, LQCD_ERR_INVALID_ARG, "set_dslash_threads: bad arguments");
+    return set_error(c, LQCD_ERR_INVALID_ARG, "set_dslash_variant: bad arguments");
   const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);
-  c->tuned_threads[(long)P * 100000 + nrhs] = threads;
+  c->tuned_variant[(long)P * 100000 + nrhs] = variant;
   return LQCD_OK;
 }
 
@@ -914,11 +915,11 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
   const void* Ao = (const char*)Ainv + clover_bytes(g, P);
   DslashCall k{P, EPI_CH, 0, in, nullptr, nullptr, out, U, Ao, 1, nrhs, 0.0, 1.0, c->d_tc_full};
   k.coord = coord_of(c, 1);
-  int threads = 0;
-  auto it = c->tuned_threads.find((long)P * 100000 + nrhs);
-  if (it != c->tuned_threads.end()) threads = it->second;
+  int variant = 0;
+  auto it = c->tuned_variant.find((long)P * 100000 + nrhs);
+  if (it != c->tuned_variant.end()) variant = it->second;
   // warm-up
-  launch_dslash(g, k, c->work, threads);
+  launch_dslash(g, k, c->work, variant);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -929,7 +930,7 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
       lqcd::count_launch();
     }
     cudaEventRecord(e0, c->work);
-    launch_dslash(g, k, c->work, threads);
+    launch_dslash(g, k, c->work, variant);
     cudaEventRecord(e1, c->work);
     cudaEventSynchronize(e1);
     float ms = 0;

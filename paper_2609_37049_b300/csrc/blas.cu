@@ -17,7 +17,7 @@ VGeom make_vgeom(const Geom& g, int nrhs, int npar) {
   v.g = g;
   v.nrhs = nrhs;
   v.npar = npar;
-  int target = 256 / nrhs;
+  int target = 128 / nrhs;  // blocks of at most 128 threads (the dslash launch bound)
   if (target < 1) target = 1;
   int S = 1;
   while (S * 2 <= target && (g.Vth % (S * 2)) == 0) S *= 2;

@@ -148,8 +148,10 @@ LQCD_D void hop_dir(const DslashParams& pr, long cb, long s, int cmu, int Lmu, l
   }
 }
 
-template <int P, int EPI, bool DAG, int RED>
-__global__ void __launch_bounds__(256) dslash_kernel(const DslashParams pr) {
+// MINB: minimum resident blocks of 128 threads the compiler must allow (register cap 128 / 80 / 64
+// per thread for MINB = 4 / 6 / 8); the autotuner picks the variant per precision and RHS count.
+template <int P, int EPI, bool DAG, int RED, int MINB>
+__global__ void __launch_bounds__(128, MINB) dslash_kernel(const DslashParams pr) {
   using R = typename Traits<P>::real;
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long cb = tid / pr.nrhs;
@@ -241,45 +243,57 @@ __global__ void clover_only_kernel(const void* C, const void* in, void* out, lon
   store_spinor<P>(out, stride, tid, s);
 }
 
-template <int P, int EPI, int RED>
-static void launch_p_e(const DslashParams& pr, bool dag, long blocks, int tpb, size_t shm, cudaStream_t st) {
+template <int P, int EPI, int RED, int MINB>
+static void launch_v(const DslashParams& pr, bool dag, long blocks, int tpb, size_t shm, cudaStream_t st) {
   if (dag)
-    dslash_kernel<P, EPI, true, RED><<<blocks, tpb, shm, st>>>(pr);
+    dslash_kernel<P, EPI, true, RED, MINB><<<blocks, tpb, shm, st>>>(pr);
   else
-    dslash_kernel<P, EPI, false, RED><<<blocks, tpb, shm, st>>>(pr);
+    dslash_kernel<P, EPI, false, RED, MINB><<<blocks, tpb, shm, st>>>(pr);
   lqcd::count_launch();
 }
 
+template <int P, int EPI, int RED>
+static void launch_p_e(const DslashParams& pr, bool dag, long blocks, int tpb, size_t shm, int variant,
+                       cudaStream_t st) {
+  // register-capped variants only where the kernel is not FP64-ALU bound
+  if constexpr (P != P64) {
+    if (variant == 1) return launch_v<P, EPI, RED, 6>(pr, dag, blocks, tpb, shm, st);
+    if (variant == 2) return launch_v<P, EPI, RED, 8>(pr, dag, blocks, tpb, shm, st);
+  }
+  launch_v<P, EPI, RED, 4>(pr, dag, blocks, tpb, shm, st);
+}
+
 template <int P, int RED>
-static void launch_p(const DslashParams& pr, int epi, bool dag, long blocks, int tpb, size_t shm, cudaStream_t st) {
+static void launch_p(const DslashParams& pr, int epi, bool dag, long blocks, int tpb, size_t shm, int variant,
+                     cudaStream_t st) {
   if constexpr (RED == RED_NONE) {
     switch (epi) {
-      case EPI_H: launch_p_e<P, EPI_H, RED>(pr, dag, blocks, tpb, shm, st); break;
-      case EPI_CH: launch_p_e<P, EPI_CH, RED>(pr, dag, blocks, tpb, shm, st); break;
-      case EPI_Y_H: launch_p_e<P, EPI_Y_H, RED>(pr, dag, blocks, tpb, shm, st); break;
-      case EPI_Y_CH: launch_p_e<P, EPI_Y_CH, RED>(pr, dag, blocks, tpb, shm, st); break;
-      case EPI_C_YH: launch_p_e<P, EPI_C_YH, RED>(pr, dag, blocks, tpb, shm, st); break;
-      case EPI_CY_H: launch_p_e<P, EPI_CY_H, RED>(pr, dag, blocks, tpb, shm, st); break;
-      default: launch_p_e<P, EPI_RES, RED>(pr, dag, blocks, tpb, shm, st); break;
+      case EPI_H: launch_p_e<P, EPI_H, RED>(pr, dag, blocks, tpb, shm, variant, st); break;
+      case EPI_CH: launch_p_e<P, EPI_CH, RED>(pr, dag, blocks, tpb, shm, variant, st); break;
+      case EPI_Y_H: launch_p_e<P, EPI_Y_H, RED>(pr, dag, blocks, tpb, shm, variant, st); break;
+      case EPI_Y_CH: launch_p_e<P, EPI_Y_CH, RED>(pr, dag, blocks, tpb, shm, variant, st); break;
+      case EPI_C_YH: launch_p_e<P, EPI_C_YH, RED>(pr, dag, blocks, tpb, shm, variant, st); break;
+      case EPI_CY_H: launch_p_e<P, EPI_CY_H, RED>(pr, dag, blocks, tpb, shm, variant, st); break;
+      default: launch_p_e<P, EPI_RES, RED>(pr, dag, blocks, tpb, shm, variant, st); break;
     }
   } else {
     // fused reductions are used by the Schur operator's second half only
-    launch_p_e<P, EPI_Y_CH, RED>(pr, dag, blocks, tpb, shm, st);
+    launch_p_e<P, EPI_Y_CH, RED>(pr, dag, blocks, tpb, shm, variant, st);
   }
 }
 
 template <int RED>
 static void launch_prec(int prec, const DslashParams& pr, int epi, bool dag, long blocks, int tpb, size_t shm,
-                        cudaStream_t st) {
+                        int variant, cudaStream_t st) {
   if (prec == P64)
-    launch_p<P64, RED>(pr, epi, dag, blocks, tpb, shm, st);
+    launch_p<P64, RED>(pr, epi, dag, blocks, tpb, shm, variant, st);
   else if (prec == P32)
-    launch_p<P32, RED>(pr, epi, dag, blocks, tpb, shm, st);
+    launch_p<P32, RED>(pr, epi, dag, blocks, tpb, shm, variant, st);
   else
-    launch_p<P16, RED>(pr, epi, dag, blocks, tpb, shm, st);
+    launch_p<P16, RED>(pr, epi, dag, blocks, tpb, shm, variant, st);
 }
 
-void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int threads) {
+void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int variant) {
   DslashParams pr;
   pr.g = g;
   pr.in = c.in;
@@ -298,20 +312,21 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int thre
   pr.a = c.a;
   pr.b = c.b;
   const bool dag = c.dagger != 0;
+  if (variant < 0 || variant > 2) variant = 0;
   if (c.red == RED_NONE) {
     long nthreads = g.Vh * (long)c.nrhs;
-    int tpb = threads > 0 ? threads : 128;
-    launch_prec<RED_NONE>(c.prec, pr, c.epi, dag, (nthreads + tpb - 1) / tpb, tpb, 0, st);
+    const int tpb = 128;
+    launch_prec<RED_NONE>(c.prec, pr, c.epi, dag, (nthreads + tpb - 1) / tpb, tpb, 0, variant, st);
   } else {
-    // one block = red_sites sites (inside one timeslice) x nrhs right-hand sides
+    // one block = red_sites sites (inside one timeslice) x nrhs right-hand sides (<= 128 threads)
     const int tpb = c.red_sites * c.nrhs;
     const long blocks = g.Vh / c.red_sites;
     const int nd = c.red == RED_DOT_Z ? 2 : 3;
     const size_t shm = (size_t)nd * tpb * sizeof(double);
     if (c.red == RED_DOT_Z)
-      launch_prec<RED_DOT_Z>(c.prec, pr, c.epi, dag, blocks, tpb, shm, st);
+      launch_prec<RED_DOT_Z>(c.prec, pr, c.epi, dag, blocks, tpb, shm, variant, st);
     else
-      launch_prec<RED_DOT_Y_NORM>(c.prec, pr, c.epi, dag, blocks, tpb, shm, st);
+      launch_prec<RED_DOT_Y_NORM>(c.prec, pr, c.epi, dag, blocks, tpb, shm, variant, st);
   }
 }
 

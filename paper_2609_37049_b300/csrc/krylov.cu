@@ -66,14 +66,14 @@ static void schur(lqcd_ctx* c, const Inner& in, const void* src, void* dst, int 
                   cudaStream_t st) {
   DslashCall k1 = call(c, in.prec, EPI_CH, src, nullptr, nullptr, in.tmp, in.U, in.Ainv_o, 1, in.nrhs, 0.0, 1.0,
                        in.tc);
-  launch_dslash(c->g, k1, st, in.threads);
+  launch_dslash(c->g, k1, st, in.variant);
   DslashCall k2 = call(c, in.prec, EPI_Y_CH, in.tmp, src, nullptr, dst, in.U, in.Ainv_e, 0, in.nrhs, 1.0,
                        -in.kappa * in.kappa, in.tc);
   k2.red = red;
   k2.zred = zred;
   k2.partial = in.partial;
   k2.red_sites = in.vg.S;
-  launch_dslash(c->g, k2, st, in.threads);
+  launch_dslash(c->g, k2, st, in.variant);
 }
 
 static void bicg_iteration(lqcd_ctx* c, const Inner& in, cudaStream_t st) {
@@ -90,7 +90,7 @@ static void bicg_iteration(lqcd_ctx* c, const Inner& in, cudaStream_t st) {
 static std::string graph_key(const Inner& in, int chunk) {
   char buf[512];
   snprintf(buf, sizeof buf, "bicg:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p", in.prec, in.nrhs, in.nseg,
-           chunk, in.threads, in.b, in.x, in.r, in.p, in.v, in.s, in.t, in.tmp, (void*)in.ks.rho, in.partial,
+           chunk, in.variant, in.b, in.x, in.r, in.p, in.v, in.s, in.t, in.tmp, (void*)in.ks.rho, in.partial,
            (const void*)in.tc, (const void*)in.si, in.U);
   return buf;
 }
@@ -273,7 +273,7 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
 
   VGeom vgF = make_vgeom(g, nrhs, 2);  // full lattice
   VGeom vgH = make_vgeom(g, nrhs, 1);  // one parity
-  if (vgH.threads() > 256) return set_error(c, LQCD_ERR_INVALID_ARG, "solve: rhs_block > 256");
+  if (vgH.threads() > 128) return set_error(c, LQCD_ERR_INVALID_ARG, "solve: rhs_block > 128");
   const size_t sb64 = spinor_bytes(g, P64, nrhs), sbP = spinor_bytes(g, P, nrhs);
   const size_t cbP = clover_bytes(g, P);
 
@@ -314,10 +314,10 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   in.t = ws_get(c, "i_t", sbP);
   in.tmp = ws_get(c, "i_tmp", sbP);
   in.kappa = c->kappa;
-  in.threads = 0;
+  in.variant = 0;
   {
-    auto it = c->tuned_threads.find((long)P * 100000 + nrhs);
-    if (it != c->tuned_threads.end()) in.threads = it->second;
+    auto it = c->tuned_variant.find((long)P * 100000 + nrhs);
+    if (it != c->tuned_variant.end()) in.variant = it->second;
   }
   char* ksb = (char*)ws_get(c, "kstate", (size_t)nsys * (4 * 16 + 3 * 8 + 3 * 4) + 64);
   in.ks.count = (int*)ws_get(c, "kcount", 64);
@@ -371,6 +371,8 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
       const size_t sb16 = spinor_bytes(g, P16, nrhs);
       f.in16 = in;
       f.in16.prec = P16;
+      auto tv = c->tuned_variant.find((long)P16 * 100000 + nrhs);
+      f.in16.variant = tv != c->tuned_variant.end() ? tv->second : 0;
       f.in16.U = c->U16;
       f.in16.Ainv_e = off(c->Ainv16, clover_bytes(g, P16), 0);
       f.in16.Ainv_o = off(c->Ainv16, clover_bytes(g, P16), 1);
@@ -406,7 +408,7 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
       launch_clover_only(g, P, in.Ainv_o, off(rin, sbP, 1), in.tmp, nrhs, st);
       DslashCall kp = call(c, P, EPI_C_YH, in.tmp, off(rin, sbP, 0), nullptr, bhat, in.U, in.Ainv_e, 0, nrhs, 1.0,
                            c->kappa, tc);
-      launch_dslash(g, kp, st, in.threads);
+      launch_dslash(g, kp, st, in.variant);
       bs.dslash += 1;
     }
     if (use_gcr) {  // inner flexible GCR (FP32) with the FP16 MR or network preconditioner
@@ -422,7 +424,7 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
       PhaseTimer pt(c, "reconstruct");
       DslashCall kr = call(c, P, EPI_C_YH, in.x, off(rin, sbP, 1), nullptr, off(ein, sbP, 1), in.U, in.Ainv_o, 1,
                            nrhs, 1.0, c->kappa, tc);
-      launch_dslash(g, kr, st, in.threads);
+      launch_dslash(g, kr, st, in.variant);
       bs.dslash += 1;
       recip(scale, iscale, nsys, st);
       v_axpy_mixed(P, x, ein, vgF, si, nseg, iscale, oact, st);

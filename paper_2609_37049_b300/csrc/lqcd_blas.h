@@ -74,7 +74,7 @@ struct Inner {
   KState ks;
   double* partial;
   double kappa;
-  int threads;
+  int variant;  // dslash launch variant (register cap)
 };
 
 // ---- gauge-covariant network preconditioner (nn.cu)

@@ -90,7 +90,8 @@ struct DslashCall {
   int red_sites = 0;
 };
 
-void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int threads = 0);
+// variant: register cap of the FP32 / FP16 kernels (0: 128, 1: 80, 2: 64 registers per thread)
+void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int variant = 0);
 void launch_clover_only(const Geom& g, int prec, const void* C, const void* in, void* out, int nrhs,
                         cudaStream_t st);
 
@@ -132,7 +133,7 @@ struct lqcd_ctx {
   std::string err;
   int device = 0;
   // autotuned threads per block for the dslash, keyed by prec * 100000 + nrhs
-  std::map<long, int> tuned_threads;
+  std::map<long, int> tuned_variant;
   // instantiated CUDA graphs of Krylov iteration chunks, keyed by buffers and shape
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<cudaGraphExec_t, long long> graph_kernels;  // kernel nodes per instantiated graph

@@ -33,7 +33,7 @@ EXPORTED = [
     "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
     "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
-    "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_threads",
+    "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -123,7 +123,7 @@ def load_library(path=_LIB_PATH):
                                               vp]),
         "lqcd_phase_times": (ip, [vp, ctypes.c_char_p, ip, ip]),
         "lqcd_tune_dslash": (ip, [vp, ip, ip, c_int_p, ctypes.POINTER(ctypes.c_double)]),
-        "lqcd_set_dslash_threads": (ip, [vp, ip, ip, ip]),
+        "lqcd_set_dslash_variant": (ip, [vp, ip, ip, ip]),
         "lqcd_nn_num_weights": (ip, []),
         "lqcd_nn_set_weights": (ip, [vp, vp]),
         "lqcd_nn_get_weights": (ip, [vp, vp]),
@@ -303,8 +303,8 @@ class Context:
         self._check(_lib.lqcd_tune_dslash(self.h, int(prec), int(nrhs), ctypes.byref(bt), ctypes.byref(ms)))
         return bt.value, ms.value
 
-    def set_dslash_threads(self, prec, nrhs, threads):
-        return self._check(_lib.lqcd_set_dslash_threads(self.h, int(prec), int(nrhs), int(threads)))
+    def set_dslash_variant(self, prec, nrhs, variant):
+        return self._check(_lib.lqcd_set_dslash_variant(self.h, int(prec), int(nrhs), int(variant)))
 
     # ---- learned preconditioner
     def nn_set_weights(self, Ws):

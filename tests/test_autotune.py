@@ -13,10 +13,10 @@ class FakeCtx:
 
     def tune_dslash(self, prec, n):
         self.timed.append((prec, n))
-        return (256 if n >= 64 else 128), 0.01 * n ** 0.8  # wider blocks: cheaper per RHS
+        return (2 if n >= 64 else 0), 0.01 * n ** 0.8  # wider blocks: cheaper per RHS
 
-    def set_dslash_threads(self, prec, n, t):
-        self.installed.append((prec, n, t))
+    def set_dslash_variant(self, prec, n, v):
+        self.installed.append((prec, n, v))
 
 
 def test_tune_writes_cache_and_reload_installs_it(tmp_path):
@@ -28,7 +28,7 @@ def test_tune_writes_cache_and_reload_installs_it(tmp_path):
     assert len(db) == 1
     c2 = FakeCtx()
     ch2 = autotune.tune(c2, cache=cache)
-    assert ch2 == ch and c2.timed == [] and (lqcd.LQCD_PREC_F32, 64, 256) in c2.installed
+    assert ch2 == ch and c2.timed == [] and (lqcd.LQCD_PREC_F32, 64, 2) in c2.installed
 
 
 def test_memory_budget_excludes_wide_blocks(tmp_path):
