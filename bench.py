@@ -61,8 +61,10 @@ def parse():
 
 def profile_dslash(only_variant=-1):
     """The FP32 / FP16 / FP64 even-odd hopping + inverse-clover kernels of the workload, a few
-    launches each per launch variant (register cap 128 / 80 / 64 per thread; FP64 has only the
-    first), L2 flushed between launches (inputs: 64-RHS FP32 batch = 400 MB > L2)."""
+    launches each per launch variant (0-2: direct loads, register cap 128 / 80 / 64 per thread;
+    3-5: neighbour spinors staged by bulk copies 2 / 3 / 4 hops ahead; FP64: 0-2 with register
+    caps 128 / 255 / 168),
+    L2 flushed between launches (inputs: 64-RHS FP32 batch = 400 MB > L2)."""
     import torch
     from lqcd_inputs import gauge_field
     from paper_2609_37049_b300 import Context, lqcd
@@ -72,7 +74,7 @@ def profile_dslash(only_variant=-1):
     out = {}
     for name, prec, nrhs in (("f32", lqcd.LQCD_PREC_F32, RHS_BLOCK), ("f16", lqcd.LQCD_PREC_F16, RHS_BLOCK),
                              ("f64", lqcd.LQCD_PREC_F64, 8)):
-        for v in ((0,) if prec == lqcd.LQCD_PREC_F64 else (0, 1, 2)):
+        for v in (range(3) if prec == lqcd.LQCD_PREC_F64 else range(6)):
             if only_variant >= 0 and v != only_variant:
                 continue
             ctx.set_dslash_variant(prec, nrhs, v)
@@ -359,8 +361,8 @@ def run_ours(args, rank, world):
                       "lattice": "16^3x32", "eps": EPS, "kappa": KAPPA, "c_sw": CSW, "n_ev": N_EV,
                       "domains": "8 x 4", "rhs_per_step": rhs_per_step, "rhs_block": RHS_BLOCK,
                       "sources": "lowest Laplacian eigenvectors (GPU eigensolver)",
-                      "l2": "working set > L2 (126 MB): 64-RHS spinor batches of 25-50 MB each, links+clover "
-                            "and ~10 vectors per batch live at once", "parallelism": "rhs-sharded x%d" % world},
+                      "l2": "inputs larger than L2 (126 MB): each 64-RHS FP32 half-lattice batch vector is "
+                            "403 MB and each FP64 full-lattice one 1.6 GB", "parallelism": "rhs-sharded x%d" % world},
            "e2e": e2e, "plain_fp64": plain, "mixed_same_sample_rhs_per_s": mixed_same,
            "speedup_vs_plain": mixed_same / plain["value"], "solvers": solvers, "tuning": tuning,
            "dslash": dsl, "roofline": roofline,

@@ -758,7 +758,7 @@ extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_varia
   cudaEventCreate(&e1);
   double best = 1e30;
   int bt = 0;
-  const int nvar = P == P64 ? 1 : 3;  // FP64 has one variant (ALU bound)
+  const int nvar = P == P64 ? 3 : 6;  // the staged variants 3-5 are FP32 / FP16 only
   for (int var = 0; var < nvar; var++) {
     launch_dslash(g, k, c->work, var);
     cudaEventRecord(e0, c->work);
@@ -775,6 +775,8 @@ extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_varia
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (int e = cuda_check(c, "tune_dslash")) return e;
+  if (dslash_pipe_timeouts(true))
+    return set_error(c, LQCD_ERR_TIMEOUT, "tune_dslash: a staged dslash copy did not complete within its wait limit");
   c->tuned_variant[(long)P * 100000 + nrhs] = bt;
   *best_variant = bt;
   *best_ms = best;
@@ -782,7 +784,7 @@ extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_varia
 }
 
 extern "C" int lqcd_set_dslash_variant(lqcd_ctx* c, int prec, int nrhs, int variant) {
-  if (!c || nrhs < 1 || variant < 0 || variant > 2 ||
+  if (!c || nrhs < 1 || variant < 0 || variant > 5 ||
       (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
     return set_error(c, LQCD_ERR_INVALID_ARG, "set_dslash_variant: bad arguments");
   const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);

@@ -396,6 +396,8 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   bs.dslash = 0;
   int total_iters = 0;
   const size_t cb64 = clover_bytes(g, P64);
+  const auto tv64 = c->tuned_variant.find((long)P64 * 100000 + nrhs);
+  const int v64 = tv64 != c->tuned_variant.end() ? tv64->second : 0;  // FP64 residual launch variant
   for (int cyc = 0; cyc < max_outer; cyc++) {
     count_active(oact, nsys, in.ks.count, st);
     cudaMemcpyAsync(count_host, in.ks.count, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -434,7 +436,7 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
       for (int p = 0; p < 2; p++) {
         DslashCall k = call(c, P64, EPI_RES, off(x, sb64, 1 - p), off(x, sb64, p), off(b, sb64, p),
                             off(r64, sb64, p), c->U64, off(c->A64, cb64, p), p, nrhs, 1.0, -c->kappa, tc);
-        launch_dslash(g, k, st);
+        launch_dslash(g, k, st, v64);
       }
       bs.dslash += 2;
       v_norm2(P64, r64, vgF, si, nseg, partial, r2, st);
@@ -447,6 +449,8 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   cudaMemcpyAsync(bs.iters.data(), in.ks.iters, nsys * sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e));
+  if (dslash_pipe_timeouts(true))
+    return set_error(c, LQCD_ERR_TIMEOUT, "solve: a staged dslash copy did not complete within its wait limit");
   flush_phase_times(c);
   for (int i = 0; i < nsys; i++) {
     if (!std::isfinite(bs.rel[i])) return set_error(c, LQCD_ERR_NAN, "solve: non-finite residual");

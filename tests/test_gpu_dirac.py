@@ -126,3 +126,37 @@ def test_not_converged_reports_partial_result():
                    allow_not_converged=True)
     assert rc == lqcd.LQCD_ERR_NOT_CONVERGED
     assert 1e-10 < st.max_true_resid < 1.0
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_dslash_launch_variants_agree(prec):
+    """Every dslash launch variant (register caps; neighbour spinors staged by bulk copies) runs the
+    same arithmetic in the same order: the mixed solves take the same iterations and agree to
+    round-off, and each reaches the oracle's true residual.  32 RHS so the staged kernel applies."""
+    case = ROUGH
+    U = gauge(case, 77)
+    op = WilsonClover(U, case["kappa"], case["c_sw"])
+    ext = case["extents"]
+    nrhs = 32
+    b = random_spinors(case["dims"], nrhs, 13)
+    ctx = Context(case["dims"])
+    ctx.gauge_upload(U, case["kappa"], case["c_sw"])
+    ctx.set_domains(ext)
+    p = lqcd.LQCD_PREC_F32 if prec == "f32" else lqcd.LQCD_PREC_F16
+    params = default_params(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=p, rhs_block=nrhs)
+    for domain in (False, True):
+        ref_op = op.restricted(ext) if domain else op
+        ref = None
+        for v in range(6):
+            ctx.set_dslash_variant(p, nrhs, v)
+            ctx.set_dslash_variant(lqcd.LQCD_PREC_F64, nrhs, v % 3)  # the FP64 true-residual launches
+            x = np.zeros_like(b)
+            st = Stats(nrhs, len(ext) if domain else 1)
+            ctx.solve(b, x, params, domain=domain, stats=st)
+            res = per_domain_resid(b, b - ref_op.apply(x), ext if domain else [case["dims"][3]])
+            assert res.max() <= 1.02e-10, (v, res.max())
+            if ref is None:
+                ref = (x.copy(), st.iters.copy())
+            else:
+                assert np.array_equal(st.iters, ref[1]), (v, st.iters, ref[1])
+                assert np.linalg.norm(x - ref[0]) / np.linalg.norm(ref[0]) < 1e-12, v
