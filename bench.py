@@ -83,6 +83,25 @@ def profile_dslash(only_variant=-1):
     print(json.dumps(out), flush=True)
 
 
+def captured_traffic(variant):
+    """DRAM bytes per launch of the FP32 dslash from the committed ncu summary, or None when the
+    kernel sources changed since the capture or the tuned variant is not the captured one."""
+    import hashlib
+    import re
+    h = hashlib.sha1()
+    for f in ("dslash.cu", "dslash_ops.cuh", "lqcd_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_37049_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    try:
+        with open(os.path.join(ROOT, "profiles", "dslash_f32_16x16x16x32_nrhs64.md")) as fh:
+            m = re.search(r"roofline-traffic: bytes=(\d+) variant=(\d+) sources=([0-9a-f]+)", fh.read())
+    except OSError:
+        return None
+    if not m or m.group(3) != h.hexdigest() or int(m.group(2)) != int(variant):
+        return None
+    return int(m.group(1))
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -345,13 +364,7 @@ def run_ours(args, rank, world):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "dslash_kernel<P32,EPI_CH> (eo hopping + A^-1, %d RHS)" % RHS_BLOCK,
                 "peak_kind": peak_kind}
-    prof = os.path.join(ROOT, "profiles", "dslash_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                roofline["traffic"] = json.load(f).get("traffic_per_launch")
-        except Exception:
-            pass
+    roofline["traffic"] = captured_traffic(tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(RHS_BLOCK), 0))
 
     res = {"metric": "distillation RHS/s at FP64 resid 1e-10 (mixed FP64/FP32 solver)", "value": value,
            "unit": "RHS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
