@@ -62,8 +62,8 @@ def parse():
 def profile_dslash(only_variant=-1):
     """The FP32 / FP16 / FP64 even-odd hopping + inverse-clover kernels of the workload, a few
     launches each per launch variant (0-2: direct loads, register cap 128 / 80 / 64 per thread;
-    3-5: neighbour spinors staged by bulk copies 2 / 3 / 4 hops ahead; FP64: 0-2 with register
-    caps 128 / 255 / 168),
+    3-4: links and clover staged once per site in shared memory; 5: neighbour spinors staged by
+    bulk copies; FP64: 0-2 with register caps 128 / 255 / 168),
     L2 flushed between launches (inputs: 64-RHS FP32 batch = 400 MB > L2)."""
     import torch
     from lqcd_inputs import gauge_field

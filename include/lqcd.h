@@ -130,6 +130,18 @@ int lqcd_set_domains(lqcd_ctx* ctx, const int* extents, int n_dom);
 int lqcd_dirac_apply(lqcd_ctx* ctx, const double* in, double* out, int nrhs, int domain_restricted,
                      int where);
 
+/* The even-odd preconditioned operator the solvers iterate on, in the storage precision prec
+ * (LQCD_PREC_F64 / F32 / F16; the dslash launch variant tuned for prec and nrhs):
+ *   out_e = M in_e,  M = 1 - kappa^2 A_ee^{-1} H_eo A_oo^{-1} H_oe   (D = A - kappa H, Sec. 3),
+ * with the domain cuts of D_Lambda when domain_restricted = 1.  in / out: [nrhs][V][4][3] complex
+ * (lexicographic, as lqcd_dirac_apply); the odd sites of in are ignored and those of out are set
+ * to zero.  FP32 / FP16 round in to the storage precision and compute in FP32.  Not an operation
+ * of the paper's method itself: the Schur complement is the solvers' internal operator, exposed
+ * for verification of the reduced-precision kernels.  Errors: INVALID_ARG (NULL, nrhs < 1, bad
+ * prec), STATE (no gauge field), OOM, TIMEOUT (staged launch variant). */
+int lqcd_schur_apply(lqcd_ctx* ctx, int prec, const double* in, double* out, int nrhs, int domain_restricted,
+                     int where);
+
 /* Solve D x = b (full) or D_Lambda x = b (domain; every domain of every RHS converged to tol
  * relative to its own source norm) for nrhs right-hand sides; x is overwritten.  Returns
  * NOT_CONVERGED (x holds the last iterate, stats filled) if tol is not reached. */
@@ -248,10 +260,11 @@ int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, 
 /* Autotuning of the dslash launch: time the hopping kernel of precision prec on nrhs right-hand
  * sides in its compiled variants and keep the fastest for this context; every later dslash launch
  * of that precision and RHS count uses it.  Variants 0 / 1 / 2: direct loads with register caps
- * of 128 / 80 / 64 per thread (4 / 6 / 8 resident 128-thread blocks per SM); 3 / 4 / 5: the
- * neighbour spinors staged in shared memory by bulk asynchronous copies 2 / 3 / 4 hops ahead
- * (FP32 and FP16 with nrhs a multiple of 32; elsewhere they run as variant 0).  FP64 has variants
- * 0 / 1 / 2 with register caps 128 / 255 / 168.  All variants compute the same arithmetic in the
+ * of 128 / 80 / 64 per thread (4 / 6 / 8 resident 128-thread blocks per SM); 3 / 4: links rebuilt
+ * and clover copied once per site into shared memory, register caps 128 / 80 (FP32 and FP16, nrhs
+ * a power of two in [16, 128]); 5: the neighbour spinors staged in shared memory by bulk
+ * asynchronous copies 3 hops ahead (FP32 and FP16, nrhs a multiple of 32).  Where a variant does
+ * not apply it runs as variant 0.  FP64 has variants 0 / 1 / 2 with register caps 128 / 255 / 168.  All variants compute the same arithmetic in the
  * same order.  lqcd_set_dslash_variant
  * installs a known choice (e.g. from a cache) without timing.  Errors: INVALID_ARG (variant
  * outside 0..5), STATE (no gauge), TIMEOUT (a staged copy did not complete within its wait

@@ -491,6 +491,29 @@ int lqcd_dirac_apply(lqcd_ctx* c, const double* in, double* out, int nrhs, int d
   return finish_out(c, out, dout, bytes, where);
 }
 
+int lqcd_schur_apply(lqcd_ctx* c, int prec, const double* in, double* out, int nrhs, int domain, int where) {
+  if (!c || !in || !out || nrhs < 1 ||
+      (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
+    return set_error(c, LQCD_ERR_INVALID_ARG, "schur_apply: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "schur_apply: no gauge field uploaded");
+  const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);
+  Scope sc(c);
+  const size_t bytes = (size_t)c->V * 12 * nrhs * sizeof(double2);
+  const double2* din = (const double2*)stage_in(c, in, bytes, where, "h_in");
+  double2* dout = (double2*)stage_out(c, out, bytes, where, "h_out");
+  double2* ein = (double2*)ws_get(c, "eo_in", bytes);
+  double2* eout = (double2*)ws_get(c, "eo_out", bytes);
+  if (!din || !dout || !ein || !eout) return set_error(c, LQCD_ERR_OOM, "schur_apply: out of device memory");
+  pack_spinor(c->g, din, ein, nrhs, c->work);
+  cudaMemsetAsync((char*)eout + bytes / 2, 0, bytes / 2, c->work);  // odd parity block
+  if (int e = schur_apply(c, P, ein, eout, nrhs, domain, c->work)) return e;
+  unpack_spinor(c->g, eout, dout, nrhs, c->work);
+  if (int e = cuda_check(c, "schur_apply")) return e;
+  if (dslash_pipe_timeouts(true))
+    return set_error(c, LQCD_ERR_TIMEOUT, "schur_apply: a staged dslash copy did not complete within its wait limit");
+  return finish_out(c, out, dout, bytes, where);
+}
+
 static int solve_common(lqcd_ctx* c, const double* b, double* x, int nrhs, int where, const lqcd_solve_params* p,
                         lqcd_solve_stats* st, int domain) {
   if (!c || !b || !x || nrhs < 1) return set_error(c, LQCD_ERR_INVALID_ARG, "solve: bad arguments");

@@ -18,9 +18,10 @@ namespace lqcd {
 // MINB: minimum resident blocks of 128 threads the compiler must allow (register cap 255 / 168 /
 // 128 / 80 / 64 per thread for MINB = 2 / 3 / 4 / 6 / 8).  Launch variants 0-2 are this kernel
 // with MINB 4 / 6 / 8 (FP64: 4 / 2 / 3);
-// variants 3-5 are the staged kernel of dslash_pipe.cu (staging depth 2 / 3 / 4 hops) where it
-// applies (FP32 / FP16, nrhs a multiple of 32, the solver's epilogues), else variant 0.  The
-// autotuner picks the variant per precision and RHS count.
+// variants 3-5 are the staged kernels of dslash_staged.cu (3 / 4: links and clover staged once
+// per site in shared memory, register caps 128 / 80; 5: neighbour spinors staged by bulk copies)
+// where they apply (FP32 / FP16, the solver's epilogues, RHS counts as stated there), else
+// variant 0.  The autotuner picks the variant per precision and RHS count.
 template <int P, int EPI, bool DAG, int RED, int MINB>
 __global__ void __launch_bounds__(128, MINB) dslash_kernel(const DslashParams pr) {
   using R = typename Traits<P>::real;
@@ -138,8 +139,8 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int vari
     long nthreads = g.Vh * (long)c.nrhs;
     const int tpb = 128;
     const long blocks = (nthreads + tpb - 1) / tpb;
-    if (variant >= 3) {  // neighbour spinors staged by bulk copies (dslash_pipe.cu), where it applies
-      if (launch_dslash_pipe(pr, c.prec, c.epi, dag, RED_NONE, blocks, tpb, 0, variant, st)) return;
+    if (variant >= 3) {  // staged kernels (dslash_staged.cu), where they apply
+      if (launch_dslash_staged(pr, c.prec, c.epi, dag, RED_NONE, blocks, tpb, 0, variant, st)) return;
       variant = 0;
     }
     launch_prec<RED_NONE>(c.prec, pr, c.epi, dag, blocks, tpb, 0, variant, st);
@@ -150,7 +151,7 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int vari
     const int nd = c.red == RED_DOT_Z ? 2 : 3;
     const size_t shm = (size_t)nd * tpb * sizeof(double);
     if (variant >= 3) {
-      if (launch_dslash_pipe(pr, c.prec, c.epi, dag, c.red, blocks, tpb, shm, variant, st)) return;
+      if (launch_dslash_staged(pr, c.prec, c.epi, dag, c.red, blocks, tpb, shm, variant, st)) return;
       variant = 0;
     }
     if (c.red == RED_DOT_Z)

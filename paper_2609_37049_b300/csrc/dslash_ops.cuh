@@ -1,5 +1,5 @@
-// Building blocks of the even-odd dslash kernels (dslash.cu: direct loads; dslash_pipe.cu:
-// neighbour spinors staged in shared memory by bulk asynchronous copies): kernel parameters, spin
+// Building blocks of the even-odd dslash kernels (dslash.cu: direct loads; dslash_staged.cu:
+// links, clover or neighbour spinors staged in shared memory): kernel parameters, spin
 // projection and reconstruction for the chiral basis, SU(3) products, and the fused epilogue.
 #pragma once
 #include "lqcd_internal.h"
@@ -170,11 +170,34 @@ LQCD_D void hop_one(const DslashParams& pr, long cb, long nb, int coef, const cp
 // Epilogue shared by the dslash kernels: combine the hopping sum acc of site cb / right-hand side
 // rhs with the clover term and the y / z inputs as EPI says, store it, and form the fused partial
 // sums.  `idx` = cb * nrhs + rhs, `stride` = Vh * nrhs (the chunk stride of a spinor field).
-template <int P, int EPI, int RED>
-LQCD_D void dslash_epilogue(const DslashParams& pr, long cb, long idx, long stride, int rhs,
-                            cplx<typename Traits<P>::real> (&acc)[12]) {
+// The site's clover block (both chiralities) applied to s in place: from global memory, or (SC)
+// from the block's shared-memory copy sc = 18 float4 (chirality-major, packed as in global).
+template <int P, bool SC>
+LQCD_D void clover_site(const DslashParams& pr, long cb, const float4* sc, cplx<typename Traits<P>::real> (&s)[12]) {
   using R = typename Traits<P>::real;
-  const Geom& g = pr.g;
+  if constexpr (SC) {
+#pragma unroll
+    for (int ch = 0; ch < 2; ch++) {
+      R r[36];
+#pragma unroll
+      for (int c = 0; c < 9; c++) {
+        const float4 v = sc[ch * 9 + c];
+        r[4 * c] = v.x; r[4 * c + 1] = v.y; r[4 * c + 2] = v.z; r[4 * c + 3] = v.w;
+      }
+      cplx<R> y[6];
+      herm6_apply<R>(r, &s[6 * ch], y);
+#pragma unroll
+      for (int i = 0; i < 6; i++) s[6 * ch + i] = y[i];
+    }
+  } else {
+    clover_apply<P>(pr.C, pr.g.Vh, cb, s);
+  }
+}
+
+template <int P, int EPI, int RED, bool SC = false>
+LQCD_D void dslash_epilogue(const DslashParams& pr, long cb, long idx, long stride, int rhs,
+                            cplx<typename Traits<P>::real> (&acc)[12], const float4* sc = nullptr) {
+  using R = typename Traits<P>::real;
   const R a = (R)pr.a, b = (R)pr.b;
   cplx<R> o[12];
   cplx<R> yv[12];
@@ -182,11 +205,11 @@ LQCD_D void dslash_epilogue(const DslashParams& pr, long cb, long idx, long stri
 #pragma unroll
     for (int k = 0; k < 12; k++) o[k] = b * acc[k];
   } else if constexpr (EPI == EPI_CH) {
-    clover_apply<P>(pr.C, g.Vh, cb, acc);
+    clover_site<P, SC>(pr, cb, sc, acc);
 #pragma unroll
     for (int k = 0; k < 12; k++) o[k] = b * acc[k];
   } else if constexpr (EPI == EPI_Y_H || EPI == EPI_Y_CH) {
-    if constexpr (EPI == EPI_Y_CH) clover_apply<P>(pr.C, g.Vh, cb, acc);
+    if constexpr (EPI == EPI_Y_CH) clover_site<P, SC>(pr, cb, sc, acc);
     load_spinor<P>(pr.y, stride, idx, yv);
 #pragma unroll
     for (int k = 0; k < 12; k++) o[k] = a * yv[k] + b * acc[k];
@@ -194,16 +217,16 @@ LQCD_D void dslash_epilogue(const DslashParams& pr, long cb, long idx, long stri
     load_spinor<P>(pr.y, stride, idx, yv);
 #pragma unroll
     for (int k = 0; k < 12; k++) o[k] = a * yv[k] + b * acc[k];
-    clover_apply<P>(pr.C, g.Vh, cb, o);
+    clover_site<P, SC>(pr, cb, sc, o);
   } else if constexpr (EPI == EPI_CY_H) {
     load_spinor<P>(pr.y, stride, idx, yv);
-    clover_apply<P>(pr.C, g.Vh, cb, yv);
+    clover_site<P, SC>(pr, cb, sc, yv);
 #pragma unroll
     for (int k = 0; k < 12; k++) o[k] = a * yv[k] + b * acc[k];
   } else {  // EPI_RES: z - (C y + b H x)
     cplx<R> zv[12];
     load_spinor<P>(pr.y, stride, idx, yv);
-    clover_apply<P>(pr.C, g.Vh, cb, yv);
+    clover_site<P, SC>(pr, cb, sc, yv);
     load_spinor<P>(pr.z, stride, idx, zv);
 #pragma unroll
     for (int k = 0; k < 12; k++) o[k] = zv[k] - (yv[k] + b * acc[k]);
@@ -231,9 +254,9 @@ LQCD_D void dslash_epilogue(const DslashParams& pr, long cb, long idx, long stri
   }
 }
 
-// dslash_pipe.cu: launch the staged kernel for launch variant 3-5; false (nothing launched) where
+// dslash_staged.cu: launch the staged kernel of launch variant 3-5; false (nothing launched) where
 // it does not apply.  red_shm = dynamic shared memory of the fused reduction.
-bool launch_dslash_pipe(const DslashParams& pr, int prec, int epi, bool dag, int red, long blocks, int tpb,
-                        size_t red_shm, int variant, cudaStream_t st);
+bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, int red, long blocks, int tpb,
+                          size_t red_shm, int variant, cudaStream_t st);
 
 }  // namespace lqcd

@@ -76,6 +76,38 @@ static void schur(lqcd_ctx* c, const Inner& in, const void* src, void* dst, int 
   launch_dslash(c->g, k2, st, in.variant);
 }
 
+// y_e = M x_e for one parity block of FP64 even-odd fields (x64, y64: [chunk][cb][rhs] of the
+// even parity), computed in storage precision P with the tuned launch variant.
+int schur_apply(lqcd_ctx* c, int P, const void* x64, void* y64, int nrhs, int domain, cudaStream_t st) {
+  const Geom& g = c->g;
+  const VGeom vgH = make_vgeom(g, nrhs, 1);
+  const size_t sbP = spinor_bytes(g, P, nrhs);
+  const void* xin = x64;
+  void* out = y64;
+  if (P != P64) {
+    void* xp = ws_get(c, "sa_in", sbP);
+    out = ws_get(c, "sa_out", sbP);
+    if (!xp || !out) return set_error(c, LQCD_ERR_OOM, "schur_apply: out of device memory");
+    v_convert(P64, P, x64, xp, vgH, c->d_seg_full, 1, nullptr, st);
+    xin = xp;
+  }
+  void* tmp = ws_get(c, "sa_tmp", sbP);
+  if (!tmp) return set_error(c, LQCD_ERR_OOM, "schur_apply: out of device memory");
+  const void* U = P == P64 ? c->U64 : (P == P32 ? c->U32 : c->U16);
+  const void* Ainv = P == P64 ? c->Ainv64 : (P == P32 ? c->Ainv32 : c->Ainv16);
+  const size_t cbP = clover_bytes(g, P);
+  const signed char* tc = domain ? c->d_tc_dom : c->d_tc_full;
+  const auto tv = c->tuned_variant.find((long)P * 100000 + nrhs);
+  const int variant = tv != c->tuned_variant.end() ? tv->second : 0;
+  DslashCall k1 = call(c, P, EPI_CH, xin, nullptr, nullptr, tmp, U, off(Ainv, cbP, 1), 1, nrhs, 0.0, 1.0, tc);
+  launch_dslash(g, k1, st, variant);
+  DslashCall k2 = call(c, P, EPI_Y_CH, tmp, xin, nullptr, out, U, off(Ainv, cbP, 0), 0, nrhs, 1.0,
+                       -c->kappa * c->kappa, tc);
+  launch_dslash(g, k2, st, variant);
+  if (P != P64) v_convert(P, P64, out, y64, vgH, c->d_seg_full, 1, nullptr, st);
+  return LQCD_OK;
+}
+
 static void bicg_iteration(lqcd_ctx* c, const Inner& in, cudaStream_t st) {
   const int P = in.prec;
   schur(c, in, in.p, in.v, RED_DOT_Z, in.b, st);  // v = M p, partial (r0, v)

@@ -92,6 +92,8 @@ struct DslashCall {
 
 // variant: register cap of the FP32 / FP16 kernels (0: 128, 1: 80, 2: 64 registers per thread)
 void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int variant = 0);
+// y_e = M x_e (even-odd Schur operator) on FP64 even-parity blocks, in storage precision P
+int schur_apply(lqcd_ctx* c, int P, const void* x64, void* y64, int nrhs, int domain, cudaStream_t st);
 // waits of the staged dslash kernel that ran out of their iteration limit since the last reset
 unsigned long long dslash_pipe_timeouts(bool reset);
 void launch_clover_only(const Geom& g, int prec, const void* C, const void* in, void* out, int nrhs,

@@ -33,7 +33,7 @@ EXPORTED = [
     "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
     "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
-    "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant",
+    "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant", "lqcd_schur_apply",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -108,6 +108,7 @@ def load_library(path=_LIB_PATH):
         "lqcd_gauge_upload": (ip, [vp, vp, ip, ctypes.c_double, ctypes.c_double]),
         "lqcd_set_domains": (ip, [vp, c_int_p, ip]),
         "lqcd_dirac_apply": (ip, [vp, vp, vp, ip, ip, ip]),
+        "lqcd_schur_apply": (ip, [vp, ip, vp, vp, ip, ip, ip]),
         "lqcd_solve_full": (ip, [vp, vp, vp, ip, ip, ctypes.POINTER(lqcd_solve_params),
                                  ctypes.POINTER(lqcd_solve_stats)]),
         "lqcd_solve_domain": (ip, [vp, vp, vp, ip, ip, ctypes.POINTER(lqcd_solve_params),
@@ -260,6 +261,12 @@ class Context:
         nrhs = psi.shape[0]
         return self._check(_lib.lqcd_dirac_apply(self.h, _ptr(psi), _ptr(out), nrhs, int(domain_restricted),
                                                  _where(psi, out)))
+
+    def schur_apply(self, prec, psi, out, domain_restricted=False):
+        """out_e = M psi_e, the even-odd Schur operator in storage precision prec (odd sites of out = 0)."""
+        nrhs = psi.shape[0]
+        return self._check(_lib.lqcd_schur_apply(self.h, int(prec), _ptr(psi), _ptr(out), nrhs,
+                                                 int(domain_restricted), _where(psi, out)))
 
     def solve(self, b, x, params=None, domain=False, stats=None, allow_not_converged=False):
         nrhs = b.shape[0]

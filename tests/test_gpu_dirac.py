@@ -128,16 +128,18 @@ def test_not_converged_reports_partial_result():
     assert 1e-10 < st.max_true_resid < 1.0
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16"])
-def test_dslash_launch_variants_agree(prec):
-    """Every dslash launch variant (register caps; neighbour spinors staged by bulk copies) runs the
-    same arithmetic in the same order: the mixed solves take the same iterations and agree to
-    round-off, and each reaches the oracle's true residual.  32 RHS so the staged kernel applies."""
+@pytest.mark.parametrize("prec,nrhs", [("f32", 16), ("f32", 32), ("f16", 32)])
+def test_dslash_launch_variants_agree(prec, nrhs):
+    """Every dslash launch variant (register caps; links and clover staged per site in shared
+    memory; neighbour spinors staged by bulk copies) computes the same operator up to FP32
+    rounding (the compiler may contract the same expressions differently): each mixed solve
+    reaches the oracle's true residual, takes within two iterations of variant 0 per RHS, and
+    agrees with it within the solves' accuracy.  16 RHS = 8 sites per staged block; 32 RHS also
+    runs the bulk-copy kernel."""
     case = ROUGH
     U = gauge(case, 77)
     op = WilsonClover(U, case["kappa"], case["c_sw"])
     ext = case["extents"]
-    nrhs = 32
     b = random_spinors(case["dims"], nrhs, 13)
     ctx = Context(case["dims"])
     ctx.gauge_upload(U, case["kappa"], case["c_sw"])
@@ -158,5 +160,50 @@ def test_dslash_launch_variants_agree(prec):
             if ref is None:
                 ref = (x.copy(), st.iters.copy())
             else:
-                assert np.array_equal(st.iters, ref[1]), (v, st.iters, ref[1])
-                assert np.linalg.norm(x - ref[0]) / np.linalg.norm(ref[0]) < 1e-12, v
+                assert np.abs(st.iters - ref[1]).max() <= 2, (v, st.iters, ref[1])
+                assert np.linalg.norm(x - ref[0]) / np.linalg.norm(ref[0]) < 1e-8, v
+
+
+def oracle_schur(op, x):
+    """M x_e = x_e - kappa^2 A_ee^-1 H_eo A_oo^-1 H_oe x_e from the oracle's pieces (even sites)."""
+    from oracle.dirac import apply_site_matrix, hopping, parity_table
+    Lx, Ly, Lz, Lt = op.dims
+    par = parity_table(op.dims).reshape(Lt, Lz, Ly, Lx)
+    even = (par == 0)[..., None, None]
+    odd = (par == 1)[..., None, None]
+    Ainv = np.linalg.inv(op.A)
+    xe = x * even
+    z = apply_site_matrix(Ainv, hopping(op.Ue, xe) * odd) * odd
+    return xe - op.kappa ** 2 * apply_site_matrix(Ainv, hopping(op.Ue, z) * even) * even
+
+
+# storage precision -> (launch variants, max relative error against the FP64 oracle)
+SCHUR_PRECS = {"f64": (range(3), 1e-13), "f32": (range(6), 2e-6), "f16": (range(6), 4e-3)}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("nrhs", [3, 16, 32])
+@pytest.mark.parametrize("domain", [False, True])
+def test_schur_operator_parity(prec, nrhs, domain):
+    """The solvers' even-odd operator in each storage precision and launch variant, element by
+    element against the oracle (FP32 / FP16 bounds: storage rounding of inputs, links and clover
+    plus FP32 arithmetic).  nrhs 3 runs every variant as the direct kernel; 16 / 32 the staged
+    kernels (8 / 4 sites per block; 32 also the bulk-copy kernel)."""
+    case = ROUGH
+    U = gauge(case, 555)
+    op = WilsonClover(U, case["kappa"], case["c_sw"])
+    ext = case["extents"]
+    ref_op = op.restricted(ext) if domain else op
+    x = random_spinors(case["dims"], nrhs, 21)
+    ref = oracle_schur(ref_op, x)
+    ctx = Context(case["dims"])
+    ctx.gauge_upload(U, case["kappa"], case["c_sw"])
+    ctx.set_domains(ext)
+    p = {"f64": lqcd.LQCD_PREC_F64, "f32": lqcd.LQCD_PREC_F32, "f16": lqcd.LQCD_PREC_F16}[prec]
+    variants, tol = SCHUR_PRECS[prec]
+    for v in variants:
+        ctx.set_dslash_variant(p, nrhs, v)
+        out = np.zeros_like(x)
+        ctx.schur_apply(p, x, out, domain_restricted=domain)
+        err = rel_max(out, ref)
+        assert err < tol, (prec, v, err)
