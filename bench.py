@@ -62,7 +62,7 @@ def parse():
 def profile_dslash(only_variant=-1):
     """The FP32 / FP16 / FP64 even-odd hopping + inverse-clover kernels of the workload, a few
     launches each per launch variant (0-2: direct loads, register cap 128 / 80 / 64 per thread;
-    3-4: links and clover staged once per site in shared memory; 5: neighbour spinors staged by
+    3: links and clover staged once per site in shared memory; 4: neighbour spinors staged by
     bulk copies; FP64: 0-2 with register caps 128 / 255 / 168),
     L2 flushed between launches (inputs: 64-RHS FP32 batch = 400 MB > L2)."""
     import torch
@@ -74,7 +74,7 @@ def profile_dslash(only_variant=-1):
     out = {}
     for name, prec, nrhs in (("f32", lqcd.LQCD_PREC_F32, RHS_BLOCK), ("f16", lqcd.LQCD_PREC_F16, RHS_BLOCK),
                              ("f64", lqcd.LQCD_PREC_F64, 8)):
-        for v in (range(3) if prec == lqcd.LQCD_PREC_F64 else range(6)):
+        for v in (range(3) if prec == lqcd.LQCD_PREC_F64 else range(5)):
             if only_variant >= 0 and v != only_variant:
                 continue
             ctx.set_dslash_variant(prec, nrhs, v)
@@ -89,7 +89,7 @@ def captured_traffic(variant):
     import hashlib
     import re
     h = hashlib.sha1()
-    for f in ("dslash.cu", "dslash_ops.cuh", "lqcd_common.cuh"):
+    for f in ("dslash.cu", "dslash_ops.cuh", "dslash_staged.cu", "lqcd_common.cuh"):
         with open(os.path.join(ROOT, "paper_2609_37049_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     try:
@@ -361,10 +361,12 @@ def run_ours(args, rank, world):
         ms_l, by = ctx.dslash_bench(prec, RHS_BLOCK if prec != lqcd.LQCD_PREC_F64 else 8, 20, True)
         dsl[name] = {"ms": ms_l, "GBs": by / ms_l / 1e6, "bytes": by}
     achieved = dsl["f32"]["GBs"]
+    v32 = int(tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(RHS_BLOCK), 0))
+    kname = {3: "dslash_sl_kernel", 4: "dslash_pipe_kernel"}.get(v32, "dslash_kernel")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "dslash_kernel<P32,EPI_CH> (eo hopping + A^-1, %d RHS)" % RHS_BLOCK,
-                "peak_kind": peak_kind}
-    roofline["traffic"] = captured_traffic(tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(RHS_BLOCK), 0))
+                "traffic": captured_traffic(v32), "peak_kind": peak_kind,
+                "kernel": "%s<P32,EPI_CH> (launch variant %d: eo hopping + A^-1, %d RHS)" % (kname, v32, RHS_BLOCK),
+                "algo_bytes_per_launch": dsl["f32"]["bytes"]}
 
     res = {"metric": "distillation RHS/s at FP64 resid 1e-10 (mixed FP64/FP32 solver)", "value": value,
            "unit": "RHS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -260,14 +260,14 @@ int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, 
 /* Autotuning of the dslash launch: time the hopping kernel of precision prec on nrhs right-hand
  * sides in its compiled variants and keep the fastest for this context; every later dslash launch
  * of that precision and RHS count uses it.  Variants 0 / 1 / 2: direct loads with register caps
- * of 128 / 80 / 64 per thread (4 / 6 / 8 resident 128-thread blocks per SM); 3 / 4: links rebuilt
- * and clover copied once per site into shared memory, register caps 128 / 80 (FP32 and FP16, nrhs
- * a power of two in [16, 128]); 5: the neighbour spinors staged in shared memory by bulk
- * asynchronous copies 3 hops ahead (FP32 and FP16, nrhs a multiple of 32).  Where a variant does
+ * of 128 / 80 / 64 per thread (4 / 6 / 8 resident 128-thread blocks per SM); 3: links rebuilt and
+ * clover copied once per site into shared memory, 32-bit indexing, register cap 80 (FP32 and
+ * FP16, nrhs a power of two in [16, 128]); 4: the neighbour spinors staged in shared memory by
+ * bulk asynchronous copies 3 hops ahead (FP32 and FP16, nrhs a multiple of 32).  Where a variant does
  * not apply it runs as variant 0.  FP64 has variants 0 / 1 / 2 with register caps 128 / 255 / 168.  All variants compute the same arithmetic in the
  * same order.  lqcd_set_dslash_variant
  * installs a known choice (e.g. from a cache) without timing.  Errors: INVALID_ARG (variant
- * outside 0..5), STATE (no gauge), TIMEOUT (a staged copy did not complete within its wait
+ * outside 0..4), STATE (no gauge), TIMEOUT (a staged copy did not complete within its wait
  * limit; the solvers report the same). */
 int lqcd_tune_dslash(lqcd_ctx* ctx, int prec, int nrhs, int* best_variant, double* best_ms);
 int lqcd_set_dslash_variant(lqcd_ctx* ctx, int prec, int nrhs, int variant);

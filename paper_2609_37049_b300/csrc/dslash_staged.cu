@@ -1,12 +1,12 @@
 // Even-odd dslash kernels (same operator and epilogues as dslash.cu) that stage per-site data in
 // shared memory, selected by the dslash launch variant:
 //
-// * variants 3 / 4 (dslash_sl_kernel): the eight links of every site of the block are loaded and
-//   their third rows rebuilt once per site by a few threads, and the site's clover blocks copied
-//   once, into shared memory; the hopping threads then read them as broadcasts instead of each
+// * variant 3 (dslash_sl_kernel): the eight links of every site of the block are loaded and their
+//   third rows rebuilt once per site by a few threads, and the site's clover blocks copied once,
+//   into shared memory; the hopping threads then read them as broadcasts instead of each
 //   rebuilding the links (the direct kernel repeats the rebuild for every right-hand side).  Site
-//   and element indices are 32-bit (the host checks that the fields fit).
-// * variant 5 (dslash_pipe_kernel): the eight neighbour spinors of every output site staged by
+//   and element indices are 32-bit (the host checks that the fields fit).  Register cap 80.
+// * variant 4 (dslash_pipe_kernel): the eight neighbour spinors of every output site staged by
 //   bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier) 3 hops ahead of
 //   the arithmetic.  One warp = 32 right-hand sides of one output site (nrhs a multiple of 32),
 //   so the warp's share of one 16-byte chunk of a neighbour spinor is one contiguous 512-byte run
@@ -296,9 +296,11 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl_kernel(const DslashParams
       if (c < Vh) {
         const int mu = k >> 1;
         int lcb = c, par = pr.out_par;
-        if (k & 1) {  // backward hop: the link of the neighbour s - mu
-          const unsigned cw = __ldg(pr.coord + c);
-          const int x = cw & 0xff, y = (cw >> 8) & 0xff, z = (cw >> 16) & 0xff, t = cw >> 24;
+        if (k & 1) {  // backward hop: the link of the neighbour s - mu (coordinates by
+                      // arithmetic, not the table, so the link load is the only global latency)
+          const int xh = c % g.Lxh, yzt = c / g.Lxh, y = yzt % g.Ly, zt = yzt / g.Ly, z = zt % g.Lz,
+                    t = zt / g.Lz;
+          const int x = 2 * xh + ((pr.out_par + y + z + t) & 1);
           const int s = x + sy * y + sz * z + sw * t;
           const int cm = mu == 0 ? x : (mu == 1 ? y : (mu == 2 ? z : t));
           const int Lm = mu == 0 ? g.Lx : (mu == 1 ? g.Ly : (mu == 2 ? g.Lz : g.Lt));
@@ -328,14 +330,14 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl_kernel(const DslashParams
       }
     }
   }
-  __syncthreads();
-
   const int tid = blockIdx.x * 128 + threadIdx.x;
   const int cb = tid >> lg;
   const int rhs = tid & (nr - 1);
+  const unsigned cw = cb < Vh ? __ldg(pr.coord + cb) : 0u;  // issued before the barrier
+  __syncthreads();
+
   if (RED == RED_NONE && cb >= Vh) return;
   const int sl = threadIdx.x >> lg;
-  const unsigned cw = __ldg(pr.coord + cb);
   const int x = cw & 0xff, y = (cw >> 8) & 0xff, z = (cw >> 16) & 0xff, t = cw >> 24;
   const int s = x + sy * y + sz * z + sw * t;
   const int stride = Vh * nr;
@@ -450,9 +452,9 @@ bool launch_p(const DslashParams& pr, int epi, int red, long blocks, int tpb, si
 
 bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, int red, long blocks, int tpb,
                           size_t red_shm, int variant, cudaStream_t st) {
-  if (prec == P64 || dag || variant < 3 || variant > 5) return false;
+  if (prec == P64 || dag || variant < 3 || variant > 4) return false;
   const long nr = pr.nrhs;
-  if (variant == 5) {  // bulk-copy staged spinors, staging depth 3
+  if (variant == 4) {  // bulk-copy staged spinors, staging depth 3
     if (nr % 32 != 0 || tpb % 32 != 0) return false;
     open_all();
     if (prec == P32) return launch_p<P32>(pr, epi, red, blocks, tpb, red_shm, 3, st);
@@ -462,11 +464,8 @@ bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, i
   if (nr < 16 || nr > 128 || (nr & (nr - 1)) != 0 || tpb != 128) return false;
   if (pr.g.Vh % (128 / nr) != 0 || blocks * (128 / nr) != pr.g.Vh) return false;
   if (12 * pr.g.Vh * nr >= (1L << 31)) return false;
-  if (prec == P32)
-    return variant == 3 ? launch_sl_e<P32, 4>(pr, epi, red, blocks, red_shm, st)
-                        : launch_sl_e<P32, 6>(pr, epi, red, blocks, red_shm, st);
-  return variant == 3 ? launch_sl_e<P16, 4>(pr, epi, red, blocks, red_shm, st)
-                      : launch_sl_e<P16, 6>(pr, epi, red, blocks, red_shm, st);
+  if (prec == P32) return launch_sl_e<P32, 6>(pr, epi, red, blocks, red_shm, st);
+  return launch_sl_e<P16, 6>(pr, epi, red, blocks, red_shm, st);
 }
 
 unsigned long long dslash_pipe_timeouts(bool reset) {
