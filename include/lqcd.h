@@ -126,6 +126,16 @@ int lqcd_gauge_upload(lqcd_ctx* ctx, const double* links, int where, double kapp
  * they do not sum to Lt (nothing changed). */
 int lqcd_set_domains(lqcd_ctx* ctx, const int* extents, int n_dom);
 
+/* The same tiling shifted to start at timeslice t_start: domain d covers
+ * t_start + (e_0 + ... + e_{d-1}) + [0, e_d) modulo Lt, so the last domain may wrap around the
+ * time boundary.  Shifted tilings place the regions Lambda_0, Lambda_1 of width Delta around the
+ * chosen x0, y0 (Sec. 2.1, Fig. 1; Sec. 4 chooses Delta per separation).  The Dirichlet cuts sit
+ * between consecutive domains, the antiperiodic (or open) boundary phase stays on the t-hop
+ * from Lt-1 to 0, and every domain-mode call (solves, perambulators, correlator validity) uses the
+ * shifted domains.  lqcd_set_domains(ctx, e, n) = lqcd_set_domains_at(ctx, 0, e, n).  Errors:
+ * INVALID_ARG (as lqcd_set_domains, or t_start outside [0, Lt); nothing changed). */
+int lqcd_set_domains_at(lqcd_ctx* ctx, int t_start, const int* extents, int n_dom);
+
 /* out = D in (domain_restricted = 0) or out = D_Lambda in (1), FP64, nrhs spinors. */
 int lqcd_dirac_apply(lqcd_ctx* ctx, const double* in, double* out, int nrhs, int domain_restricted,
                      int where);

@@ -11,9 +11,11 @@ action).  The paper fixes neither normalisation nor signs; this oracle takes the
 fermion boundary condition in time as a phase on the t-links leaving t = T-1 (antiperiodic: -1,
 periodic: +1, open: 0), periodic in space; the clover term uses the original links.
 
-Domain restriction (Sec. 2.1): the time axis is tiled by consecutive domains starting at t = 0.
-D_Lambda keeps every term of D whose two sites lie in the same domain, i.e. it is D with the
-t-hops between t and t+1 (mod T) removed wherever dom(t) != dom(t+1); the clover term is kept.
+Domain restriction (Sec. 2.1): the time axis is tiled by consecutive domains starting at
+t = t_start (0 unless a shifted tiling places the regions around chosen x0, y0, Fig. 1; the last
+domain then wraps around the time boundary).  D_Lambda keeps every term of D whose two sites lie
+in the same domain, i.e. it is D with the t-hops between t and t+1 (mod T) removed wherever
+dom(t) != dom(t+1); the clover term is kept.
 For a single domain covering all of T nothing is removed.  The block-diagonal operator over all
 domains is what the simultaneous multi-site-source solves of Sec. 4 invert.
 
@@ -70,22 +72,31 @@ def eo_order(dims):
     return perm, cb
 
 
-def domain_of_t(extents, Lt):
-    """dom[t] for a tiling of [0, Lt) by consecutive domains of the given extents, from t = 0."""
+def domain_of_t(extents, Lt, t_start=0):
+    """dom[t] for a tiling of the periodic time axis by consecutive domains of the given extents,
+    domain 0 starting at t_start: domain d holds t_start + e_0 + ... + e_{d-1} + [0, e_d) mod Lt."""
     extents = [int(e) for e in extents]
     if any(e < 1 for e in extents) or sum(extents) != Lt:
         raise ValueError("domain extents must be >= 1 and tile the time extent")
-    return np.repeat(np.arange(len(extents)), extents)
+    if not 0 <= int(t_start) < Lt:
+        raise ValueError("t_start outside [0, Lt)")
+    dom = np.empty(Lt, dtype=np.int64)
+    t = int(t_start)
+    for d, e in enumerate(extents):
+        for k in range(e):
+            dom[(t + k) % Lt] = d
+        t += e
+    return dom
 
 
-def cut_after(extents, Lt):
+def cut_after(extents, Lt, t_start=0):
     """cut[t] = True where the t-hop between t and t+1 (mod Lt) joins two different domains."""
-    d = domain_of_t(extents, Lt)
+    d = domain_of_t(extents, Lt, t_start)
     return d != np.roll(d, -1)
 
 
 # ----------------------------------------------------------------------------- links
-def fermion_links(U, bc_t=BC_ANTIPERIODIC, extents=None):
+def fermion_links(U, bc_t=BC_ANTIPERIODIC, extents=None, t_start=0):
     """Links seen by the fermion hopping term: U with the time boundary phase on the t-links
     from t = Lt-1 and, for the domain operator, zero on every t-link that crosses a cut."""
     Ue = U.copy()
@@ -93,7 +104,7 @@ def fermion_links(U, bc_t=BC_ANTIPERIODIC, extents=None):
     phase = {BC_PERIODIC: 1.0, BC_ANTIPERIODIC: -1.0, BC_OPEN: 0.0}[bc_t]
     Ue[Lt - 1, :, :, :, 3] *= phase
     if extents is not None:
-        for t in np.nonzero(cut_after(extents, Lt))[0]:
+        for t in np.nonzero(cut_after(extents, Lt, t_start))[0]:
             Ue[t, :, :, :, 3] = 0.0
     return Ue
 
@@ -191,14 +202,15 @@ class WilsonClover:
     """D = A - kappa H on a fixed gauge field; ``extents`` (optional) makes it the Dirichlet
     domain operator D_Lambda (block diagonal over the domains of the tiling)."""
 
-    def __init__(self, U, kappa, c_sw, bc_t=BC_ANTIPERIODIC, extents=None):
+    def __init__(self, U, kappa, c_sw, bc_t=BC_ANTIPERIODIC, extents=None, t_start=0):
         self.U = U
         self.dims = (U.shape[3], U.shape[2], U.shape[1], U.shape[0])
         self.kappa = float(kappa)
         self.c_sw = float(c_sw)
         self.bc_t = bc_t
         self.extents = None if extents is None else [int(e) for e in extents]
-        self.Ue = fermion_links(U, bc_t, self.extents)
+        self.t_start = int(t_start)
+        self.Ue = fermion_links(U, bc_t, self.extents, self.t_start)
         self.A = clover_matrix(U, kappa, c_sw)
 
     @property
@@ -213,9 +225,10 @@ class WilsonClover:
         Ah = np.conj(np.swapaxes(self.A, -1, -2))
         return apply_site_matrix(Ah, psi) - self.kappa * hopping(self.Ue, psi, dagger=True)
 
-    def restricted(self, extents):
-        """The domain operator D_Lambda of this operator for a tiling of the time axis."""
-        return WilsonClover(self.U, self.kappa, self.c_sw, self.bc_t, extents)
+    def restricted(self, extents, t_start=0):
+        """The domain operator D_Lambda of this operator for a tiling of the time axis whose
+        domain 0 starts at t_start."""
+        return WilsonClover(self.U, self.kappa, self.c_sw, self.bc_t, extents, t_start)
 
     def dense(self, chunk=512):
         """The full 12V x 12V matrix, columns ordered by (site, spin, colour)."""

@@ -159,10 +159,11 @@ def point_loops(Dinv_diag, gamma_ids):
 
 
 # ----------------------------------------------------------------------------- correlators
-def disc_correlators(L, Lt, Ld, Ltd, extents, vev=True):
+def disc_correlators(L, Lt, Ld, Ltd, extents, vev=True, t_start=0):
     """Full, completely factorised and subtracted disconnected correlators.
 
-    L, Lt, Ld, Ltd: [n_cfg, n_gamma, T] full and domain loops (Gamma and Gamma-tilde).
+    L, Lt, Ld, Ltd: [n_cfg, n_gamma, T] full and domain loops (Gamma and Gamma-tilde); the
+    domains are the tiling `extents` starting at t_start.
     Returns dict with C, C_dd, dC [n_gamma, T, T] (index [g, x0, y0]), valid [T, T],
     C_avg, dC_avg [n_gamma, T] (index Delta t = x0 - y0 mod T), n_valid [T], and the four
     pieces of Eqs. corr1-corr4 as terms [4, n_gamma, T, T]."""
@@ -177,7 +178,7 @@ def disc_correlators(L, Lt, Ld, Ltd, extents, vev=True):
     C = conn(L, Lt)
     C_dd = conn(Ld, Ltd)
     dC = C - C_dd
-    dom = domain_of_t(extents, T)
+    dom = domain_of_t(extents, T, t_start)
     valid = (dom[:, None] != dom[None, :]).astype(np.int32)
     C_avg = np.zeros((n_g, T), dtype=np.complex128)
     dC_avg = np.zeros((n_g, T), dtype=np.complex128)

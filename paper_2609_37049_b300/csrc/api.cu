@@ -197,11 +197,18 @@ void fill_tables(lqcd_ctx* c) {
   memset(&c->seg_dom, 0, sizeof(SegInfo));
   int n = (int)c->extents.size();
   c->seg_dom.nseg = n;
-  int t = 0;
+  int t = c->t_start;  // domain d covers t_start + (e_0 + ... + e_{d-1}) + [0, e_d), mod T
   for (int d = 0; d < n; d++) {
+    const int e = c->extents[d];
+    for (int k = 0; k < e; k++) c->seg_dom.seg_of_t[(t + k) % T] = (unsigned char)d;
     c->seg_dom.t0[d] = (unsigned short)t;
-    for (int k = 0; k < c->extents[d]; k++) c->seg_dom.seg_of_t[t++] = (unsigned char)d;
-    c->seg_dom.t1[d] = (unsigned short)t;
+    if (t + e <= T) {
+      c->seg_dom.t1[d] = (unsigned short)(t + e);
+    } else {  // wraps: [t, T) and [0, t + e - T)
+      c->seg_dom.t1[d] = (unsigned short)T;
+      c->seg_dom.t1b[d] = (unsigned short)(t + e - T);
+    }
+    t = (t + e) % T;
   }
   for (int tt = 0; tt < LQCD_MAXT; tt++) c->tc_dom[tt] = 0;
   for (int tt = 0; tt < T; tt++) {
@@ -459,8 +466,10 @@ int lqcd_gauge_upload(lqcd_ctx* c, const double* links, int where, double kappa,
   return LQCD_OK;
 }
 
-int lqcd_set_domains(lqcd_ctx* c, const int* extents, int n_dom) {
-  if (!c || !extents || n_dom < 1 || n_dom > c->g.Lt)
+int lqcd_set_domains(lqcd_ctx* c, const int* extents, int n_dom) { return lqcd_set_domains_at(c, 0, extents, n_dom); }
+
+int lqcd_set_domains_at(lqcd_ctx* c, int t_start, const int* extents, int n_dom) {
+  if (!c || !extents || n_dom < 1 || n_dom > c->g.Lt || t_start < 0 || t_start >= c->g.Lt)
     return set_error(c, LQCD_ERR_INVALID_ARG, "set_domains: bad arguments");
   int sum = 0;
   for (int d = 0; d < n_dom; d++) {
@@ -470,6 +479,7 @@ int lqcd_set_domains(lqcd_ctx* c, const int* extents, int n_dom) {
   if (sum != c->g.Lt) return set_error(c, LQCD_ERR_INVALID_ARG, "set_domains: extents do not tile Lt");
   cudaStreamSynchronize(c->work);
   c->extents.assign(extents, extents + n_dom);
+  c->t_start = t_start;
   fill_tables(c);
   return LQCD_OK;
 }

@@ -53,14 +53,17 @@ LQCD_D void seg_sum_g(const double* partial, const VGeom& vg, const SegInfo* si,
                       double (&out)[ND]) {
   __shared__ double sm[ND][128];
   const int rhs = blockIdx.x, seg = blockIdx.y;
-  const long t0 = si ? si->t0[seg] : 0, t1 = si ? si->t1[seg] : vg.g.Lt;
   double acc[ND];
 #pragma unroll
   for (int k = 0; k < ND; k++) acc[k] = 0.0;
-  const long b0 = t0 * vg.bpt, nb = (t1 - t0) * vg.bpt;
-  for (long b = threadIdx.x; b < nb; b += blockDim.x) {
+  for (int rg = 0; rg < 2; rg++) {  // the segment's timeslice range(s)
+    const long t0 = si ? (rg ? si->t0b[seg] : si->t0[seg]) : 0;
+    const long t1 = si ? (rg ? si->t1b[seg] : si->t1[seg]) : (rg ? 0 : vg.g.Lt);
+    const long b0 = t0 * vg.bpt, nb = (t1 - t0) * vg.bpt;
+    for (long b = threadIdx.x; b < nb; b += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < ND; k++) acc[k] += partial[((b0 + b) * vg.nrhs + rhs) * nd_stride + k0 + k];
+      for (int k = 0; k < ND; k++) acc[k] += partial[((b0 + b) * vg.nrhs + rhs) * nd_stride + k0 + k];
+    }
   }
 #pragma unroll
   for (int k = 0; k < ND; k++) sm[k][threadIdx.x] = acc[k];

@@ -17,11 +17,16 @@ namespace lqcd {
 // power of two dividing the half-timeslice volume so every block lies inside one timeslice of
 // one parity.  Segments are ranges of timeslices (one per domain, or one for the full lattice);
 // a Krylov "system" is one (rhs, segment) pair, index sys = rhs * nseg + seg.
+// Time segments (domains) of a solve: segment k covers timeslices [t0, t1) and, for a domain
+// that wraps around the time boundary (tilings that start at t_start > 0), also [t0b, t1b)
+// (empty when t0b == t1b).
 struct SegInfo {
   int nseg;
   unsigned char seg_of_t[LQCD_MAXT];
   unsigned short t0[LQCD_MAXT];
   unsigned short t1[LQCD_MAXT];
+  unsigned short t0b[LQCD_MAXT];
+  unsigned short t1b[LQCD_MAXT];
 };
 
 struct VGeom {
@@ -123,6 +128,7 @@ struct lqcd_ctx {
   void* A32 = nullptr;
   // domain tiling of the time axis
   std::vector<int> extents;
+  int t_start = 0;  // first timeslice of domain 0 (the tiling wraps around the time boundary)
   signed char tc_full[LQCD_MAXT];
   signed char tc_dom[LQCD_MAXT];
   signed char* d_tc_full = nullptr;  // device copies [Lt]

@@ -29,7 +29,7 @@ LQCD_PREC_F64, LQCD_PREC_F32, LQCD_PREC_F16 = 0, 1, 2
 
 EXPORTED = [
     "lqcd_default_params", "lqcd_create", "lqcd_destroy", "lqcd_set_stream", "lqcd_last_error",
-    "lqcd_gauge_upload", "lqcd_set_domains", "lqcd_dirac_apply", "lqcd_solve_full",
+    "lqcd_gauge_upload", "lqcd_set_domains", "lqcd_set_domains_at", "lqcd_dirac_apply", "lqcd_solve_full",
     "lqcd_solve_domain", "lqcd_perambulator", "lqcd_loops", "lqcd_disc_correlator",
     "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
@@ -107,6 +107,7 @@ def load_library(path=_LIB_PATH):
         "lqcd_last_error": (ctypes.c_char_p, [vp]),
         "lqcd_gauge_upload": (ip, [vp, vp, ip, ctypes.c_double, ctypes.c_double]),
         "lqcd_set_domains": (ip, [vp, c_int_p, ip]),
+        "lqcd_set_domains_at": (ip, [vp, ip, c_int_p, ip]),
         "lqcd_dirac_apply": (ip, [vp, vp, vp, ip, ip, ip]),
         "lqcd_schur_apply": (ip, [vp, ip, vp, vp, ip, ip, ip]),
         "lqcd_solve_full": (ip, [vp, vp, vp, ip, ip, ctypes.POINTER(lqcd_solve_params),
@@ -223,6 +224,7 @@ class Context:
         if rc != LQCD_OK:
             raise LqcdError(rc, _lib.lqcd_last_error(None).decode())
         self.extents = [self.dims[3]]
+        self.t_start = 0
 
     @property
     def volume(self):
@@ -252,9 +254,11 @@ class Context:
         return self._check(_lib.lqcd_gauge_upload(self.h, _ptr(links), _where(links), float(kappa),
                                                   float(c_sw)))
 
-    def set_domains(self, extents):
-        rc = self._check(_lib.lqcd_set_domains(self.h, _int_array(extents), len(extents)))
+    def set_domains(self, extents, t_start=0):
+        """Tile the time axis by domains of the given extents, domain 0 starting at t_start."""
+        rc = self._check(_lib.lqcd_set_domains_at(self.h, int(t_start), _int_array(extents), len(extents)))
         self.extents = [int(e) for e in extents]
+        self.t_start = int(t_start)
         return rc
 
     def dirac_apply(self, psi, out, domain_restricted=False):

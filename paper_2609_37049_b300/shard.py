@@ -9,14 +9,17 @@ loops (a few kilobytes) to the rank that forms the correlators.
 import numpy as np
 
 
-def source_groups(Lt, extents):
-    """Source groups of a tiling of [0, Lt): group g holds t0(d) + g for every domain d wide enough,
-    g = 0 .. max(extents) - 1 (domains narrower than g + 1 drop out of group g)."""
+def source_groups(Lt, extents, t_start=0):
+    """Source groups of a tiling of the time axis whose domain 0 starts at t_start: group g holds
+    t0(d) + g (mod Lt) for every domain d wide enough, g = 0 .. max(extents) - 1 (domains narrower
+    than g + 1 drop out of group g)."""
     extents = [int(e) for e in extents]
     if sum(extents) != Lt or min(extents) < 1:
         raise ValueError("extents must tile the time axis")
-    starts = np.cumsum([0] + extents[:-1])
-    return [[int(s + g) for s, e in zip(starts, extents) if g < e] for g in range(max(extents))]
+    if not 0 <= int(t_start) < Lt:
+        raise ValueError("t_start outside [0, Lt)")
+    starts = int(t_start) + np.cumsum([0] + extents[:-1])
+    return [[int((s + g) % Lt) for s, e in zip(starts, extents) if g < e] for g in range(max(extents))]
 
 
 def shard(units, rank, world):

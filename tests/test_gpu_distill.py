@@ -125,6 +125,30 @@ def test_domain_mode_uneven_grouping(small_config):
     assert tau_rel(td, to) < 1e-9
 
 
+def test_shifted_tiling_perambulators_and_correlators(small_config):
+    """A tiling starting at t = 3 (domain [3, 5] wraps as t = 7, 0): domain-mode perambulators
+    against the oracle's shifted D_Lambda, and the correlator validity table and subtracted
+    correlator against the oracle on the same loops."""
+    c = small_config
+    case = c["case"]
+    ext, t0 = [4, 4], 3
+    ctx = Context(case["dims"])
+    ctx.gauge_upload(c["U"], case["kappa"], case["c_sw"])
+    ctx.set_domains(ext, t_start=t0)
+    T, n_ev = case["dims"][3], case["n_ev"]
+    opd = WilsonClover(c["U"], case["kappa"], case["c_sw"]).restricted(ext, t0)
+    want = perambulators(opd, c["V"], range(T))
+    td = _gpu_tau(ctx, c["V"], n_ev, range(T), lqcd.LQCD_MODE_DOMAIN)
+    assert tau_rel(td, want) < 1e-9
+    assert tau_rel(td, c["tau_d"]) > 1e-6  # differs from the unshifted tiling's perambulators
+    L, Lt, Ld, Ltd = _random_loops(2, len(GAMMAS), T, 5)
+    out = _gpu_corr(ctx, L, Lt, Ld, Ltd, True)
+    o = disc_correlators(L, Lt, Ld, Ltd, ext, vev=True, t_start=t0)
+    assert np.array_equal(out["valid"], o["valid"]) and np.array_equal(out["n_valid"], o["n_valid"])
+    assert np.abs(out["dC"] - o["dC"]).max() <= 1e-13 * np.abs(o["C"]).max()
+    assert np.abs(out["dC_avg"] - o["dC_avg"]).max() <= 1e-13 * np.abs(o["C"]).max()
+
+
 def test_colour_vector_sources_rough_field():
     case = ROUGH
     U = gauge(case, 3003)

@@ -51,6 +51,15 @@ def test_source_groups_tile_every_timeslice_once():
         source_groups(8, [4, 3])
 
 
+def test_source_groups_of_shifted_tiling():
+    """Tiling [3, 5] starting at t = 6: domain 0 = {6, 7, 0}, domain 1 = {1, ..., 5}."""
+    groups = source_groups(8, [3, 5], t_start=6)
+    assert groups == [[6, 1], [7, 2], [0, 3], [4], [5]]
+    assert sorted(t for g in groups for t in g) == list(range(8))
+    with pytest.raises(ValueError):
+        source_groups(8, [3, 5], t_start=8)
+
+
 def test_units_for_step_cover_all_units_across_ranks():
     units = source_groups(32, [4] * 8)
     seen = [units_for_step(units, s, r, 2) for s in range(2) for r in range(2)]

@@ -147,6 +147,13 @@ def test_geometry_tables():
     assert not cut_after([12], 12).any()
     with pytest.raises(ValueError):
         domain_of_t([4, 4], 12)
+    # shifted tilings (regions placed around chosen x0, y0): the last domain wraps around
+    assert list(domain_of_t([3, 5], 8, t_start=6)) == [0, 1, 1, 1, 1, 1, 0, 0]
+    assert list(np.nonzero(cut_after([3, 5], 8, t_start=6))[0]) == [0, 5]
+    assert list(domain_of_t([2, 4, 2, 4], 12, 3)) == [3, 3, 3, 0, 0, 1, 1, 1, 1, 2, 2, 3]
+    assert list(np.nonzero(cut_after([2, 4, 2, 4], 12, 3))[0]) == [2, 4, 8, 10]
+    with pytest.raises(ValueError):
+        domain_of_t([4, 4], 8, t_start=8)
 
 
 def test_domain_operator_block_structure():
@@ -156,11 +163,27 @@ def test_domain_operator_block_structure():
     op = WilsonClover(U, 0.125, 1.6)
     D = op.dense()
     t = np.repeat(coords(dims)[3], 12)
-    for ext in ([2, 4, 2], [3, 5], [1, 7]):
-        dom = domain_of_t(ext, 8)[t]
+    for ext, t0 in (([2, 4, 2], 0), ([3, 5], 0), ([1, 7], 0), ([3, 5], 6), ([2, 4, 2], 7), ([1, 7], 3)):
+        dom = domain_of_t(ext, 8, t0)[t]
         want = np.where(dom[:, None] == dom[None, :], D, 0)
-        assert np.abs(op.restricted(ext).dense() - want).max() == 0
+        assert np.abs(op.restricted(ext, t0).dense() - want).max() == 0
     assert np.abs(op.restricted([8]).dense() - D).max() == 0
+    assert np.abs(op.restricted([8], 5).dense() - D).max() == 0
+
+
+@pytest.mark.parametrize("shift", [1, 3, 6])
+def test_shifted_tiling_translation_covariance(shift):
+    """With periodic time boundary conditions, translating the gauge field, the spinor and the
+    tiling by the same number of timeslices commutes with D_Lambda: D_Lambda[T U, t_start = s]
+    (T psi) = T (D_Lambda[U, t_start = 0] psi), (T f)(t) = f(t - s)."""
+    dims = (2, 2, 4, 8)
+    U = gauge_field(dims, 0.5, 57)
+    psi = random_spinors(dims, 2, 58)
+    ext = [3, 5]
+    ref = WilsonClover(U, KAPPA, CSW, BC_PERIODIC, ext).apply(psi)
+    Us = np.roll(U, shift, axis=0)
+    got = WilsonClover(Us, KAPPA, CSW, BC_PERIODIC, ext, t_start=shift).apply(np.roll(psi, shift, axis=1))
+    assert np.abs(got - np.roll(ref, shift, axis=1)).max() < 1e-13
 
 
 def test_schur_factorisation_of_propagator():
