@@ -197,6 +197,28 @@ int lqcd_disc_correlator(lqcd_ctx* ctx, const double* L, const double* Lt, const
                          double* dC, double* C_avg, double* dC_avg, int* valid, int* n_valid,
                          double* terms, int where);
 
+/* Quark-line connected correlator of Eq. Cfull with distilled quark lines, from all-sink
+ * perambulators (lqcd_perambulator with LQCD_SINKS_ALL, full mode):
+ *   C[g][x0][k] = - Tr[ Gamma tau(x0, y0) Gamma~ tau(y0, x0) ],  y0 = t_src[k],
+ * trace over eigenvector and spin, Gamma~ = gamma_t Gamma^dag gamma_t, tau(y0, x0) =
+ * gamma_5 tau(x0, y0)^dag gamma_5 (gamma_5-hermiticity of D), and the minus sign of the fermion
+ * loop; C_avg[g][dt] = mean over k of C[g][(t_src[k] + dt) mod Lt][k] (may be NULL).
+ * tau_all: [n_t][Lt][n_ev][4][n_ev][4] complex (sink t', sink eigvec, sink spin, source eigvec,
+ * source spin), C: [n_gamma][Lt][n_t], C_avg: [n_gamma][Lt].  gamma_ids index the 16 Clifford
+ * elements as in lqcd_loops.  Errors: INVALID_ARG (sizes, t_src or gamma ids out of range), OOM. */
+int lqcd_conn_correlator(lqcd_ctx* ctx, const double* tau_all, int n_ev, const int* t_src, int n_t,
+                         const int* gamma_ids, int n_gamma, double* C, double* C_avg, int where);
+
+/* Noise-reduced estimator (Sec. 4): the full correlator of Eq. Cfull with the disconnected part
+ * replaced by the subtracted one of the block size Delta chosen for each separation,
+ *   C_nr[g][dt] = C_conn_avg[g][dt] + dC_avg[d][g][dt],   d = delta_of_dt[dt] >= 0,
+ *               = C_conn_avg[g][dt] + C_disc_avg[g][dt],  d = -1 (standard estimator).
+ * C_conn_avg, C_disc_avg, C_nr: [n_gamma][Lt]; dC_avg: [n_delta][n_gamma][Lt], the dC_avg outputs
+ * of lqcd_disc_correlator for n_delta tilings (NULL if n_delta = 0); delta_of_dt: [Lt] host array.
+ * Errors: INVALID_ARG (an index outside [-1, n_delta)). */
+int lqcd_nr_estimator(lqcd_ctx* ctx, const double* C_conn_avg, const double* C_disc_avg, const double* dC_avg,
+                      int n_delta, int n_gamma, const int* delta_of_dt, double* C_nr, int where);
+
 /* Distillation vectors (Sec. 3.1, 3.2): the n_ev lowest eigenpairs of the gauge-covariant 3D
  * Laplacian  (-Lap phi)(x) = sum_k [2 phi(x) - U_k(x) phi(x+k) - U_k(x-k)^dag phi(x-k)]  on every
  * timeslice of the uploaded gauge field, to residual ||(-Lap) v - lambda v|| <= tol (0 -> 1e-10).

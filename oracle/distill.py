@@ -25,6 +25,13 @@ Definitions followed (paper section / equation):
   valid only where dom(x0) != dom(y0) (non-overlapping regions, Sec. 3.1); the average over
   source positions y0 (Sec. 3.1) is taken over all y0 for C and over the valid y0 for dC.
   The four VEV-subtracted pieces of Eqs. corr1-corr4 use dL = L - L_Lambda (Sec. 4).
+* Quark-line connected part of Eq. Cfull with distilled quark lines V tau V^dag:
+      C^(c)_G(x0,y0) = - Tr[ G tau(x0,y0) Gt tau(y0,x0) ]   (trace over eigenvector and spin),
+  the Wick contraction of the same bilinears whose disconnected part is <L_G Lt_G> (the minus
+  sign is the fermion loop), read from all-sink perambulators of every source timeslice.
+* Noise-reduced estimator (Sec. 4): C^NR_Delta(x0,y0) = C^(c)(x0,y0) + dC_Delta(x0,y0), with the
+  block size Delta chosen per separation x0 - y0; where no Delta is assigned the standard
+  disconnected part C^(d) is used.
 
 Pinned by (tests/test_oracle_distill.py): free-field eigenvalues, eigen-residuals and
 orthonormality; the free-field closed form of tau^{ii}(t,t); the complete-basis identity
@@ -196,6 +203,58 @@ def disc_correlators(L, Lt, Ld, Ltd, extents, vev=True, t_start=0):
     terms = np.array([conn(Ld, Ltd), conn(Ld, dLt), conn(dL, Ltd), conn(dL, dLt)])
     return dict(C=C, C_dd=C_dd, dC=dC, valid=valid, C_avg=C_avg, dC_avg=dC_avg,
                 n_valid=n_valid, terms=terms)
+
+
+def conn_correlator(tau_all, t_src, gamma_ids):
+    """C[g, x0, k] = C^(c)(x0, y0 = t_src[k]) and its y0 average C_avg[g, dt] = mean over k of
+    C[g, (t_src[k] + dt) mod T, k].  tau_all[k, t', i, a, j, b] = tau(t', t_src[k]) (all sinks);
+    t_src must contain every timeslice, so tau(y0, x0) is read directly from the perambulator of
+    source x0 (no gamma_5-hermiticity is used here)."""
+    n_t, T, n_ev = tau_all.shape[0], tau_all.shape[1], tau_all.shape[2]
+    pos = {int(t): k for k, t in enumerate(t_src)}
+    if sorted(pos) != list(range(T)):
+        raise ValueError("conn_correlator needs the perambulators of every source timeslice")
+    table = clifford_table()
+    one = np.eye(n_ev)
+    C = np.zeros((len(gamma_ids), T, n_t), dtype=np.complex128)
+    for gi, g in enumerate(gamma_ids):
+        Gx = np.kron(one, table[g])  # acts on the (eigvec, spin) index at x0
+        Gy = np.kron(one, gamma_tilde(table[g]))  # at y0
+        for k, y0 in enumerate(t_src):
+            for x0 in range(T):
+                A = tau_all[k, x0].reshape(4 * n_ev, 4 * n_ev)  # tau(x0, y0)
+                B = tau_all[pos[x0], int(y0)].reshape(4 * n_ev, 4 * n_ev)  # tau(y0, x0)
+                C[gi, x0, k] = -np.trace(Gx @ A @ Gy @ B)
+    C_avg = np.zeros((len(gamma_ids), T), dtype=np.complex128)
+    for dt in range(T):
+        for k, y0 in enumerate(t_src):
+            C_avg[:, dt] += C[:, (int(y0) + dt) % T, k] / n_t
+    return C, C_avg
+
+
+def point_conn_correlator(Dinv, dims, gamma_ids):
+    """C^(c)(x0, y0) = - sum_{xvec, yvec} Tr[G D^{-1}(x,y) Gt D^{-1}(y,x)] from the dense inverse
+    (rows and columns ordered (site, spin, colour), sites x fastest): the point-source form that
+    distillation with a complete basis reproduces."""
+    Lx, Ly, Lz, Lt = dims
+    L3 = Lx * Ly * Lz
+    table = clifford_table()
+    Db = Dinv.reshape(Lt, L3, 4, 3, Lt, L3, 4, 3)
+    out = np.zeros((len(gamma_ids), Lt, Lt), dtype=np.complex128)
+    for gi, g in enumerate(gamma_ids):
+        G, Gt = table[g], gamma_tilde(table[g])
+        # trace over spin and colour of G S(x,y) Gt S(y,x), summed over xvec and yvec
+        out[gi] = -np.einsum("da,xpaqyrbs,bc,yrcsxpdq->xy", G, Db, Gt, Db, optimize=True)
+    return out
+
+
+def nr_estimator(C_conn_avg, C_disc_avg, dC_avg_by_delta, delta_of_dt):
+    """C^NR[g, dt] = C_conn_avg[g, dt] + dC_avg_by_delta[delta_of_dt[dt], g, dt], or
+    + C_disc_avg[g, dt] where delta_of_dt[dt] < 0 (no block size assigned)."""
+    out = np.array(C_conn_avg, dtype=np.complex128)
+    for dt, d in enumerate(delta_of_dt):
+        out[:, dt] += dC_avg_by_delta[d][:, dt] if d >= 0 else C_disc_avg[:, dt]
+    return out
 
 
 def effective_mass(C_of_dt):

@@ -715,6 +715,58 @@ int lqcd_loops(lqcd_ctx* c, const double* tau, int n_ev, int n_t, const int* gam
   return finish_out(c, Lt, dLt, lb, where);
 }
 
+int lqcd_conn_correlator(lqcd_ctx* c, const double* tau_all, int n_ev, const int* t_src, int n_t,
+                         const int* gamma_ids, int n_gamma, double* C, double* C_avg, int where) {
+  if (!c || !tau_all || !t_src || !gamma_ids || !C || n_ev < 1 || n_t < 1 || n_gamma < 1 || n_gamma > 16)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "conn_correlator: bad arguments");
+  const int T = c->g.Lt;
+  for (int k = 0; k < n_t; k++)
+    if (t_src[k] < 0 || t_src[k] >= T) return set_error(c, LQCD_ERR_INVALID_ARG, "conn_correlator: bad t");
+  for (int k = 0; k < n_gamma; k++)
+    if (gamma_ids[k] < 0 || gamma_ids[k] > 15)
+      return set_error(c, LQCD_ERR_INVALID_ARG, "conn_correlator: bad gamma id");
+  Scope sc(c);
+  const size_t tb = (size_t)n_t * T * n_ev * 4 * n_ev * 4 * sizeof(double2);
+  const size_t cb = (size_t)n_gamma * T * n_t * sizeof(double2), ab = (size_t)n_gamma * T * sizeof(double2);
+  const double2* dtau = (const double2*)stage_in(c, tau_all, tb, where, "cc_tau");
+  double2* dC = (double2*)stage_out(c, C, cb, where, "cc_C");
+  double2* dA = C_avg ? (double2*)stage_out(c, C_avg, ab, where, "cc_A") : nullptr;
+  double2* dG = (double2*)ws_get(c, "cc_G", 16 * 2 * 16 * sizeof(double2));
+  int* dts = (int*)ws_get(c, "cc_t", (size_t)n_t * sizeof(int));
+  if (!dtau || !dC || (C_avg && !dA) || !dG || !dts) return set_error(c, LQCD_ERR_OOM, "conn_correlator: OOM");
+  for (int k = 0; k < n_gamma; k++)
+    cudaMemcpyAsync(dG + (size_t)k * 32, c->d_gamma + (size_t)gamma_ids[k] * 32, 32 * sizeof(double2),
+                    cudaMemcpyDeviceToDevice, c->work);
+  cudaMemcpyAsync(dts, t_src, (size_t)n_t * sizeof(int), cudaMemcpyHostToDevice, c->work);
+  conn_correlator(dtau, n_ev, T, dts, n_t, dG, n_gamma, dC, dA, c->work);
+  if (int e = cuda_check(c, "conn_correlator")) return e;
+  if (int e = finish_out(c, C, dC, cb, where)) return e;
+  return C_avg ? finish_out(c, C_avg, dA, ab, where) : LQCD_OK;
+}
+
+int lqcd_nr_estimator(lqcd_ctx* c, const double* C_conn_avg, const double* C_disc_avg, const double* dC_avg,
+                      int n_delta, int n_gamma, const int* delta_of_dt, double* C_nr, int where) {
+  if (!c || !C_conn_avg || !C_disc_avg || !delta_of_dt || !C_nr || n_gamma < 1 || n_delta < 0 ||
+      (n_delta > 0 && !dC_avg))
+    return set_error(c, LQCD_ERR_INVALID_ARG, "nr_estimator: bad arguments");
+  const int T = c->g.Lt;
+  for (int t = 0; t < T; t++)
+    if (delta_of_dt[t] < -1 || delta_of_dt[t] >= n_delta)
+      return set_error(c, LQCD_ERR_INVALID_ARG, "nr_estimator: delta index out of range");
+  Scope sc(c);
+  const size_t ab = (size_t)n_gamma * T * sizeof(double2);
+  const double2* dc = (const double2*)stage_in(c, C_conn_avg, ab, where, "nr_c");
+  const double2* dd = (const double2*)stage_in(c, C_disc_avg, ab, where, "nr_d");
+  const double2* ddc = n_delta > 0 ? (const double2*)stage_in(c, dC_avg, n_delta * ab, where, "nr_dc") : nullptr;
+  double2* dout = (double2*)stage_out(c, C_nr, ab, where, "nr_o");
+  int* ddel = (int*)ws_get(c, "nr_del", (size_t)T * sizeof(int));
+  if (!dc || !dd || (n_delta > 0 && !ddc) || !dout || !ddel) return set_error(c, LQCD_ERR_OOM, "nr_estimator: OOM");
+  cudaMemcpyAsync(ddel, delta_of_dt, (size_t)T * sizeof(int), cudaMemcpyHostToDevice, c->work);
+  nr_estimator(dc, dd, ddc, n_gamma, T, ddel, dout, c->work);
+  if (int e = cuda_check(c, "nr_estimator")) return e;
+  return finish_out(c, C_nr, dout, ab, where);
+}
+
 int lqcd_disc_correlator(lqcd_ctx* c, const double* L, const double* Lt, const double* Ld, const double* Ltd,
                          int n_cfg, int n_gamma, int vev, double* C, double* Cdd, double* dC, double* C_avg,
                          double* dC_avg, int* valid, int* n_valid, double* terms, int where) {

@@ -222,6 +222,115 @@ void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma,
   k_loops<<<dim3(n_gamma, n_t), 128, 0, st>>>(tau, n_ev, n_t, G, n_gamma, w, L, Lt); lqcd::count_launch();
 }
 
+// ------------------------------------------------------------------ connected correlator
+// Quark-line connected part of Eq. Cfull with distilled quark lines:
+//   C[g][x0][k] = - Tr[G tau(x0,y0) Gt tau(y0,x0)],  y0 = t_src[k],
+// with tau(y0,x0)[j c][i d] = eps_c eps_d conj(tau(x0,y0)[i d][j c]) (gamma_5-hermiticity of D,
+// eps = diag(gamma_5)), so only the perambulators of the sources y0 are read:
+//   C = - sum_ij sum_abcd (eps_d G[d][a]) (Gt[b][c] eps_c) A[a][b] conj(A[d][c]),  A = tau(x0,y0)_ij.
+// One block per (gamma, x0, source); threads over the eigenvector pairs (i, j).
+__global__ void k_conn(const double2* tau, int n_ev, int T, int n_t, const double2* G, double2* C) {
+  const int gi = blockIdx.x, x0 = blockIdx.y, k = blockIdx.z;
+  __shared__ cplx<double> ge[4][4], gte[4][4];  // eps_d G[d][a], Gt[b][c] eps_c
+  __shared__ double sm[2][128];
+  if (threadIdx.x < 32) {
+    const int w = threadIdx.x >> 4, r = (threadIdx.x >> 2) & 3, q = threadIdx.x & 3;
+    const double2 v = G[((gi * 2 + w) * 4 + r) * 4 + q];
+    const double e = w == 0 ? (r < 2 ? 1.0 : -1.0) : (q < 2 ? 1.0 : -1.0);
+    if (w == 0)
+      ge[r][q] = {e * v.x, e * v.y};
+    else
+      gte[r][q] = {e * v.x, e * v.y};
+  }
+  __syncthreads();
+  const double2* base = tau + ((long)k * T + x0) * (long)n_ev * 4 * n_ev * 4;
+  cplx<double> acc = {0, 0};
+  for (int p = threadIdx.x; p < n_ev * n_ev; p += blockDim.x) {
+    const int i = p / n_ev, j = p - i * n_ev;
+    cplx<double> A[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int b = 0; b < 4; b++) {
+        const double2 v = base[(((long)i * 4 + a) * n_ev + j) * 4 + b];
+        A[a][b] = {v.x, v.y};
+      }
+    cplx<double> Q[4][4];  // Q[d][b] = sum_c conj(A[d][c]) gte[b][c]
+#pragma unroll
+    for (int d = 0; d < 4; d++)
+#pragma unroll
+      for (int b = 0; b < 4; b++) {
+        cplx<double> q = {0, 0};
+#pragma unroll
+        for (int c = 0; c < 4; c++) q = q + cjmul(A[d][c], gte[b][c]);
+        Q[d][b] = q;
+      }
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int b = 0; b < 4; b++) {
+        cplx<double> m = {0, 0};
+#pragma unroll
+        for (int d = 0; d < 4; d++) m = m + ge[d][a] * Q[d][b];
+        acc = acc + A[a][b] * m;
+      }
+  }
+  sm[0][threadIdx.x] = acc.re;
+  sm[1][threadIdx.x] = acc.im;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s >= 1; s >>= 1) {
+    if (threadIdx.x < s) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + s];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) C[((long)gi * T + x0) * n_t + k] = make_double2(-sm[0][0], -sm[1][0]);
+}
+
+// C_avg[g][dt] = mean over k of C[g][(t_src[k] + dt) mod T][k]
+__global__ void k_conn_avg(const double2* C, const int* t_src, int n_t, int T, double2* C_avg) {
+  const int gi = blockIdx.x;
+  for (int dt = threadIdx.x; dt < T; dt += blockDim.x) {
+    double re = 0, im = 0;
+    for (int k = 0; k < n_t; k++) {
+      const double2 v = C[((long)gi * T + (t_src[k] + dt) % T) * n_t + k];
+      re += v.x;
+      im += v.y;
+    }
+    C_avg[(long)gi * T + dt] = make_double2(re / n_t, im / n_t);
+  }
+}
+
+void conn_correlator(const double2* tau, int n_ev, int T, const int* t_src_dev, int n_t, const double2* G,
+                     int n_gamma, double2* C, double2* C_avg, cudaStream_t st) {
+  k_conn<<<dim3(n_gamma, T, n_t), 128, 0, st>>>(tau, n_ev, T, n_t, G, C); lqcd::count_launch();
+  if (C_avg) {
+    k_conn_avg<<<n_gamma, 128, 0, st>>>(C, t_src_dev, n_t, T, C_avg);
+    lqcd::count_launch();
+  }
+}
+
+// Noise-reduced estimator (Sec. 4): C_nr[g][dt] = conn[g][dt] + dC[d][g][dt] for the block size
+// d = delta_of_dt[dt] chosen for the separation, or + disc[g][dt] (standard estimator) if d < 0.
+__global__ void k_nr(const double2* conn, const double2* disc, const double2* dC, int n_gamma, int T,
+                     const int* delta_of_dt, double2* out) {
+  const long n = (long)n_gamma * T;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const int dt = (int)(e % T);
+    const int d = delta_of_dt[dt];
+    const double2 a = conn[e], b = d >= 0 ? dC[(long)d * n + e] : disc[e];
+    out[e] = make_double2(a.x + b.x, a.y + b.y);
+  }
+}
+
+void nr_estimator(const double2* conn, const double2* disc, const double2* dC, int n_gamma, int T,
+                  const int* delta_of_dt_dev, double2* out, cudaStream_t st) {
+  const long n = (long)n_gamma * T;
+  k_nr<<<(int)((n + 127) / 128), 128, 0, st>>>(conn, disc, dC, n_gamma, T, delta_of_dt_dev, out);
+  lqcd::count_launch();
+}
+
 // ------------------------------------------------------------------ correlators
 // conn(A, B)[g][x0][y0] = <A(x0) B(y0)> - vev * <A(x0)> <B(y0)>
 LQCD_D cplx<double> conn(const double2* A, const double2* B, int n_cfg, int n_g, int T, int g, int x0, int y0,

@@ -13,6 +13,12 @@ void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const
              double2* Cpart, int nrhs, cudaStream_t st);
 void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w, double2* L,
            double2* Lt, cudaStream_t st);
+// C [n_gamma][T][n_t], C_avg [n_gamma][T] (may be null): connected correlator from all-sink
+// perambulators tau [n_t][T][n_ev][4][n_ev][4]; G as for loops.
+void conn_correlator(const double2* tau, int n_ev, int T, const int* t_src_dev, int n_t, const double2* G,
+                     int n_gamma, double2* C, double2* C_avg, cudaStream_t st);
+void nr_estimator(const double2* conn, const double2* disc, const double2* dC, int n_gamma, int T,
+                  const int* delta_of_dt_dev, double2* out, cudaStream_t st);
 void correlators(const double2* L, const double2* Lt, const double2* Ld, const double2* Ltd, int n_cfg, int n_g,
                  int T, int vev, const int* dom, double2* C, double2* Cdd, double2* dC, double2* C_avg,
                  double2* dC_avg, int* valid, int* n_valid, double2* terms, double2* dL, double2* dLt,

@@ -34,6 +34,7 @@ EXPORTED = [
     "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
     "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant", "lqcd_schur_apply",
+    "lqcd_conn_correlator", "lqcd_nr_estimator",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -118,6 +119,8 @@ def load_library(path=_LIB_PATH):
                                    ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_stats)]),
         "lqcd_loops": (ip, [vp, vp, ip, ip, c_int_p, ip, vp, vp, vp, ip]),
         "lqcd_disc_correlator": (ip, [vp, vp, vp, vp, vp, ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, ip]),
+        "lqcd_conn_correlator": (ip, [vp, vp, ip, c_int_p, ip, c_int_p, ip, vp, vp, ip]),
+        "lqcd_nr_estimator": (ip, [vp, vp, vp, vp, ip, ip, c_int_p, vp, ip]),
         "lqcd_dslash_bench": (ip, [vp, ip, ip, ip, ip, dp, dp]),
         "lqcd_kernel_launches": (ctypes.c_longlong, []),
         "lqcd_laplace_eigs": (ip, [vp, ip, vp, vp, ip, ctypes.c_double, c_int_p]),
@@ -307,6 +310,21 @@ class Context:
             self.h, _ptr(L), _ptr(Lt), _ptr(Ld), _ptr(Ltd), n_cfg, n_g, int(vev), _ptr(out["C"]),
             _ptr(out["Cdd"]), _ptr(out["dC"]), _ptr(out["C_avg"]), _ptr(out["dC_avg"]),
             _ptr(out["valid"], np.int32), _ptr(out["n_valid"], np.int32), _ptr(terms), w))
+
+    def conn_correlator(self, tau_all, n_ev, t_src, gamma_ids, C, C_avg=None):
+        """C[g, x0, k] (and C_avg[g, dt]) from all-sink perambulators tau_all[k, t', i, a, j, b]."""
+        n_t = len(t_src)
+        return self._check(_lib.lqcd_conn_correlator(
+            self.h, _ptr(tau_all), int(n_ev), _int_array(t_src), n_t, _int_array(gamma_ids), len(gamma_ids),
+            _ptr(C), _ptr(C_avg), _where(tau_all, C)))
+
+    def nr_estimator(self, C_conn_avg, C_disc_avg, dC_avg, delta_of_dt, out):
+        """out[g, dt] = C_conn_avg + (dC_avg[delta_of_dt[dt]] or C_disc_avg where the index is -1)."""
+        n_g = C_conn_avg.shape[0]
+        n_delta = 0 if dC_avg is None else dC_avg.shape[0]
+        return self._check(_lib.lqcd_nr_estimator(
+            self.h, _ptr(C_conn_avg), _ptr(C_disc_avg), _ptr(dC_avg), n_delta, n_g, _int_array(delta_of_dt),
+            _ptr(out), _where(C_conn_avg, C_disc_avg, out)))
 
     # ---- autotuning
     def tune_dslash(self, prec, nrhs):

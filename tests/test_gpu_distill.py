@@ -10,7 +10,7 @@ import pytest
 from lqcd_inputs import colour_vectors
 from oracle.dirac import WilsonClover
 from oracle.distill import (laplace_eigs, perambulators, loops, disc_correlators,
-                            profile_weights)
+                            profile_weights, conn_correlator, nr_estimator)
 from tests.lattice_cases import SMALL, ROUGH, gauge
 
 pytestmark = pytest.mark.gpu
@@ -112,6 +112,41 @@ def test_all_sinks_and_ragged_batches(small_config):
                   sinks=lqcd.LQCD_SINKS_ALL)
     to = perambulators(op, c["V"], [2, 5], sinks="all")
     assert tau_rel(ta.reshape(2, -1), to.reshape(2, -1)) < 1e-9
+
+
+def test_connected_correlator_and_nr_estimator(small_config):
+    """Connected correlator from all-sink perambulators: the GPU contraction (gamma_5-hermiticity
+    form) on the oracle's perambulators at FP64 round-off, end to end from the GPU's perambulators
+    at 1e-9, a subset of sources column by column; and the noise-reduced estimator exactly."""
+    c = small_config
+    case = c["case"]
+    ctx = _ctx(case, c["U"])
+    T, n_ev = case["dims"][3], case["n_ev"]
+    op = WilsonClover(c["U"], case["kappa"], case["c_sw"])
+    t_all = list(range(T))
+    to = perambulators(op, c["V"], t_all, sinks="all")
+    gids = [5, 0, 1, 4, 10]
+    Co, Co_avg = conn_correlator(to, t_all, gids)
+    C = np.zeros((len(gids), T, T), complex)
+    C_avg = np.zeros((len(gids), T), complex)
+    ctx.conn_correlator(np.ascontiguousarray(to), n_ev, t_all, gids, C, C_avg)
+    scale = np.abs(Co).max()
+    assert np.abs(C - Co).max() <= 1e-13 * scale and np.abs(C_avg - Co_avg).max() <= 1e-13 * scale
+    sub = [6, 1]
+    Cs = np.zeros((len(gids), T, 2), complex)
+    ctx.conn_correlator(np.ascontiguousarray(to[sub]), n_ev, sub, gids, Cs)
+    assert np.abs(Cs - Co[:, :, sub]).max() <= 1e-13 * scale
+    ta = _gpu_tau(ctx, c["V"], n_ev, t_all, lqcd.LQCD_MODE_FULL, sinks=lqcd.LQCD_SINKS_ALL)
+    ctx.conn_correlator(ta, n_ev, t_all, gids, C, C_avg)
+    assert np.abs(C - Co).max() <= 1e-9 * scale
+    # noise-reduced estimator: two block sizes, the standard estimator at the shortest separations
+    rng = np.random.default_rng(9)
+    cplx = lambda *sh: rng.normal(size=sh) + 1j * rng.normal(size=sh)
+    disc, dC = cplx(len(gids), T), cplx(2, len(gids), T)
+    sel = [-1, -1, 0, 0, 1, 1, 1, 0]
+    out = np.zeros((len(gids), T), complex)
+    ctx.nr_estimator(np.ascontiguousarray(Co_avg), disc, dC, sel, out)
+    assert np.array_equal(out, nr_estimator(Co_avg, disc, dC, sel))
 
 
 def test_domain_mode_uneven_grouping(small_config):

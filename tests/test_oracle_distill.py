@@ -8,7 +8,8 @@ from lqcd_inputs import gauge_field, unit_gauge_field, random_gauge_transform, c
 from oracle.dirac import WilsonClover
 from oracle.gamma import gammas, clifford_table
 from oracle.distill import (laplacian3d, laplace_eigs, perambulators, loops, point_loops,
-                            disc_correlators, profile_weights, effective_mass)
+                            disc_correlators, profile_weights, effective_mass, conn_correlator,
+                            point_conn_correlator, nr_estimator)
 
 
 def test_free_laplacian_spectrum():
@@ -80,6 +81,40 @@ def test_complete_basis_loops_equal_point_traces():
     blocks = np.array([Dinv[s * n:(s + 1) * n, s * n:(s + 1) * n] for s in range(32)])
     P = point_loops(blocks.reshape(4, 2, 2, 2, 12, 12), gids)
     assert np.abs(L - P).max() < 1e-11 * np.abs(P).max()
+
+
+def test_complete_basis_connected_correlator_equals_point_contraction():
+    """With N_ev = 3 L^3 the distilled connected correlator -Tr[G tau(x0,y0) Gt tau(y0,x0)] is the
+    point-source one, -sum_{xvec,yvec} Tr[G D^-1(x,y) Gt D^-1(y,x)], from dense LU; and the
+    hermiticity tau(y0,x0) = g5 tau(x0,y0)^dag g5 holds between the all-sink perambulators."""
+    dims = (2, 2, 2, 4)
+    U = gauge_field(dims, 0.5, 73)
+    op = WilsonClover(U, 0.125, 1.6)
+    lam, V = laplace_eigs(U, 24)
+    tau = perambulators(op, V, range(4), sinks="all", tol=1e-13)
+    gids = [5, 0, 1, 13]
+    C, C_avg = conn_correlator(tau, list(range(4)), gids)
+    P = point_conn_correlator(np.linalg.inv(op.dense()), dims, gids)
+    assert np.abs(C - P).max() < 1e-11 * np.abs(P).max()
+    eps = np.array([1, 1, -1, -1])
+    A = tau[0, 2]  # tau(2, 0)
+    B = tau[2, 0]  # tau(0, 2)
+    want = np.einsum("c,d,idjc->jcid", eps, eps, np.conj(A))
+    assert np.abs(B - want).max() < 1e-11 * np.abs(B).max()
+    assert np.allclose(C_avg[:, 1], np.mean([C[:, (y + 1) % 4, y] for y in range(4)], axis=0))
+    # pseudoscalar: Gt(g5) = -g5, so C = +Tr[S(x,y) S(x,y)^dag] > 0
+    assert np.abs(C[0].imag).max() < 1e-11 * np.abs(C[0]).max() and np.all(C[0].real > 0)
+
+
+def test_nr_estimator_selects_block_size_per_separation():
+    T = 6
+    conn = np.arange(2 * T).reshape(2, T).astype(complex)
+    disc = 100 + np.zeros((2, T), complex)
+    dC = np.array([1000 + np.zeros((2, T)), 2000 + np.zeros((2, T))], dtype=complex)
+    out = nr_estimator(conn, disc, dC, [-1, -1, 0, 0, 1, 1])
+    assert np.array_equal(out[:, :2], conn[:, :2] + 100)
+    assert np.array_equal(out[:, 2:4], conn[:, 2:4] + 1000)
+    assert np.array_equal(out[:, 4:], conn[:, 4:] + 2000)
 
 
 def test_loops_gauge_invariant_and_real():
