@@ -219,9 +219,26 @@ int lqcd_conn_correlator(lqcd_ctx* ctx, const double* tau_all, int n_ev, const i
 int lqcd_nr_estimator(lqcd_ctx* ctx, const double* C_conn_avg, const double* C_disc_avg, const double* dC_avg,
                       int n_delta, int n_gamma, const int* delta_of_dt, double* C_nr, int where);
 
+/* APE smearing of the spatial links for the distillation vectors (Sec. 3.1 computes them on
+ * APE-smeared links; the paper gives no parameters, so they are inputs).  n_iter steps of
+ *   X_k(x) = (1 - alpha) U_k(x) + (alpha/4) sum_{j != k spatial} [U_j(x) U_k(x+j) U_j(x+k)^dag
+ *                                                + U_j(x-j)^dag U_k(x-j) U_j(x-j+k)],
+ *   U'_k(x) = X W-projected onto SU(3): W = X (X^dag X)^(-1/2) divided by det(W)^(1/3)
+ * (principal root), k = x, y, z, in FP64, starting from the uploaded links each call.  The
+ * smeared field is kept in the context and used by lqcd_laplace_eigs until the next
+ * lqcd_gauge_upload or a call with n_iter = 0.  The Dirac operator never uses it.  Errors:
+ * INVALID_ARG (n_iter < 0, alpha outside [0, 1]), STATE (no gauge field), NAN (a staple sum with
+ * no polar factor). */
+int lqcd_ape_smear(lqcd_ctx* ctx, double alpha, int n_iter);
+
+/* The smeared spatial links: out [V][3 (k = x, y, z)][3][3] complex, site order of the links.
+ * Errors: STATE (no smeared field). */
+int lqcd_smeared_links(lqcd_ctx* ctx, double* out, int where);
+
 /* Distillation vectors (Sec. 3.1, 3.2): the n_ev lowest eigenpairs of the gauge-covariant 3D
  * Laplacian  (-Lap phi)(x) = sum_k [2 phi(x) - U_k(x) phi(x+k) - U_k(x-k)^dag phi(x-k)]  on every
- * timeslice of the uploaded gauge field, to residual ||(-Lap) v - lambda v|| <= tol (0 -> 1e-10).
+ * timeslice of the uploaded gauge field (of its APE-smeared spatial links after lqcd_ape_smear),
+ * to residual ||(-Lap) v - lambda v|| <= tol (0 -> 1e-10).
  *   V:      [Lt][n_ev][Lx Ly Lz][3] complex, unit norm, largest-modulus component (first on ties)
  *           made real positive;   lambda: [Lt][n_ev] real, ascending per timeslice.
  *   iters (may be NULL): filter iterations of the slowest timeslice chunk.

@@ -13,6 +13,7 @@ complex128, with no blocking, fusion or reordering beyond what the definitions s
 * ``dirac``   site indexing, even-odd and domain tables, clover-improved Wilson operator D,
               its adjoint, the Dirichlet domain operator D_Lambda (Sec. 2.1), dense D.
 * ``solve``   CG on the normal equations and dense LU solves.
+* ``smear``   spatial APE smearing with the polar-factor SU(3) projection (Sec. 3.1 smeared links).
 * ``distill`` covariant 3D Laplacian eigenvectors, distillation sources, perambulators
               tau = V^dagger D^{-1} V, quark loops (Sec. 2, Sec. 3.1-3.2) and the full,
               completely factorised and subtracted disconnected correlators (Eqs. Cdisc,

@@ -410,7 +410,7 @@ int lqcd_destroy(lqcd_ctx* c) {
   flush_phase_times(c);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
-  void* bufs[] = {c->U64, c->U32, c->U16, c->A64, c->Ainv64, c->Ainv32, c->Ainv16, c->A32,
+  void* bufs[] = {c->U64, c->U32, c->U16, c->Usm, c->A64, c->Ainv64, c->Ainv32, c->Ainv16, c->A32,
                   c->d_tc_full, c->d_tc_dom, c->d_seg_full, c->d_seg_dom, c->d_gamma, c->d_coord,
                   c->nn_weights, c->nn_w16, c->nn_m, c->nn_v};
   for (void* p : bufs)
@@ -463,7 +463,28 @@ int lqcd_gauge_upload(lqcd_ctx* c, const double* links, int where, double kappa,
   if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, std::string("gauge_upload: ") + cudaGetErrorString(e));
   if (hb) return set_error(c, LQCD_ERR_NAN, "gauge_upload: singular clover block");
   c->have_gauge = true;
+  c->have_smeared = false;  // a new field drops the previous smearing
   return LQCD_OK;
+}
+
+int lqcd_ape_smear(lqcd_ctx* c, double alpha, int n_iter) {
+  if (!c || n_iter < 0 || !(alpha >= 0.0 && alpha <= 1.0))
+    return set_error(c, LQCD_ERR_INVALID_ARG, "ape_smear: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "ape_smear: no gauge field uploaded");
+  Scope sc(c);
+  return ape_smear(c, alpha, n_iter);
+}
+
+int lqcd_smeared_links(lqcd_ctx* c, double* out, int where) {
+  if (!c || !out) return set_error(c, LQCD_ERR_INVALID_ARG, "smeared_links: bad arguments");
+  if (!c->have_smeared) return set_error(c, LQCD_ERR_STATE, "smeared_links: no smeared field");
+  Scope sc(c);
+  const size_t bytes = (size_t)c->V * 27 * sizeof(double2);
+  double2* dout = (double2*)stage_out(c, out, bytes, where, "h_sm");
+  if (!dout) return set_error(c, LQCD_ERR_OOM, "smeared_links: out of device memory");
+  unpack_smeared(c, dout);
+  if (int e = cuda_check(c, "smeared_links")) return e;
+  return finish_out(c, out, dout, bytes, where);
 }
 
 int lqcd_set_domains(lqcd_ctx* c, const int* extents, int n_dom) { return lqcd_set_domains_at(c, 0, extents, n_dom); }

@@ -277,7 +277,8 @@ static void lap_apply(lqcd_ctx* c, const double2* X, const double2* Z, double2* 
                       double b, double cc) {
   const long L3 = (long)c->g.Lx * c->g.Ly * c->g.Lz;
   long n = (long)nt * L3 * m;
-  k_lap<<<(n + 255) / 256, 256, 0, c->work>>>(X, Z, out, (const double2*)c->U64, c->g, t0, nt, m, a, b, cc);
+  const double2* U = (const double2*)(c->have_smeared ? c->Usm : c->U64);  // smeared links if present
+  k_lap<<<(n + 255) / 256, 256, 0, c->work>>>(X, Z, out, U, c->g, t0, nt, m, a, b, cc);
   count_launch();
 }
 

@@ -120,6 +120,9 @@ struct lqcd_ctx {
   void* U64 = nullptr;
   void* U32 = nullptr;
   void* U16 = nullptr;
+  // APE-smeared spatial links (FP64, layout of U64 for mu < 3), used by the Laplacian eigensolver
+  void* Usm = nullptr;
+  bool have_smeared = false;
   // clover A and A^-1 per parity: [par][chir][chunks][Vh]
   void* A64 = nullptr;
   void* Ainv64 = nullptr;
@@ -197,6 +200,9 @@ void set_capturing(bool on);
 void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes);
 void* pinned_get(lqcd_ctx* c, size_t bytes);
 int set_error(lqcd_ctx* c, int code, const std::string& msg);
+// smear.cu: spatial APE smearing of the uploaded links into c->Usm; unpack to [V][3][3][3]
+int ape_smear(lqcd_ctx* c, double alpha, int n_iter);
+void unpack_smeared(lqcd_ctx* c, double2* out);
 size_t clover_bytes(const Geom& g, int prec);   // one parity
 size_t link_bytes(const Geom& g, int prec);     // all mu, both parities
 size_t spinor_bytes(const Geom& g, int prec, int nrhs);  // one parity

@@ -34,7 +34,7 @@ EXPORTED = [
     "lqcd_dslash_bench", "lqcd_kernel_launches", "lqcd_laplace_eigs", "lqcd_disc_correlator_noalloc",
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
     "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant", "lqcd_schur_apply",
-    "lqcd_conn_correlator", "lqcd_nr_estimator",
+    "lqcd_conn_correlator", "lqcd_nr_estimator", "lqcd_ape_smear", "lqcd_smeared_links",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -119,6 +119,8 @@ def load_library(path=_LIB_PATH):
                                    ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_stats)]),
         "lqcd_loops": (ip, [vp, vp, ip, ip, c_int_p, ip, vp, vp, vp, ip]),
         "lqcd_disc_correlator": (ip, [vp, vp, vp, vp, vp, ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, ip]),
+        "lqcd_ape_smear": (ip, [vp, ctypes.c_double, ip]),
+        "lqcd_smeared_links": (ip, [vp, vp, ip]),
         "lqcd_conn_correlator": (ip, [vp, vp, ip, c_int_p, ip, c_int_p, ip, vp, vp, ip]),
         "lqcd_nr_estimator": (ip, [vp, vp, vp, vp, ip, ip, c_int_p, vp, ip]),
         "lqcd_dslash_bench": (ip, [vp, ip, ip, ip, ip, dp, dp]),
@@ -310,6 +312,14 @@ class Context:
             self.h, _ptr(L), _ptr(Lt), _ptr(Ld), _ptr(Ltd), n_cfg, n_g, int(vev), _ptr(out["C"]),
             _ptr(out["Cdd"]), _ptr(out["dC"]), _ptr(out["C_avg"]), _ptr(out["dC_avg"]),
             _ptr(out["valid"], np.int32), _ptr(out["n_valid"], np.int32), _ptr(terms), w))
+
+    def ape_smear(self, alpha, n_iter):
+        """Smear the spatial links (used by laplace_eigs); n_iter = 0 drops the smearing."""
+        return self._check(_lib.lqcd_ape_smear(self.h, float(alpha), int(n_iter)))
+
+    def smeared_links(self, out):
+        """out[t, z, y, x, k, 3, 3] (k = x, y, z): the smeared spatial links."""
+        return self._check(_lib.lqcd_smeared_links(self.h, _ptr(out), _where(out)))
 
     def conn_correlator(self, tau_all, n_ev, t_src, gamma_ids, C, C_avg=None):
         """C[g, x0, k] (and C_avg[g, dt]) from all-sink perambulators tau_all[k, t', i, a, j, b]."""
