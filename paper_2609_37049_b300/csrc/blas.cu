@@ -233,21 +233,6 @@ __global__ void k_bicg_fin_init(const double* partial, VGeom vg, const SegInfo* 
   ks.active[sys] = (s[0] > 0.0) && (!outer_active || outer_active[sys]);
 }
 
-// partial (r0, v)
-template <int P>
-__global__ void k_dot(const void* a, const void* b, VGeom vg, const SegInfo* si, double* partial) {
-  using R = typename Traits<P>::real;
-  VThread v = vthread(vg, si);
-  cplx<R> x[12], y[12];
-  load_spinor<P>(a, v.stride, v.idx, x);
-  load_spinor<P>(b, v.stride, v.idx, y);
-  cplx<R> s = {R(0), R(0)};
-#pragma unroll
-  for (int k = 0; k < 12; k++) s = s + cjmul(x[k], y[k]);
-  double d[2] = {(double)s.re, (double)s.im};
-  block_reduce<2>(d, partial, vg, v.site_local, v.rhs);
-}
-
 LQCD_D double2 cdiv(double2 a, double2 b) {
   double den = b.x * b.x + b.y * b.y;
   return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
@@ -290,120 +275,81 @@ __global__ void k_bicg_s(const void* r, const void* vv, void* s, VGeom vg, const
   store_spinor<P>(s, v.stride, v.idx, x);
 }
 
-// partial (t, s), (t, t)
-template <int P>
-__global__ void k_dot_ts(const void* t, const void* s, VGeom vg, const SegInfo* si, double* partial) {
-  using R = typename Traits<P>::real;
-  VThread v = vthread(vg, si);
-  cplx<R> x[12], y[12];
-  load_spinor<P>(t, v.stride, v.idx, x);
-  load_spinor<P>(s, v.stride, v.idx, y);
-  cplx<R> ts = {R(0), R(0)};
-  R tt = 0;
-#pragma unroll
-  for (int k = 0; k < 12; k++) {
-    ts = ts + cjmul(x[k], y[k]);
-    tt += norm2(x[k]);
-  }
-  double d[3] = {(double)ts.re, (double)ts.im, (double)tt};
-  block_reduce<3>(d, partial, vg, v.site_local, v.rhs);
-}
-
-__global__ void k_bicg_fin_omega(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks) {
-  double s[3];
-  seg_sum<3>(partial, vg, si, s);
-  if (threadIdx.x) return;
-  const int sys = blockIdx.x * nseg + blockIdx.y;
-  if (!ks.active[sys] || !(s[2] > 0.0) || !isfinite(s[2])) {
-    ks.omega[sys] = make_double2(0.0, 0.0);
-    return;
-  }
-  ks.omega[sys] = make_double2(s[0] / s[2], s[1] / s[2]);
-}
-
-// x += alpha p + omega s; r = s - omega t; partial (r0, r), (r, r)
-template <int P>
-__global__ void k_bicg_xr(void* x, const void* p, const void* s, const void* t, void* r, const void* r0, VGeom vg,
-                          const SegInfo* si, int nseg, KState ks, double* partial) {
-  using R = typename Traits<P>::real;
-  VThread v = vthread(vg, si);
-  const int sys = v.rhs * nseg + v.seg;
-  double2 al = ks.alpha[sys], om = ks.omega[sys];
-  cplx<R> a = {(R)al.x, (R)al.y}, w = {(R)om.x, (R)om.y};
-  cplx<R> xv[12], pv[12], sv[12], tv[12];
-  load_spinor<P>(x, v.stride, v.idx, xv);
-  load_spinor<P>(p, v.stride, v.idx, pv);
-  load_spinor<P>(s, v.stride, v.idx, sv);
-  load_spinor<P>(t, v.stride, v.idx, tv);
-#pragma unroll
-  for (int k = 0; k < 12; k++) {
-    xv[k] = xv[k] + a * pv[k] + w * sv[k];
-    sv[k] = sv[k] - w * tv[k];  // new r
-  }
-  store_spinor<P>(x, v.stride, v.idx, xv);
-  store_spinor<P>(r, v.stride, v.idx, sv);
-  cplx<R> r0v[12];
-  load_spinor<P>(r0, v.stride, v.idx, r0v);
-  cplx<R> d0 = {R(0), R(0)};
-  R rr = 0;
-#pragma unroll
-  for (int k = 0; k < 12; k++) {
-    d0 = d0 + cjmul(r0v[k], sv[k]);
-    rr += norm2(sv[k]);
-  }
-  double d[3] = {(double)d0.re, (double)d0.im, (double)rr};
-  block_reduce<3>(d, partial, vg, v.site_local, v.rhs);
-}
-
-__global__ void k_bicg_fin_beta(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks) {
-  double s[3];
-  seg_sum<3>(partial, vg, si, s);
+// One reduction phase per BiCGStab iteration: after t = M s, whose fused reduction gives
+// (t,s), (t,t), (r0,t), (r0,s), (s,s), every scalar of the iteration is known:
+//   omega = (t,s)/(t,t),  rho' = (r0, s - omega t) = (r0,s) - omega (r0,t),
+//   beta = (rho'/rho)(alpha/omega),  |r'|^2 = |s|^2 - |(t,s)|^2/(t,t)  (stopping test),
+// so x, r and p are updated in one pass (k_bicg_xrp) instead of two with a reduction between.
+__global__ void k_bicg_fin_tail(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+  double s[8];
+  seg_sum<8>(partial, vg, si, s);
   if (threadIdx.x) return;
   const int sys = blockIdx.x * nseg + blockIdx.y;
   if (!ks.active[sys]) {
+    ks.omega[sys] = make_double2(0.0, 0.0);
     ks.beta[sys] = make_double2(0.0, 0.0);
     return;
   }
-  double2 rho_new = make_double2(s[0], s[1]);
-  ks.r2[sys] = s[2];
+  const double tt = s[2];
+  if (!(tt > 0.0) || !isfinite(tt)) {  // t = 0 (s = 0) or overflow: stop this system
+    ks.omega[sys] = make_double2(0.0, 0.0);
+    ks.beta[sys] = make_double2(0.0, 0.0);
+    ks.active[sys] = 0;
+    ks.flag[sys] = isfinite(tt) ? 1 : 2;
+    ks.iters[sys] += 1;
+    return;
+  }
+  const double2 om = make_double2(s[0] / tt, s[1] / tt);
+  ks.omega[sys] = om;
+  const double2 rho_new = make_double2(s[5] - (om.x * s[3] - om.y * s[4]), s[6] - (om.x * s[4] + om.y * s[3]));
+  double r2 = s[7] - (s[0] * s[0] + s[1] * s[1]) / tt;
+  r2 = r2 > 0.0 ? r2 : 0.0;
+  ks.r2[sys] = r2;
   ks.iters[sys] += 1;
-  double2 om = ks.omega[sys], rho = ks.rho[sys];
-  if (!isfinite(s[2])) {
+  ks.beta[sys] = make_double2(0.0, 0.0);
+  if (!isfinite(r2) || !isfinite(s[7])) {
     ks.active[sys] = 0;
     ks.flag[sys] = 2;
-    ks.beta[sys] = make_double2(0.0, 0.0);
     return;
   }
-  if (s[2] <= ks.stop2[sys]) {
+  if (r2 <= ks.stop2[sys]) {  // converged: this iteration's x and r updates still apply
     ks.active[sys] = 0;
-    ks.beta[sys] = make_double2(0.0, 0.0);
     return;
   }
-  double om2 = om.x * om.x + om.y * om.y, rh2 = rho.x * rho.x + rho.y * rho.y;
+  const double2 rho = ks.rho[sys];
+  const double om2 = om.x * om.x + om.y * om.y, rh2 = rho.x * rho.x + rho.y * rho.y;
   if (!(om2 > 0.0) || !(rh2 > 0.0)) {
     ks.active[sys] = 0;
     ks.flag[sys] = 1;
-    ks.beta[sys] = make_double2(0.0, 0.0);
     return;
   }
   ks.beta[sys] = cmul2(cdiv(rho_new, rho), cdiv(ks.alpha[sys], om));
   ks.rho[sys] = rho_new;
 }
 
-// p = r + beta (p - omega v)
+// x += alpha p + omega s;  r = s - omega t;  p = r + beta (p - omega v)
 template <int P>
-__global__ void k_bicg_p(void* p, const void* r, const void* vv, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+__global__ void k_bicg_xrp(void* x, void* p, const void* s, const void* t, void* r, const void* vv, VGeom vg,
+                           const SegInfo* si, int nseg, KState ks) {
   using R = typename Traits<P>::real;
   VThread v = vthread(vg, si);
   const int sys = v.rhs * nseg + v.seg;
-  double2 be = ks.beta[sys], om = ks.omega[sys];
-  cplx<R> b = {(R)be.x, (R)be.y}, w = {(R)om.x, (R)om.y};
-  cplx<R> pv[12], rv[12], vv2[12];
+  const double2 al = ks.alpha[sys], om = ks.omega[sys], be = ks.beta[sys];
+  const cplx<R> a = {(R)al.x, (R)al.y}, w = {(R)om.x, (R)om.y}, bt = {(R)be.x, (R)be.y};
+  cplx<R> xv[12], pv[12], sv[12], tv[12], vv2[12];
+  load_spinor<P>(x, v.stride, v.idx, xv);
   load_spinor<P>(p, v.stride, v.idx, pv);
-  load_spinor<P>(r, v.stride, v.idx, rv);
+  load_spinor<P>(s, v.stride, v.idx, sv);
+  load_spinor<P>(t, v.stride, v.idx, tv);
   load_spinor<P>(vv, v.stride, v.idx, vv2);
 #pragma unroll
-  for (int k = 0; k < 12; k++) pv[k] = rv[k] + b * (pv[k] - w * vv2[k]);
+  for (int k = 0; k < 12; k++) {
+    xv[k] = xv[k] + a * pv[k] + w * sv[k];
+    sv[k] = sv[k] - w * tv[k];                     // new r
+    pv[k] = sv[k] + bt * (pv[k] - w * vv2[k]);      // new p
+  }
+  store_spinor<P>(x, v.stride, v.idx, xv);
+  store_spinor<P>(r, v.stride, v.idx, sv);
   store_spinor<P>(p, v.stride, v.idx, pv);
 }
 
@@ -499,21 +445,9 @@ void bicg_init(int prec, const void* b, void* r, void* p, void* x, const VGeom& 
   k_bicg_fin_init<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks, delta, outer_active); lqcd::count_launch();
 }
 
-void bicg_alpha(int prec, const void* r0, const void* v, const VGeom& vg, const SegInfo* si, int nseg,
-                double* partial, const KState& ks, cudaStream_t st) {
-  DISPATCH_P(prec, k_dot, <<<vg.blocks, vg.threads(), shm(vg, 2), st>>>(r0, v, vg, si, partial));
-  k_bicg_fin_alpha<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
-}
-
 void bicg_s(int prec, const void* r, const void* v, void* s, const VGeom& vg, const SegInfo* si, int nseg,
             const KState& ks, cudaStream_t st) {
   DISPATCH_P(prec, k_bicg_s, <<<vg.blocks, vg.threads(), 0, st>>>(r, v, s, vg, si, nseg, ks));
-}
-
-void bicg_omega(int prec, const void* t, const void* s, const VGeom& vg, const SegInfo* si, int nseg,
-                double* partial, const KState& ks, cudaStream_t st) {
-  DISPATCH_P(prec, k_dot_ts, <<<vg.blocks, vg.threads(), shm(vg, 3), st>>>(t, s, vg, si, partial));
-  k_bicg_fin_omega<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
 }
 
 // Finishing kernels alone, for partial sums produced by a dslash with fused reductions.
@@ -522,22 +456,12 @@ void bicg_fin_alpha_only(const double* partial, const VGeom& vg, const SegInfo* 
   k_bicg_fin_alpha<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
   lqcd::count_launch();
 }
-void bicg_fin_omega_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
-                         cudaStream_t st) {
-  k_bicg_fin_omega<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
-  lqcd::count_launch();
-}
 
-void bicg_xr(int prec, void* x, const void* p, const void* s, const void* t, void* r, const void* r0,
-             const VGeom& vg, const SegInfo* si, int nseg, double* partial, const KState& ks, cudaStream_t st) {
-  DISPATCH_P(prec, k_bicg_xr,
-             <<<vg.blocks, vg.threads(), shm(vg, 3), st>>>(x, p, s, t, r, r0, vg, si, nseg, ks, partial));
-  k_bicg_fin_beta<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
-}
-
-void bicg_p(int prec, void* p, const void* r, const void* v, const VGeom& vg, const SegInfo* si, int nseg,
-            const KState& ks, cudaStream_t st) {
-  DISPATCH_P(prec, k_bicg_p, <<<vg.blocks, vg.threads(), 0, st>>>(p, r, v, vg, si, nseg, ks));
+void bicg_tail(int prec, void* x, void* p, const void* s, const void* t, void* r, const void* v,
+               const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
+               cudaStream_t st) {
+  k_bicg_fin_tail<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
+  DISPATCH_P(prec, k_bicg_xrp, <<<vg.blocks, vg.threads(), 0, st>>>(x, p, s, t, r, v, vg, si, nseg, ks));
 }
 
 void count_active(const int* active, int n, int* count, cudaStream_t st) {

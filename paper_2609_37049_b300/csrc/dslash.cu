@@ -148,7 +148,7 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int vari
     // one block = red_sites sites (inside one timeslice) x nrhs right-hand sides (<= 128 threads)
     const int tpb = c.red_sites * c.nrhs;
     const long blocks = g.Vh / c.red_sites;
-    const int nd = c.red == RED_DOT_Z ? 2 : 3;
+    const int nd = c.red == RED_DOT_Z ? 2 : (c.red == RED_TS_R0 ? 8 : 3);
     const size_t shm = (size_t)nd * tpb * sizeof(double);
     if (variant >= 3) {
       if (launch_dslash_staged(pr, c.prec, c.epi, dag, c.red, blocks, tpb, shm, variant, st)) return;
@@ -156,6 +156,8 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int vari
     }
     if (c.red == RED_DOT_Z)
       launch_prec<RED_DOT_Z>(c.prec, pr, c.epi, dag, blocks, tpb, shm, variant, st);
+    else if (c.red == RED_TS_R0)
+      launch_prec<RED_TS_R0>(c.prec, pr, c.epi, dag, blocks, tpb, shm, variant, st);
     else
       launch_prec<RED_DOT_Y_NORM>(c.prec, pr, c.epi, dag, blocks, tpb, shm, variant, st);
   }

@@ -241,6 +241,22 @@ LQCD_D void dslash_epilogue(const DslashParams& pr, long cb, long idx, long stri
     for (int k = 0; k < 12; k++) d = d + cjmul(zv[k], o[k]);
     double v[2] = {(double)d.re, (double)d.im};
     block_reduce_rhs<2>(v, pr.partial, pr.S, pr.nrhs, (int)(threadIdx.x / pr.nrhs), rhs);
+  } else if constexpr (RED == RED_TS_R0) {  // (out, y), (out, out), (z, out), (z, y), (y, y)
+    cplx<R> zv[12];
+    load_spinor<P>(pr.zred, stride, idx, zv);
+    cplx<R> ty = {R(0), R(0)}, zo = {R(0), R(0)}, zy = {R(0), R(0)};
+    R oo = 0, yy = 0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      ty = ty + cjmul(o[k], yv[k]);
+      zo = zo + cjmul(zv[k], o[k]);
+      zy = zy + cjmul(zv[k], yv[k]);
+      oo += norm2(o[k]);
+      yy += norm2(yv[k]);
+    }
+    double v[8] = {(double)ty.re, (double)ty.im, (double)oo, (double)zo.re,
+                   (double)zo.im, (double)zy.re, (double)zy.im, (double)yy};
+    block_reduce_rhs<8>(v, pr.partial, pr.S, pr.nrhs, (int)(threadIdx.x / pr.nrhs), rhs);
   } else if constexpr (RED == RED_DOT_Y_NORM) {  // (out, y), (out, out); y is the EPI_Y_* input
     cplx<R> d = {R(0), R(0)};
     R nn = 0;

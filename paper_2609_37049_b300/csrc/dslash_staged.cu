@@ -361,7 +361,10 @@ void launch_sl(const DslashParams& pr, long blocks, size_t shm, cudaStream_t st)
 
 template <int P, int MINB>
 bool launch_sl_e(const DslashParams& pr, int epi, int red, long blocks, size_t shm, cudaStream_t st) {
-  if (red == RED_DOT_Z) {
+  if (red == RED_TS_R0) {
+    if (epi != EPI_Y_CH) return false;
+    launch_sl<P, EPI_Y_CH, RED_TS_R0, MINB>(pr, blocks, shm, st);
+  } else if (red == RED_DOT_Z) {
     if (epi != EPI_Y_CH) return false;
     launch_sl<P, EPI_Y_CH, RED_DOT_Z, MINB>(pr, blocks, shm, st);
   } else if (red == RED_DOT_Y_NORM) {
@@ -420,6 +423,7 @@ void launch_k(const DslashParams& pr, long blocks, int tpb, size_t shm, cudaStre
 
 template <int P, int NS>
 bool launch_ns(const DslashParams& pr, int epi, int red, long blocks, int tpb, size_t shm, cudaStream_t st) {
+  if (red != RED_NONE && red != RED_DOT_Z && red != RED_DOT_Y_NORM) return false;  // direct kernel instead
   if (red == RED_DOT_Z) {
     if (epi != EPI_Y_CH) return false;
     launch_k<P, EPI_Y_CH, RED_DOT_Z, NS>(pr, blocks, tpb, shm, st);

@@ -113,10 +113,9 @@ static void bicg_iteration(lqcd_ctx* c, const Inner& in, cudaStream_t st) {
   schur(c, in, in.p, in.v, RED_DOT_Z, in.b, st);  // v = M p, partial (r0, v)
   bicg_fin_alpha_only(in.partial, in.vg, in.si, in.nseg, in.ks, st);
   bicg_s(P, in.r, in.v, in.s, in.vg, in.si, in.nseg, in.ks, st);
-  schur(c, in, in.s, in.t, RED_DOT_Y_NORM, nullptr, st);  // t = M s, partial (t, s), (t, t)
-  bicg_fin_omega_only(in.partial, in.vg, in.si, in.nseg, in.ks, st);
-  bicg_xr(P, in.x, in.p, in.s, in.t, in.r, in.b, in.vg, in.si, in.nseg, in.partial, in.ks, st);
-  bicg_p(P, in.p, in.r, in.v, in.vg, in.si, in.nseg, in.ks, st);
+  // t = M s, partial (t, s), (t, t), (r0, t), (r0, s), (s, s): the iteration's last reduction
+  schur(c, in, in.s, in.t, RED_TS_R0, in.b, st);
+  bicg_tail(P, in.x, in.p, in.s, in.t, in.r, in.v, in.partial, in.vg, in.si, in.nseg, in.ks, st);
 }
 
 static std::string graph_key(const Inner& in, int chunk) {

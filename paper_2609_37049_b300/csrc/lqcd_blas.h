@@ -13,20 +13,14 @@ void v_zero(int prec, void* x, const VGeom& vg, cudaStream_t st);
 void v_copy(int prec, const void* a, void* b, const VGeom& vg, cudaStream_t st);
 void bicg_init(int prec, const void* b, void* r, void* p, void* x, const VGeom& vg, const SegInfo* si, int nseg,
                double* partial, const KState& ks, const double* delta, const int* outer_active, cudaStream_t st);
-void bicg_alpha(int prec, const void* r0, const void* v, const VGeom& vg, const SegInfo* si, int nseg,
-                double* partial, const KState& ks, cudaStream_t st);
 void bicg_s(int prec, const void* r, const void* v, void* s, const VGeom& vg, const SegInfo* si, int nseg,
             const KState& ks, cudaStream_t st);
-void bicg_omega(int prec, const void* t, const void* s, const VGeom& vg, const SegInfo* si, int nseg,
-                double* partial, const KState& ks, cudaStream_t st);
+// after t = M s with the RED_TS_R0 reduction in `partial`: all scalars, then x, r, p in one pass
+void bicg_tail(int prec, void* x, void* p, const void* s, const void* t, void* r, const void* v,
+               const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
+               cudaStream_t st);
 void bicg_fin_alpha_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
                          cudaStream_t st);
-void bicg_fin_omega_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
-                         cudaStream_t st);
-void bicg_xr(int prec, void* x, const void* p, const void* s, const void* t, void* r, const void* r0,
-             const VGeom& vg, const SegInfo* si, int nseg, double* partial, const KState& ks, cudaStream_t st);
-void bicg_p(int prec, void* p, const void* r, const void* v, const VGeom& vg, const SegInfo* si, int nseg,
-            const KState& ks, cudaStream_t st);
 void count_active(const int* active, int n, int* count, cudaStream_t st);
 
 // ---- flexible GCR and MR preconditioner (gcr.cu)

@@ -71,8 +71,10 @@ enum Epi {
 // Dot products fused into the epilogue (second half of the Schur operator, EPI_Y_CH only):
 //   RED_DOT_Z:      partial (zred, out)             -> 2 doubles per (block, rhs)
 //   RED_DOT_Y_NORM: partial (out, y), (out, out)    -> 3 doubles per (block, rhs)
+//   RED_TS_R0:      partial (out, y), (out, out), (zred, out), (zred, y), (y, y)
+//                                                   -> 8 doubles per (block, rhs)
 // with blocks of red_sites sites x nrhs (the VGeom blocks of the same batch).
-enum Red { RED_NONE = 0, RED_DOT_Z = 1, RED_DOT_Y_NORM = 2 };
+enum Red { RED_NONE = 0, RED_DOT_Z = 1, RED_DOT_Y_NORM = 2, RED_TS_R0 = 3 };
 
 struct DslashCall {
   int prec;
