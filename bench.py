@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-dslash", action="store_true",
                     help="only time the dslash kernels of the workload (small command for ncu captures)")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="set up the workload, run one warm step and one step inside the NVTX range "
+                         "'bench_step' (for ncu --nvtx-include), print no bench line")
     ap.add_argument("--dslash-variant", type=int, default=-1,
                     help="with --profile-dslash: time only this launch variant (default: all)")
     return ap.parse_args()
@@ -266,6 +269,15 @@ def run_ours(args, rank, world):
         ctx.disc_correlator(loopsF, loopsFt, loopsD, loopsDt, 0, corr)
 
     rhs_per_step = 2 * n_grp * N_EV * 4
+    if args.profile_step:  # one warm step, then one step inside an NVTX range for an ncu launch list
+        step(0)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_step")
+        step(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_step": "done", "rhs": rhs_per_step}), flush=True)
+        return
     for s in range(args.warmup):
         step(s)
     torch.cuda.synchronize()
@@ -454,7 +466,7 @@ def main():
             print(json.dumps(run_reference(args)), flush=True)
         return
     res = run_ours(args, rank, world)
-    if rank == 0:
+    if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
 
 
