@@ -121,6 +121,69 @@ LQCD_D void seg_sum(const double* partial, const VGeom& vg, const SegInfo* si, d
   }
 }
 
+// Two-level segment sums for the BiCGStab scalars (one parity, vg.npar = 1).  The per-block
+// partials of a segment are first summed over chunks of kChunk consecutive blocks, threads over
+// the (rhs, k) entries of a block so that every read is coalesced; the finishing kernel of a
+// system then adds its segment's chunk sums.  Fixed order: deterministic.
+constexpr int kChunk = 64;
+
+template <int ND>
+__global__ void k_chunk_sum(const double* partial, VGeom vg, const SegInfo* si, int nchunk, double* p2) {
+  const int c = blockIdx.x, seg = blockIdx.y;
+  const int e = threadIdx.x;  // rhs * ND + k
+  if (e >= vg.nrhs * ND) return;
+  const long t0 = si ? si->t0[seg] : 0, t1 = si ? si->t1[seg] : vg.g.Lt;
+  const long u0 = si ? si->t0b[seg] : 0, u1 = si ? si->t1b[seg] : 0;
+  const long n0 = (t1 - t0) * vg.bpt, n1 = (u1 - u0) * vg.bpt;
+  const long f0 = (long)c * kChunk, f1 = min(f0 + kChunk, n0 + n1);
+  const long w = (long)vg.nrhs * ND;
+  double acc = 0;
+#pragma unroll 8
+  for (long f = f0; f < f1; f++) {
+    const long b = f < n0 ? t0 * vg.bpt + f : u0 * vg.bpt + (f - n0);
+    acc += partial[b * w + e];
+  }
+  p2[((long)seg * nchunk + c) * w + e] = acc;
+}
+
+// Sum of the chunk sums of system (rhs = blockIdx.x, seg = blockIdx.y); valid in thread 0.
+template <int ND>
+LQCD_D void chunk_total(const double* p2, int nchunk, int nrhs, double (&out)[ND]) {
+  __shared__ double sm[ND][128];
+  const int rhs = blockIdx.x, seg = blockIdx.y;
+  double acc[ND];
+#pragma unroll
+  for (int k = 0; k < ND; k++) acc[k] = 0.0;
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < ND; k++) acc[k] += p2[(((long)seg * nchunk + c) * nrhs + rhs) * ND + k];
+  }
+#pragma unroll
+  for (int k = 0; k < ND; k++) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s >= 1; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int k = 0; k < ND; k++) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < ND; k++) out[k] = sm[k][0];
+  }
+}
+
+// chunks needed by the largest segment of a half-lattice batch
+int seg_chunks(const VGeom& vg, const SegInfo& si_host) {
+  long most = 0;
+  for (int s = 0; s < si_host.nseg; s++) {
+    const long n = ((long)(si_host.t1[s] - si_host.t0[s]) + (si_host.t1b[s] - si_host.t0b[s])) * vg.bpt;
+    most = n > most ? n : most;
+  }
+  return (int)((most + kChunk - 1) / kChunk);
+}
+
 // ------------------------------------------------------------------ generic kernels
 template <int P>
 __global__ void k_norm2(const void* x, VGeom vg, const SegInfo* si, double* partial) {
@@ -239,9 +302,9 @@ LQCD_D double2 cdiv(double2 a, double2 b) {
 }
 LQCD_D double2 cmul2(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
-__global__ void k_bicg_fin_alpha(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+__global__ void k_bicg_fin_alpha(const double* p2, int nchunk, int nrhs, int nseg, KState ks) {
   double s[2];
-  seg_sum<2>(partial, vg, si, s);
+  chunk_total<2>(p2, nchunk, nrhs, s);
   if (threadIdx.x) return;
   const int sys = blockIdx.x * nseg + blockIdx.y;
   double2 r0v = make_double2(s[0], s[1]);
@@ -280,9 +343,9 @@ __global__ void k_bicg_s(const void* r, const void* vv, void* s, VGeom vg, const
 //   omega = (t,s)/(t,t),  rho' = (r0, s - omega t) = (r0,s) - omega (r0,t),
 //   beta = (rho'/rho)(alpha/omega),  |r'|^2 = |s|^2 - |(t,s)|^2/(t,t)  (stopping test),
 // so x, r and p are updated in one pass (k_bicg_xrp) instead of two with a reduction between.
-__global__ void k_bicg_fin_tail(const double* partial, VGeom vg, const SegInfo* si, int nseg, KState ks) {
+__global__ void k_bicg_fin_tail(const double* p2, int nchunk, int nrhs, int nseg, KState ks) {
   double s[8];
-  seg_sum<8>(partial, vg, si, s);
+  chunk_total<8>(p2, nchunk, nrhs, s);
   if (threadIdx.x) return;
   const int sys = blockIdx.x * nseg + blockIdx.y;
   if (!ks.active[sys]) {
@@ -451,16 +514,18 @@ void bicg_s(int prec, const void* r, const void* v, void* s, const VGeom& vg, co
 }
 
 // Finishing kernels alone, for partial sums produced by a dslash with fused reductions.
-void bicg_fin_alpha_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
-                         cudaStream_t st) {
-  k_bicg_fin_alpha<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks);
+void bicg_fin_alpha_only(const double* partial, double* p2, int nchunk, const VGeom& vg, const SegInfo* si,
+                         int nseg, const KState& ks, cudaStream_t st) {
+  k_chunk_sum<2><<<dim3(nchunk, nseg), vg.nrhs * 2, 0, st>>>(partial, vg, si, nchunk, p2); lqcd::count_launch();
+  k_bicg_fin_alpha<<<fin_grid(vg, nseg), 128, 0, st>>>(p2, nchunk, vg.nrhs, nseg, ks);
   lqcd::count_launch();
 }
 
 void bicg_tail(int prec, void* x, void* p, const void* s, const void* t, void* r, const void* v,
-               const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
-               cudaStream_t st) {
-  k_bicg_fin_tail<<<fin_grid(vg, nseg), 128, 0, st>>>(partial, vg, si, nseg, ks); lqcd::count_launch();
+               const double* partial, double* p2, int nchunk, const VGeom& vg, const SegInfo* si, int nseg,
+               const KState& ks, cudaStream_t st) {
+  k_chunk_sum<8><<<dim3(nchunk, nseg), vg.nrhs * 8, 0, st>>>(partial, vg, si, nchunk, p2); lqcd::count_launch();
+  k_bicg_fin_tail<<<fin_grid(vg, nseg), 128, 0, st>>>(p2, nchunk, vg.nrhs, nseg, ks); lqcd::count_launch();
   DISPATCH_P(prec, k_bicg_xrp, <<<vg.blocks, vg.threads(), 0, st>>>(x, p, s, t, r, v, vg, si, nseg, ks));
 }
 

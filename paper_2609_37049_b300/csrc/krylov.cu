@@ -111,18 +111,19 @@ int schur_apply(lqcd_ctx* c, int P, const void* x64, void* y64, int nrhs, int do
 static void bicg_iteration(lqcd_ctx* c, const Inner& in, cudaStream_t st) {
   const int P = in.prec;
   schur(c, in, in.p, in.v, RED_DOT_Z, in.b, st);  // v = M p, partial (r0, v)
-  bicg_fin_alpha_only(in.partial, in.vg, in.si, in.nseg, in.ks, st);
+  bicg_fin_alpha_only(in.partial, in.partial2, in.nchunk, in.vg, in.si, in.nseg, in.ks, st);
   bicg_s(P, in.r, in.v, in.s, in.vg, in.si, in.nseg, in.ks, st);
   // t = M s, partial (t, s), (t, t), (r0, t), (r0, s), (s, s): the iteration's last reduction
   schur(c, in, in.s, in.t, RED_TS_R0, in.b, st);
-  bicg_tail(P, in.x, in.p, in.s, in.t, in.r, in.v, in.partial, in.vg, in.si, in.nseg, in.ks, st);
+  bicg_tail(P, in.x, in.p, in.s, in.t, in.r, in.v, in.partial, in.partial2, in.nchunk, in.vg, in.si, in.nseg,
+            in.ks, st);
 }
 
 static std::string graph_key(const Inner& in, int chunk) {
   char buf[512];
-  snprintf(buf, sizeof buf, "bicg:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p", in.prec, in.nrhs, in.nseg,
-           chunk, in.variant, in.b, in.x, in.r, in.p, in.v, in.s, in.t, in.tmp, (void*)in.ks.rho, in.partial,
-           (const void*)in.tc, (const void*)in.si, in.U);
+  snprintf(buf, sizeof buf, "bicg:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p", in.prec, in.nrhs,
+           in.nseg, chunk, in.variant, in.nchunk, in.b, in.x, in.r, in.p, in.v, in.s, in.t, in.tmp,
+           (void*)in.ks.rho, in.partial, (void*)in.partial2, (const void*)in.tc, (const void*)in.si, in.U);
   return buf;
 }
 
@@ -366,6 +367,9 @@ int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain,
   in.ks.iters = in.ks.active + nsys;
   in.ks.flag = in.ks.iters + nsys;
   in.partial = partial;
+  in.nchunk = seg_chunks(vgH, domain ? c->seg_dom : c->seg_full);
+  in.partial2 = (double*)ws_get(c, "partial2", (size_t)nseg * in.nchunk * nrhs * 8 * sizeof(double));
+  if (!in.partial2) return set_error(c, LQCD_ERR_OOM, "solve: out of device memory");
   int* count_host = (int*)pinned_get(c, 64);
   cudaMemsetAsync(in.ks.iters, 0, nsys * sizeof(int), st);
 

@@ -15,12 +15,16 @@ void bicg_init(int prec, const void* b, void* r, void* p, void* x, const VGeom& 
                double* partial, const KState& ks, const double* delta, const int* outer_active, cudaStream_t st);
 void bicg_s(int prec, const void* r, const void* v, void* s, const VGeom& vg, const SegInfo* si, int nseg,
             const KState& ks, cudaStream_t st);
+// The BiCGStab finishing steps sum the fused-reduction partials in two levels through p2
+// ([nseg][nchunk][nrhs][ND] doubles, nchunk = seg_chunks of the batch, ND <= 8).
+int seg_chunks(const VGeom& vg, const SegInfo& si_host);
 // after t = M s with the RED_TS_R0 reduction in `partial`: all scalars, then x, r, p in one pass
 void bicg_tail(int prec, void* x, void* p, const void* s, const void* t, void* r, const void* v,
-               const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
-               cudaStream_t st);
-void bicg_fin_alpha_only(const double* partial, const VGeom& vg, const SegInfo* si, int nseg, const KState& ks,
-                         cudaStream_t st);
+               const double* partial, double* p2, int nchunk, const VGeom& vg, const SegInfo* si, int nseg,
+               const KState& ks, cudaStream_t st);
+// alpha = rho / (r0, v) after v = M p with the RED_DOT_Z reduction in `partial`
+void bicg_fin_alpha_only(const double* partial, double* p2, int nchunk, const VGeom& vg, const SegInfo* si,
+                         int nseg, const KState& ks, cudaStream_t st);
 void count_active(const int* active, int n, int* count, cudaStream_t st);
 
 // ---- flexible GCR and MR preconditioner (gcr.cu)
@@ -67,6 +71,8 @@ struct Inner {
   void *x, *r, *p, *v, *s, *t, *tmp;
   KState ks;
   double* partial;
+  double* partial2;  // chunk sums of the two-level reductions
+  int nchunk;
   double kappa;
   int variant;  // dslash launch variant (register cap)
 };
