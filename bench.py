@@ -379,6 +379,16 @@ def run_ours(args, rank, world):
                 "traffic": captured_traffic(v32), "peak_kind": peak_kind,
                 "kernel": "%s<P32,EPI_CH> (launch variant %d: eo hopping + A^-1, %d RHS)" % (kname, v32, RHS_BLOCK),
                 "algo_bytes_per_launch": dsl["f32"]["bytes"]}
+    # the FP64 hopping kernel of every true residual is bound by the FP64 pipe: 2 FP64 FMA per SM
+    # per clock; algorithmic flops 1320 (hopping) + 504 (clover) per output site and RHS
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f64_flops = 1824.0 * (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2) * 8
+    f64_peak = n_sm * 2 * 2 * 2.032e9 / 1e12
+    roofline_fp64 = {"bound": "alu", "kernel": "dslash_kernel<P64,EPI_CH> (8 RHS)", "unit": "TFLOP/s",
+                     "achieved": f64_flops / (dsl["f64"]["ms"] * 1e-3) / 1e12, "peak": f64_peak,
+                     "peak_kind": "derived: SMs x 2 FP64 FMA/clk x 2 flops x 2.032 GHz",
+                     "algo_flops_per_launch": f64_flops}
+    roofline_fp64["frac"] = roofline_fp64["achieved"] / f64_peak
 
     res = {"metric": "distillation RHS/s at FP64 resid 1e-10 (mixed FP64/FP32 solver)", "value": value,
            "unit": "RHS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -392,7 +402,7 @@ def run_ours(args, rank, world):
                             "403 MB and each FP64 full-lattice one 1.6 GB", "parallelism": "rhs-sharded x%d" % world},
            "e2e": e2e, "plain_fp64": plain, "mixed_same_sample_rhs_per_s": mixed_same,
            "speedup_vs_plain": mixed_same / plain["value"], "solvers": solvers, "tuning": tuning,
-           "dslash": dsl, "roofline": roofline,
+           "dslash": dsl, "roofline": roofline, "roofline_fp64": roofline_fp64,
            "clocks": clk.summary(), "gpu_launches": launches, "eigensolve_s": t_eig,
            "solver_stats": {"full_iters_per_step": stats["full"][-1][0], "dom_iters_per_step": stats["dom"][-1][0],
                             "max_true_resid": max(x[1] for x in stats["full"] + stats["dom"]),
