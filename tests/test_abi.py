@@ -67,3 +67,18 @@ def test_numpy_marshalling_checks():
     with pytest.raises(ValueError):
         lqcd._ptr(np.zeros(4, dtype=np.float64))
     assert lqcd._where(np.zeros(2, dtype=complex)) == lqcd.LQCD_HOST
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without the built library the binding raises instead of computing."""
+    with pytest.raises(ImportError):
+        lqcd.load_library(str(tmp_path / "liblqcd.so"))
+
+
+def test_product_never_imports_the_oracle():
+    """The package (binding, autotuner, sharding, build script) has no route to the oracle."""
+    pkg = os.path.join(ROOT, "paper_2609_37049_b300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            text = open(os.path.join(pkg, name)).read()
+            assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), name
