@@ -35,9 +35,21 @@ def _spinor_bytes(ctx, prec, nrhs):
     return ctx.volume // 2 * nrhs * 12 * per
 
 
+def _device_budget():
+    """60% of the device memory (the work vectors of one batch must fit beside the caller's)."""
+    try:
+        import torch
+        return int(0.6 * torch.cuda.mem_get_info()[1])
+    except Exception:
+        return 64 << 30
+
+
 def tune(ctx, cache=None, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F16, lqcd.LQCD_PREC_F64),
-         blocks=CANDIDATE_BLOCKS, memory_budget=64 << 30, retune=False):
-    """Tune (or load from `cache`) and install the launch choices on ctx; returns the choice dict."""
+         blocks=CANDIDATE_BLOCKS, memory_budget=None, retune=False):
+    """Tune (or load from `cache`) and install the launch choices on ctx; returns the choice dict.
+    memory_budget (bytes; default 60% of the device memory) bounds the RHS blocks tried."""
+    if memory_budget is None:
+        memory_budget = _device_budget()
     db = {}
     if cache and os.path.exists(cache) and not retune:
         with open(cache) as f:

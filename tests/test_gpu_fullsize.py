@@ -63,3 +63,29 @@ def test_fullsize_mixed_solve_true_residual(full, domain):
         for d in np.unique(dom):
             m = dom == d
             assert np.linalg.norm(r[k, m]) / np.linalg.norm(b[SAMPLE[k], m]) <= 1.02e-10, (k, d)
+
+
+def test_uneven_domains_24x48():
+    """The batched uneven-domain configuration at full size (24^3 x 48, eps 0.5, kappa 0.125,
+    domains of 6, 8, 10, 6, 8, 10 timeslices): one 16-RHS mixed domain solve, every domain of the
+    sampled RHS checked by the oracle's own D_Lambda to 1e-10."""
+    dims = (24, 24, 24, 48)
+    ext = [6, 8, 10, 6, 8, 10]
+    U = gauge_field(dims, 0.5, 9101)
+    ctx = Context(dims)
+    ctx.gauge_upload(U, 0.125, 1.6)
+    ctx.set_domains(ext)
+    b = random_spinors(dims, 16, 9102)
+    x = np.zeros_like(b)
+    st = Stats(16, len(ext))
+    ctx.solve(b, x, default_params(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F32, rhs_block=16),
+              domain=True, stats=st)
+    assert st.max_true_resid <= 1e-10
+    op = WilsonClover(U, 0.125, 1.6).restricted(ext)
+    dom = domain_of_t(ext, dims[3])
+    sample = [0, 15]
+    r = b[sample] - op.apply(x[sample])
+    for k in range(len(sample)):
+        for d in range(len(ext)):
+            m = dom == d
+            assert np.linalg.norm(r[k, m]) / np.linalg.norm(b[sample[k], m]) <= 1.02e-10, (k, d)
