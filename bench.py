@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--profile-step", action="store_true",
                     help="set up the workload, run one warm step and one step inside the NVTX range "
                          "'bench_step' (for ncu --nvtx-include), print no bench line")
+    ap.add_argument("--uneven-sample", action="store_true",
+                    help="time the 24^3x48 uneven-domain configuration (domains 6/8/10/6/8/10, 64 colour "
+                         "vectors): one domain-mode perambulator call over one source per domain and one "
+                         "full-mode source timeslice; prints one JSON line")
     ap.add_argument("--dslash-variant", type=int, default=-1,
                     help="with --profile-dslash: time only this launch variant (default: all)")
     return ap.parse_args()
@@ -103,6 +107,39 @@ def captured_traffic(variant):
     if not m or m.group(3) != h.hexdigest() or int(m.group(2)) != int(variant):
         return None
     return int(m.group(1))
+
+
+def uneven_sample():
+    """Mixed-precision perambulators at 24^3x48 with uneven domains (eps 0.5, kappa 0.125,
+    c_sw 1.6, N_ev = 64 seeded orthonormal colour vectors), autotuned launch variants."""
+    import torch
+    from lqcd_inputs import colour_vectors, gauge_field
+    from paper_2609_37049_b300 import Context, Stats, autotune, default_params, lqcd
+    dims, ext, n_ev = (24, 24, 24, 48), [6, 8, 10, 6, 8, 10], 64
+    torch.cuda.set_device(0)
+    ctx = Context(dims)
+    ctx.gauge_upload(gauge_field(dims, 0.5, 3001), KAPPA, CSW)
+    ctx.set_domains(ext)
+    tun = autotune.tune(ctx, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F64), blocks=(RHS_BLOCK,))
+    V = torch.from_numpy(colour_vectors(dims, n_ev, 3002)).cuda()
+    starts = [int(sum(ext[:d])) for d in range(len(ext))]
+    res = {}
+    for mode, name, ts in ((lqcd.LQCD_MODE_DOMAIN, "domain", starts), (lqcd.LQCD_MODE_FULL, "full", [0])):
+        tau = torch.zeros((len(ts), n_ev, 4, n_ev, 4), dtype=torch.complex128, device="cuda")
+        p = default_params(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F32, rhs_block=RHS_BLOCK)
+        st = Stats(1, 1)
+        ctx.perambulator(V, n_ev, ts, tau, mode=mode, params=p, stats=st)  # warm: graphs, workspaces
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.perambulator(V, n_ev, ts, tau, mode=mode, params=p, stats=st)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        n = 4 * n_ev * len(ts)  # each domain of a multi-site source counts as one RHS
+        res[name] = {"rhs": n, "ms": ms, "rhs_per_s": n / (ms / 1e3), "max_true_resid": st.max_true_resid}
+    print(json.dumps({"sample": "24^3x48 uneven domains 6/8/10/6/8/10, N_ev 64", "variants": tun["variant"],
+                      "results": res}), flush=True)
 
 
 def peaks():
@@ -469,6 +506,9 @@ def main():
     args = parse()
     if args.profile_dslash:
         profile_dslash(args.dslash_variant)
+        return
+    if args.uneven_sample:
+        uneven_sample()
         return
     rank, world = dist_init()
     if args.impl == "reference":
