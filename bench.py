@@ -1,26 +1,32 @@
 """Benchmark of the distillation subtraction-estimator hot path on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload scale|mixed|uneven|learned]
 
-Workload (mixed-precision configuration): 16^3 x 32 lattice, SU(3) links U = exp(i 0.5 H)
-(Philox-seeded Gaussian traceless Hermitian H), clover-Wilson kappa = 0.125, c_sw = 1.6,
-antiperiodic in time, N_ev = 32 colour vectors per timeslice (lowest eigenvectors of the
-covariant 3D Laplacian, computed on the GPU by the library's own eigensolver), eight time domains
-of extent 4, Gamma = {gamma_5, 1}.  Synthetic data; it stands in for the paper's 96 x 32^3 ensemble.
+Default workload (scale run): 48^3 x 96 lattice, SU(3) links U = exp(i 0.6 H) (Philox-seeded
+Gaussian traceless Hermitian H, seed 5001), clover-Wilson kappa = 0.126, c_sw = 1.7, antiperiodic
+in time; N_ev = 128 seeded orthonormal colour vectors (seed 5002) on the 16 source timeslices
+t = 0, 6, ..., 90; 24 time domains of extent 4 (extents 8 and 12 measured beside it);
+Gamma = {gamma_5, 1}.  Synthetic data; it stands in for the paper's 96 x 32^3 ensemble with its
+200 Laplacian eigenvectors.
 
-One step = the whole hot path for one source group, i.e. one source timeslice per domain
-(t = g, g+4, ..., g+28, g = step mod 4):
-  full-operator perambulators   8 timeslices x 32 vectors x 4 spins = 1024 right-hand sides
-  domain-operator perambulators the same 1024 (domain, RHS) pairs as 128 multi-site solves
+One step = the whole hot path for one RHS block (rhs_block right-hand sides: rhs_block / 4 source
+colour vectors x 4 spins):
+  full-operator perambulator columns of that block at one source timeslice   rhs_block RHS
+  domain-operator columns of the same block for one source group (one source timeslice per
+  domain) as one multi-site solve                        rhs_block x (domains served) RHS
   loops of both, and the full / factorised / subtracted correlators of the configuration.
-Every solve reaches FP64 true residual <= 1e-10 (FP64 defect correction around FP32 BiCGStab).
-metric value = RHS solved per second (full + domain), inputs resident in HBM.
+Consecutive steps walk the source timeslices, then the blocks.  Every solve reaches FP64 true
+residual <= 1e-10 (FP64 defect correction around FP32 BiCGStab).
+metric value = RHS solved per second (full + domain; each domain of a multi-site solve counts
+once), inputs resident in HBM.
 
-The JSON line also carries: e2e (the same step through the C ABI with host buffers: gauge
-field and colour vectors uploaded and perambulators / loops / correlators downloaded every
-step), the plain FP64 solver's RHS/s on a sample (the "vs plain" ratio), the dslash HBM
-roofline of the dominant kernel, a CPU-oracle baseline, clocks sampled during the timed region
-and the number of library kernels launched in it.
+The JSON line also carries: e2e (the same steps through the C ABI with pinned host buffers: the
+gauge field and the step's colour vectors uploaded and perambulators / loops / correlators
+downloaded every step), the plain FP64 solver and the other solvers on one sample (the
+"vs plain" ratio), the dslash roofline of the dominant kernel, domain extents 8 and 12, a CPU
+baseline of the oracle, clocks sampled during the timed region and the number of library kernels
+launched in it.
 """
 import argparse
 import json
@@ -36,110 +42,46 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DIMS = (16, 16, 16, 32)
-EPS, KAPPA, CSW = 0.5, 0.125, 1.6
-N_EV = 32
-EXTENTS = [4] * 8
+WORKLOADS = {
+    "scale": dict(
+        title="48^3x96 scale run: batched mixed-precision distillation, full + domain solves",
+        dims=(48, 48, 48, 96), eps=0.6, kappa=0.126, csw=1.7, n_ev=128, t_src=list(range(0, 96, 6)),
+        extents=[4] * 24, sweep={8: [8] * 12, 12: [12] * 8}, gauge_seed=5001, cv_seed=5002,
+        sources="seeded orthonormal colour vectors (Cholesky-QR twice)", rhs_block=16, solver_sample_rhs=4),
+    "mixed": dict(
+        title="16^3x32 mixed-precision distillation, full + domain solves",
+        dims=(16, 16, 16, 32), eps=0.5, kappa=0.125, csw=1.6, n_ev=32, t_src=list(range(32)),
+        extents=[4] * 8, sweep={}, gauge_seed=2001, cv_seed=2002,
+        sources="lowest Laplacian eigenvectors (GPU eigensolver)", rhs_block=64, solver_sample_rhs=64),
+    "uneven": dict(
+        title="24^3x48 batched uneven domains 6/8/10/6/8/10",
+        dims=(24, 24, 24, 48), eps=0.5, kappa=0.125, csw=1.6, n_ev=64, t_src=list(range(48)),
+        extents=[6, 8, 10, 6, 8, 10], sweep={}, gauge_seed=3001, cv_seed=3002,
+        sources="seeded orthonormal colour vectors (Cholesky-QR twice)", rhs_block=64, solver_sample_rhs=16),
+}
 GAMMAS = [5, 0]
-GAUGE_SEED = 1000 * 2 + 1
-RHS_BLOCK = 64
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--rhs-block", type=int, default=0, help="override the workload's RHS block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed steps and e2e (no solver comparison, sweep or roofline)")
     ap.add_argument("--profile-dslash", action="store_true",
                     help="only time the dslash kernels of the workload (small command for ncu captures)")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up the workload, run one warm step and one step inside the NVTX range "
                          "'bench_step' (for ncu --nvtx-include), print no bench line")
-    ap.add_argument("--uneven-sample", action="store_true",
-                    help="time the 24^3x48 uneven-domain configuration (domains 6/8/10/6/8/10, 64 colour "
-                         "vectors): one domain-mode perambulator call over one source per domain and one "
-                         "full-mode source timeslice; prints one JSON line")
     ap.add_argument("--dslash-variant", type=int, default=-1,
                     help="with --profile-dslash: time only this launch variant (default: all)")
+    ap.add_argument("--dslash-nrhs", type=int, default=0, help="with --profile-dslash: RHS count")
     return ap.parse_args()
-
-
-def profile_dslash(only_variant=-1):
-    """The FP32 / FP16 / FP64 even-odd hopping + inverse-clover kernels of the workload, a few
-    launches each per launch variant (0-2: direct loads, register cap 128 / 80 / 64 per thread;
-    3: links and clover staged once per site in shared memory; 4: neighbour spinors staged by
-    bulk copies; FP64: 0-2 with register caps 128 / 255 / 168),
-    L2 flushed between launches (inputs: 64-RHS FP32 batch = 400 MB > L2)."""
-    import torch
-    from lqcd_inputs import gauge_field
-    from paper_2609_37049_b300 import Context, lqcd
-    torch.cuda.set_device(0)
-    ctx = Context(DIMS)
-    ctx.gauge_upload(gauge_field(DIMS, EPS, GAUGE_SEED), KAPPA, CSW)
-    out = {}
-    for name, prec, nrhs in (("f32", lqcd.LQCD_PREC_F32, RHS_BLOCK), ("f16", lqcd.LQCD_PREC_F16, RHS_BLOCK),
-                             ("f64", lqcd.LQCD_PREC_F64, 8)):
-        for v in (range(3) if prec == lqcd.LQCD_PREC_F64 else range(5)):
-            if only_variant >= 0 and v != only_variant:
-                continue
-            ctx.set_dslash_variant(prec, nrhs, v)
-            ms, by = ctx.dslash_bench(prec, nrhs, 3, True)
-            out["%s_v%d" % (name, v)] = {"nrhs": nrhs, "ms": ms, "GBs": by / ms / 1e6, "algo_bytes": by}
-    print(json.dumps(out), flush=True)
-
-
-def captured_traffic(variant):
-    """DRAM bytes per launch of the FP32 dslash from the committed ncu summary, or None when the
-    kernel sources changed since the capture or the tuned variant is not the captured one."""
-    import hashlib
-    import re
-    h = hashlib.sha1()
-    for f in ("dslash.cu", "dslash_ops.cuh", "dslash_staged.cu", "lqcd_common.cuh"):
-        with open(os.path.join(ROOT, "paper_2609_37049_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    try:
-        with open(os.path.join(ROOT, "profiles", "dslash_f32_16x16x16x32_nrhs64.md")) as fh:
-            m = re.search(r"roofline-traffic: bytes=(\d+) variant=(\d+) sources=([0-9a-f]+)", fh.read())
-    except OSError:
-        return None
-    if not m or m.group(3) != h.hexdigest() or int(m.group(2)) != int(variant):
-        return None
-    return int(m.group(1))
-
-
-def uneven_sample():
-    """Mixed-precision perambulators at 24^3x48 with uneven domains (eps 0.5, kappa 0.125,
-    c_sw 1.6, N_ev = 64 seeded orthonormal colour vectors), autotuned launch variants."""
-    import torch
-    from lqcd_inputs import colour_vectors, gauge_field
-    from paper_2609_37049_b300 import Context, Stats, autotune, default_params, lqcd
-    dims, ext, n_ev = (24, 24, 24, 48), [6, 8, 10, 6, 8, 10], 64
-    torch.cuda.set_device(0)
-    ctx = Context(dims)
-    ctx.gauge_upload(gauge_field(dims, 0.5, 3001), KAPPA, CSW)
-    ctx.set_domains(ext)
-    tun = autotune.tune(ctx, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F64), blocks=(RHS_BLOCK,))
-    V = torch.from_numpy(colour_vectors(dims, n_ev, 3002)).cuda()
-    starts = [int(sum(ext[:d])) for d in range(len(ext))]
-    res = {}
-    for mode, name, ts in ((lqcd.LQCD_MODE_DOMAIN, "domain", starts), (lqcd.LQCD_MODE_FULL, "full", [0])):
-        tau = torch.zeros((len(ts), n_ev, 4, n_ev, 4), dtype=torch.complex128, device="cuda")
-        p = default_params(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F32, rhs_block=RHS_BLOCK)
-        st = Stats(1, 1)
-        ctx.perambulator(V, n_ev, ts, tau, mode=mode, params=p, stats=st)  # warm: graphs, workspaces
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ctx.perambulator(V, n_ev, ts, tau, mode=mode, params=p, stats=st)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        n = 4 * n_ev * len(ts)  # each domain of a multi-site source counts as one RHS
-        res[name] = {"rhs": n, "ms": ms, "rhs_per_s": n / (ms / 1e3), "max_true_resid": st.max_true_resid}
-    print(json.dumps({"sample": "24^3x48 uneven domains 6/8/10/6/8/10, N_ev 64", "variants": tun["variant"],
-                      "results": res}), flush=True)
 
 
 def peaks():
@@ -204,33 +146,49 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle baseline
-def cpu_baseline(budget_s=20.0):
-    """The oracle, as it stands, on a bounded sample of the workload (single-threaded numpy).
+def stored_cgnr_iterations(wl):
+    """The oracle's CGNR iteration count to true residual 1e-10 at the workload's couplings, as
+    measured by oracle/cgnr_iterations.py (largest lattice available with those couplings)."""
+    path = os.path.join(ROOT, "oracle", "cgnr_iterations.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except OSError:
+        return None
+    best = None
+    for e in data.values():
+        if abs(e["eps"] - wl["eps"]) < 1e-12 and abs(e["kappa"] - wl["kappa"]) < 1e-12 and \
+                abs(e["c_sw"] - wl["csw"]) < 1e-12 and e["true_resid"] <= 1e-10:
+            if best is None or np.prod(e["dims"]) > np.prod(best["dims"]):
+                best = e
+    return best
 
-    Sample: the oracle's CGNR solve of one right-hand side (t=0, j=0, beta=0 source) runs for a
-    fixed number of iterations on the full 16^3 x 32 lattice; the per-iteration time is scaled by
-    the number of iterations the oracle needs to reach FP64 true residual 1e-10 at the same
-    couplings, measured on a 4^3 x 8 field of the same recipe.  Projection and loops are timed
-    on the same solution.  Reported in RHS/s."""
-    from lqcd_inputs import gauge_field, colour_vectors
+
+def cpu_baseline(wl, budget_s=20.0, setup=None):
+    """The oracle, as it stands, on a bounded sample of the workload (numpy, one core).
+
+    Sample: the oracle's CGNR on one right-hand side (t = 0, colour vector 0, spin 0) of a
+    16^3 x 32 field with the workload's couplings, a fixed number of iterations timed; the time
+    per iteration is scaled by the volume ratio to the workload's lattice (every oracle step is a
+    site loop) and by the iteration count the oracle needs for true residual 1e-10 at these
+    couplings (measured once by oracle/cgnr_iterations.py on the largest lattice listed there).
+    The projection on the source timeslice is timed and scaled the same way.  RHS/s."""
+    from lqcd_inputs import colour_vectors, gauge_field
     from oracle.dirac import WilsonClover
+    from oracle.distill import project, sources
     from oracle.solve import cgnr
-    from oracle.distill import sources, project
 
     t0 = time.time()
-    Us = gauge_field((4, 4, 4, 8), EPS, GAUGE_SEED)
-    ops = WilsonClover(Us, KAPPA, CSW)
-    Vs = colour_vectors((4, 4, 4, 8), 1, 7, timeslices=[0])
-    bs = sources(Vs[0], 0, (4, 4, 4, 8))[:1]
-    _, info = cgnr(ops, bs, tol=1e-10)
-    n_iter = int(info["iters"][0])
-    U = gauge_field(DIMS, EPS, GAUGE_SEED)
-    op = WilsonClover(U, KAPPA, CSW)
-    V0 = colour_vectors(DIMS, 1, 7, timeslices=[0])
-    b = sources(V0[0], 0, DIMS)[:1]
-    k = 0
+    sdims = (16, 16, 16, 32)
+    if setup is None:
+        U = gauge_field(sdims, wl["eps"], wl["gauge_seed"])
+        op = WilsonClover(U, wl["kappa"], wl["csw"])
+        V0 = colour_vectors(sdims, 1, wl["cv_seed"], timeslices=[0])
+        setup = (op, V0)
+    op, V0 = setup
+    b = sources(V0[0], 0, sdims)[:1]
+    k, x = 0, None
     t1 = time.time()
-    x = None
     while True:
         x, _ = cgnr(op, b, tol=1e-30, max_iter=2, x0=x)
         k += 2
@@ -240,231 +198,399 @@ def cpu_baseline(budget_s=20.0):
     t2 = time.time()
     project(V0[0], x, 0)
     t_proj = time.time() - t2
-    per_rhs = t_iter * n_iter + t_proj
-    return {"value": 1.0 / per_rhs, "unit": "RHS/s", "cores": 1, "kind": "oracle",
-            "sample": ("oracle CGNR on one 16^3x32 RHS for %d iterations (%.2f s/iter), scaled by the "
-                       "%d iterations the oracle needs for 1e-10 at the same couplings (4^3x8 field); "
-                       "single-threaded numpy" % (k, t_iter, n_iter)),
-            "seconds": time.time() - t0}
+    ratio = float(np.prod(wl["dims"])) / float(np.prod(sdims))
+    ref = stored_cgnr_iterations(wl)
+    n_iter = ref["iters"] if ref else None
+    per_rhs = (t_iter * n_iter + t_proj) * ratio if n_iter else None
+    return {"value": (1.0 / per_rhs) if per_rhs else None, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": ("oracle CGNR on one RHS of a 16^3x32 field with the workload's couplings for %d iterations "
+                       "(%.3f s/iter), scaled by the volume ratio %.0f to %s and by the %s CGNR iterations the "
+                       "oracle needs for 1e-10 at these couplings (measured by oracle/cgnr_iterations.py on the "
+                       "%s field); single-threaded numpy (host has %d cores)"
+                       % (k, t_iter, ratio, "x".join(map(str, wl["dims"])), n_iter,
+                          "x".join(map(str, ref["dims"])) if ref else "?", os.cpu_count())),
+            "seconds": time.time() - t0}, setup
+
+
+# ----------------------------------------------------------------------------- workload set-up
+class Workload:
+    """Inputs, context, buffers and the step of one workload on this rank's GPU."""
+
+    def __init__(self, name, rhs_block=0, rank=0, world=1):
+        import torch
+        from lqcd_inputs import colour_vectors, gauge_field
+        from paper_2609_37049_b300 import Context, lqcd
+        from paper_2609_37049_b300.shard import source_groups
+
+        self.name, self.wl = name, WORKLOADS[name]
+        wl = self.wl
+        self.rank, self.world = rank, world
+        self.dims, self.T = wl["dims"], wl["dims"][3]
+        self.L3 = self.dims[0] * self.dims[1] * self.dims[2]
+        self.n_ev = wl["n_ev"]
+        self.rhs_block = rhs_block or wl["rhs_block"]
+        self.nj = self.rhs_block // 4
+        assert self.rhs_block % 4 == 0 and self.n_ev % self.nj == 0
+        self.n_blocks = self.n_ev // self.nj
+        self.t_src = list(wl["t_src"])
+        self.slot = {t: k for k, t in enumerate(self.t_src)}
+        t0 = time.time()
+        self.U = gauge_field(self.dims, wl["eps"], wl["gauge_seed"])
+        self.ctx = Context(self.dims)
+        self.ctx.gauge_upload(self.U, wl["kappa"], wl["csw"])
+        self.ctx.set_domains(wl["extents"])
+        self.t_gauge = time.time() - t0
+        t0 = time.time()
+        if wl["sources"].startswith("lowest Laplacian"):
+            Vall = torch.zeros((self.T, self.n_ev, self.L3, 3), dtype=torch.complex128, device="cuda")
+            lam = torch.zeros((self.T, self.n_ev), dtype=torch.float64, device="cuda")
+            self.ctx.laplace_eigs(self.n_ev, Vall, lam)
+            self.V = Vall[self.t_src].contiguous()
+            del Vall
+        else:
+            Vh = colour_vectors(self.dims, self.n_ev, wl["cv_seed"], timeslices=self.t_src)
+            self.V = torch.from_numpy(Vh.reshape(len(self.t_src), self.n_ev, self.L3, 3)).cuda()
+            del Vh
+        torch.cuda.synchronize()
+        self.t_vectors = time.time() - t0
+        # source groups: one source timeslice per domain, restricted to t_src
+        dom_groups = source_groups(self.T, wl["extents"])
+        tset = set(self.t_src)
+        self.groups = [g2 for g2 in ([t for t in g if t in tset] for g in dom_groups) if g2]
+        n_t = len(self.t_src)
+        c128 = dict(dtype=torch.complex128, device="cuda")
+        self.tau_f = torch.zeros((n_t, self.n_ev, 4, self.n_ev, 4), **c128)
+        # per source group: its colour vectors (a view where the slots are consecutive) and tau
+        self.Vg, self.tau_g = [], []
+        for grp in self.groups:
+            ks = [self.slot[t] for t in grp]
+            contiguous = ks == list(range(ks[0], ks[0] + len(ks)))
+            self.Vg.append(self.V[ks[0]:ks[0] + len(ks)] if contiguous else self.V[ks].contiguous())
+            self.tau_g.append(torch.zeros((len(grp), self.n_ev, 4, self.n_ev, 4), **c128))
+        self.Lb = {k: torch.zeros((len(GAMMAS), max(len(g) for g in self.groups)), **c128) for k in ("a", "b")}
+        self.loops = {k: torch.zeros((1, len(GAMMAS), self.T), **c128) for k in ("f", "ft", "d", "dt")}
+        self.corr = dict(C=torch.zeros((len(GAMMAS), self.T, self.T), **c128))
+        self.corr["Cdd"], self.corr["dC"] = torch.zeros_like(self.corr["C"]), torch.zeros_like(self.corr["C"])
+        self.corr["C_avg"] = torch.zeros((len(GAMMAS), self.T), **c128)
+        self.corr["dC_avg"] = torch.zeros_like(self.corr["C_avg"])
+        self.corr["valid"] = torch.zeros((self.T, self.T), dtype=torch.int32, device="cuda")
+        self.corr["n_valid"] = torch.zeros(self.T, dtype=torch.int32, device="cuda")
+        self.params = None
+        self.lqcd = lqcd
+        self.stats = []
+
+    def tune(self):
+        import tempfile
+        from paper_2609_37049_b300 import autotune, default_params
+        lq = self.lqcd
+        self.tuning = autotune.tune(self.ctx, cache=os.path.join(tempfile.gettempdir(), "lqcd_tuning.json"),
+                                    precisions=(lq.LQCD_PREC_F32, lq.LQCD_PREC_F64), blocks=(self.rhs_block,))
+        self.params = default_params(solver=lq.LQCD_SOLVER_MIXED, inner_prec=lq.LQCD_PREC_F32,
+                                     rhs_block=self.rhs_block)
+
+    def unit(self, step):
+        from paper_2609_37049_b300.shard import plan_unit
+        return plan_unit(step * self.world + self.rank, len(self.t_src), len(self.groups), self.n_blocks)
+
+    def rhs_of_unit(self, u):
+        k, g, b = u
+        return self.rhs_block + self.rhs_block * len(self.groups[g])
+
+    def step(self, s, host=None):
+        """One step on device buffers, or (host = dict of pinned numpy arrays) through host buffers.
+        Returns the right-hand sides solved."""
+        from paper_2609_37049_b300 import Stats
+        lq = self.lqcd
+        k, g, b = u = self.unit(s)
+        j0 = b * self.nj
+        grp = self.groups[g]
+        B = self if host is None else None
+        V = self.V if B else host["V"]
+        Vg = self.Vg[g] if B else host["Vg"][g]
+        tau_f = self.tau_f if B else host["tau_f"]
+        tau_g = self.tau_g[g] if B else host["tau_g"][g]
+        Lb, loops, corr = (self.Lb, self.loops, self.corr) if B else (host["Lb"], host["loops"], host["corr"])
+        if host is not None:
+            self.ctx.gauge_upload(host["U"], self.wl["kappa"], self.wl["csw"])
+        st = Stats(1, 1)
+        self.ctx.perambulator_cols(V[k:k + 1], self.n_ev, [self.t_src[k]], tau_f[k:k + 1], j0, self.nj,
+                                   mode=lq.LQCD_MODE_FULL, sinks=lq.LQCD_SINKS_DIAG_SRCV, params=self.params,
+                                   stats=st)
+        self.stats.append(("full", st.total_iters, st.max_true_resid, st.outer_cycles))
+        st = Stats(1, 1)
+        self.ctx.perambulator_cols(Vg, self.n_ev, grp, tau_g, j0, self.nj, mode=lq.LQCD_MODE_DOMAIN,
+                                   sinks=lq.LQCD_SINKS_DIAG_SRCV, params=self.params, stats=st)
+        self.stats.append(("dom", st.total_iters, st.max_true_resid, st.outer_cycles))
+        # loops of the timeslices this step touched, then the correlators of the configuration
+        La, Lta = Lb["a"][:, :1], Lb["b"][:, :1]
+        if B:
+            La, Lta = La.contiguous(), Lta.contiguous()
+        else:
+            La, Lta = np.ascontiguousarray(La), np.ascontiguousarray(Lta)
+        self.ctx.loops(tau_f[k:k + 1], self.n_ev, 1, GAMMAS, La, Lta)
+        loops["f"][0][:, self.t_src[k]] = La[:, 0]
+        loops["ft"][0][:, self.t_src[k]] = Lta[:, 0]
+        n = len(grp)
+        Ld, Ltd = Lb["a"][:, :n], Lb["b"][:, :n]
+        if B:
+            Ld, Ltd = Ld.contiguous(), Ltd.contiguous()
+        else:
+            Ld, Ltd = np.ascontiguousarray(Ld), np.ascontiguousarray(Ltd)
+        self.ctx.loops(tau_g, self.n_ev, n, GAMMAS, Ld, Ltd)
+        loops["d"][0][:, grp] = Ld
+        loops["dt"][0][:, grp] = Ltd
+        self.ctx.disc_correlator(loops["f"], loops["ft"], loops["d"], loops["dt"], 0, corr)
+        return self.rhs_of_unit(u)
+
+    def host_buffers(self):
+        """Pinned host copies of the step's inputs and outputs for the end-to-end measurement."""
+        import torch
+        pin = lambda t: torch.zeros(t.shape, dtype=t.dtype).pin_memory().numpy()
+        V = self.V.cpu().pin_memory().numpy()
+        Vg = []
+        for grp in self.groups:
+            ks = [self.slot[t] for t in grp]
+            contiguous = ks == list(range(ks[0], ks[0] + len(ks)))
+            Vg.append(V[ks[0]:ks[0] + len(ks)] if contiguous else
+                      torch.from_numpy(V[ks]).pin_memory().numpy())
+        h = {"U": torch.from_numpy(self.U).pin_memory().numpy(), "V": V, "Vg": Vg, "tau_f": pin(self.tau_f),
+             "tau_g": [pin(t) for t in self.tau_g], "Lb": {k: pin(v) for k, v in self.Lb.items()},
+             "loops": {k: pin(v) for k, v in self.loops.items()}, "corr": {k: pin(v) for k, v in self.corr.items()}}
+        return h
+
+    def e2e_bytes(self, s):
+        """Host<->device bytes of one end-to-end step (counted from the arrays the calls copy)."""
+        k, g, b = self.unit(s)
+        vslice = self.n_ev * self.L3 * 3 * 16
+        tau1 = self.n_ev * 4 * self.n_ev * 4 * 16
+        grp = len(self.groups[g])
+        ng = len(GAMMAS)
+        # gauge field; colour vectors; tau read back first (untouched columns) and written out;
+        # loops (tau in, loops out); correlator inputs (four loop arrays) and outputs
+        h2d = self.U.nbytes + vslice * (1 + grp) + tau1 * (1 + grp) + tau1 * (1 + grp) + 4 * ng * self.T * 16
+        d2h = tau1 * (1 + grp) + 2 * ng * (1 + grp) * 16
+        d2h += sum(v.numel() * v.element_size() for v in self.corr.values())
+        return int(h2d), int(d2h)
 
 
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args, rank, world):
     import torch
-    from lqcd_inputs import gauge_field
-    from paper_2609_37049_b300 import Context, Stats, default_params, lqcd
+    from paper_2609_37049_b300 import Stats, default_params, lqcd
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     peak, peak_kind = peaks()
-    U = gauge_field(DIMS, EPS, GAUGE_SEED)
-    ctx = Context(DIMS)
-    ctx.gauge_upload(U, KAPPA, CSW)
-    ctx.set_domains(EXTENTS)
-    T = DIMS[3]
-    L3 = DIMS[0] * DIMS[1] * DIMS[2]
-    # colour vectors: lowest Laplacian eigenvectors on the GPU (input preparation, untimed)
-    Vd = torch.zeros((T, N_EV, L3, 3), dtype=torch.complex128, device="cuda")
-    lam = torch.zeros((T, N_EV), dtype=torch.float64, device="cuda")
-    t0 = time.time()
-    ctx.laplace_eigs(N_EV, Vd, lam)
-    torch.cuda.synchronize()
-    t_eig = time.time() - t0
-    import tempfile
-    from paper_2609_37049_b300 import autotune
-    tuning = autotune.tune(ctx, cache=os.path.join(tempfile.gettempdir(), "lqcd_tuning.json"),
-                           precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F64), blocks=(RHS_BLOCK,))
-    params = default_params(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F32, rhs_block=RHS_BLOCK)
-    n_grp = len(EXTENTS)
-    tau_f = torch.zeros((n_grp, N_EV, 4, N_EV, 4), dtype=torch.complex128, device="cuda")
-    tau_d = torch.zeros_like(tau_f)
-    loopsF = torch.zeros((1, len(GAMMAS), T), dtype=torch.complex128, device="cuda")
-    loopsFt, loopsD, loopsDt = torch.zeros_like(loopsF), torch.zeros_like(loopsF), torch.zeros_like(loopsF)
-    Lb = torch.zeros((len(GAMMAS), n_grp), dtype=torch.complex128, device="cuda")
-    Ltb = torch.zeros_like(Lb)
-    corr = dict(C=torch.zeros((len(GAMMAS), T, T), dtype=torch.complex128, device="cuda"))
-    corr["Cdd"], corr["dC"] = torch.zeros_like(corr["C"]), torch.zeros_like(corr["C"])
-    corr["C_avg"] = torch.zeros((len(GAMMAS), T), dtype=torch.complex128, device="cuda")
-    corr["dC_avg"] = torch.zeros_like(corr["C_avg"])
-    corr["valid"] = torch.zeros((T, T), dtype=torch.int32, device="cuda")
-    corr["n_valid"] = torch.zeros(T, dtype=torch.int32, device="cuda")
-    stats = {"full": [], "dom": []}
-
-    from paper_2609_37049_b300.shard import source_groups, units_for_step
-    groups = source_groups(T, EXTENTS)
-
-    def step(s):
-        t_src = units_for_step(groups, s, rank, world)
-        for mode, tau, L, Lt, key in ((lqcd.LQCD_MODE_FULL, tau_f, loopsF, loopsFt, "full"),
-                                      (lqcd.LQCD_MODE_DOMAIN, tau_d, loopsD, loopsDt, "dom")):
-            st = Stats(1, 1)
-            ctx.perambulator(Vd, N_EV, t_src, tau, mode=mode, params=params, stats=st)
-            stats[key].append((st.total_iters, st.max_true_resid, st.outer_cycles))
-            ctx.loops(tau, N_EV, n_grp, GAMMAS, Lb, Ltb)
-            L[0][:, t_src] = Lb
-            Lt[0][:, t_src] = Ltb
-        ctx.disc_correlator(loopsF, loopsFt, loopsD, loopsDt, 0, corr)
-
-    rhs_per_step = 2 * n_grp * N_EV * 4
+    W = Workload(args.workload, args.rhs_block, rank, world)
+    W.tune()
     if args.profile_step:  # one warm step, then one step inside an NVTX range for an ncu launch list
-        step(0)
+        W.step(0)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("bench_step")
-        step(1)
+        W.step(1)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        print(json.dumps({"profile_step": "done", "rhs": rhs_per_step}), flush=True)
-        return
+        print(json.dumps({"profile_step": "done", "rhs": W.rhs_of_unit(W.unit(1))}), flush=True)
+        return None
     for s in range(args.warmup):
-        step(s)
+        W.step(s)
     torch.cuda.synchronize()
     dist_barrier(world)
+    W.stats.clear()
     l0 = lqcd.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rhs = 0
     with ClockSampler(dev) as clk:
         torch.cuda.synchronize()
         e0.record()
         for s in range(args.steps):
-            step(args.warmup + s)
+            rhs += W.step(args.warmup + s)
         e1.record()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     launches = lqcd.kernel_launches() - l0
     ms_max = dist_max(ms, world)
+    rhs_all = dist_sum(rhs, world)
     dist_barrier(world)
-    value = rhs_per_step * args.steps * world / (ms_max / 1e3)
-
-    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    U_h = torch.from_numpy(U).pin_memory()
-    V_h = Vd.cpu().pin_memory()
-    tau_h = torch.zeros(tau_f.shape, dtype=torch.complex128).pin_memory()
-    Lb_h = torch.zeros(Lb.shape, dtype=torch.complex128).pin_memory()
-    Ltb_h = torch.zeros_like(Lb_h).pin_memory()
-    lF_h = [torch.zeros(loopsF.shape, dtype=torch.complex128).pin_memory() for _ in range(4)]
-    corr_h = {k: torch.zeros(v.shape, dtype=v.dtype).pin_memory() for k, v in corr.items()}
-    npy = lambda t: t.numpy()
-
-    def step_e2e(s):
-        t_src = units_for_step(groups, s, rank, world)
-        ctx.gauge_upload(npy(U_h), KAPPA, CSW)
-        for mode, (L, Lt) in ((lqcd.LQCD_MODE_FULL, lF_h[:2]), (lqcd.LQCD_MODE_DOMAIN, lF_h[2:])):
-            ctx.perambulator(npy(V_h), N_EV, t_src, npy(tau_h), mode=mode, params=params)
-            ctx.loops(npy(tau_h), N_EV, n_grp, GAMMAS, npy(Lb_h), npy(Ltb_h))
-            npy(L)[0][:, t_src] = npy(Lb_h)
-            npy(Lt)[0][:, t_src] = npy(Ltb_h)
-        ctx.disc_correlator(npy(lF_h[0]), npy(lF_h[1]), npy(lF_h[2]), npy(lF_h[3]), 0,
-                            {k: npy(v) for k, v in corr_h.items()})
-
-    step_e2e(0)
-    torch.cuda.synchronize()
-    dist_barrier(world)
-    t0 = time.time()
-    e_steps = max(1, min(args.steps, 2))
-    for s in range(e_steps):
-        step_e2e(s + 1)
-    torch.cuda.synchronize()
-    e2e_s = dist_max(time.time() - t0, world)
-    h2d = U_h.numel() * 16 + 2 * V_h.numel() * 16 + 4 * loopsF.numel() * 16
-    d2h = 2 * (tau_h.numel() * 16 + 2 * Lb_h.numel() * 16) + sum(v.numel() * v.element_size()
-                                                                   for v in corr_h.values())
-    e2e = {"value": rhs_per_step * e_steps * world / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "steps": e_steps}
-
-    # ---- solvers compared on one sample: full-operator perambulator of one source timeslice
-    # (128 RHS); every one reaches FP64 true residual 1e-10
-    tau1 = torch.zeros((1, N_EV, 4, N_EV, 4), dtype=torch.complex128, device="cuda")
-
-    def sample(p):
-        ctx.perambulator(Vd, N_EV, [0], tau1, mode=lqcd.LQCD_MODE_FULL, params=p)  # graphs, buffers
-        torch.cuda.synchronize()
-        t0 = time.time()
-        st = Stats(1, 1)
-        ctx.perambulator(Vd, N_EV, [0], tau1, mode=lqcd.LQCD_MODE_FULL, params=p, stats=st)
-        torch.cuda.synchronize()
-        return {"rhs_per_s": 4 * N_EV / (time.time() - t0), "iters_per_rhs": st.total_iters / (4 * N_EV),
-                "max_true_resid": st.max_true_resid, "fallback": st.fallback}
-
-    solvers = {}
-    solvers["plain_fp64_bicgstab"] = sample(default_params(solver=lqcd.LQCD_SOLVER_BICGSTAB64, rhs_block=RHS_BLOCK))
-    solvers["mixed_fp32_bicgstab"] = sample(params)
-    solvers["mixed_fgcr_fp16_mr4"] = sample(default_params(solver=lqcd.LQCD_SOLVER_MIXED,
-                                                           inner_prec=lqcd.LQCD_PREC_F16, precond_iters=4,
-                                                           rhs_block=RHS_BLOCK))
-    solvers["mixed_fgcr_none"] = sample(default_params(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F16,
-                                                       precond_iters=-1, rhs_block=RHS_BLOCK))
-    ctx.nn_set_weights(lqcd.nn_initial_weights(5, 0.05))
-    t0 = time.time()
-    hist = ctx.nn_train(n_pairs=64, epochs=12, batch=8, lr=3e-3, seed=11)
-    torch.cuda.synchronize()
-    train_s = time.time() - t0
-    solvers["mixed_fgcr_learned"] = sample(default_params(solver=lqcd.LQCD_SOLVER_FGCR_NN, rhs_block=RHS_BLOCK))
-    solvers["mixed_fgcr_learned"].update({"train_seconds": train_s, "train_pairs": 64, "epochs": 12,
-                                          "loss_first": float(hist[0]), "loss_last": float(hist[-1])})
-    plain = dict(solvers["plain_fp64_bicgstab"], value=solvers["plain_fp64_bicgstab"]["rhs_per_s"], unit="RHS/s",
-                 sample="full-operator perambulator of one source timeslice (128 RHS), BiCGStab entirely in FP64")
-    mixed_same = solvers["mixed_fp32_bicgstab"]["rhs_per_s"]
-
-    # ---- dslash roofline of the dominant kernel (FP32 hopping + inverse clover, RHS block)
-    dsl = {}
-    for name, prec in (("f32", lqcd.LQCD_PREC_F32), ("f16", lqcd.LQCD_PREC_F16), ("f64", lqcd.LQCD_PREC_F64)):
-        ms_l, by = ctx.dslash_bench(prec, RHS_BLOCK if prec != lqcd.LQCD_PREC_F64 else 8, 20, True)
-        dsl[name] = {"ms": ms_l, "GBs": by / ms_l / 1e6, "bytes": by}
-    achieved = dsl["f32"]["GBs"]
-    v32 = int(tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(RHS_BLOCK), 0))
-    kname = {3: "dslash_sl_kernel", 4: "dslash_pipe_kernel"}.get(v32, "dslash_kernel")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": captured_traffic(v32), "peak_kind": peak_kind,
-                "kernel": "%s<P32,EPI_CH> (launch variant %d: eo hopping + A^-1, %d RHS)" % (kname, v32, RHS_BLOCK),
-                "algo_bytes_per_launch": dsl["f32"]["bytes"]}
-    # the FP64 hopping kernel of every true residual is bound by the FP64 pipe: 2 FP64 FMA per SM
-    # per clock; algorithmic flops 1320 (hopping) + 504 (clover) per output site and RHS
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    f64_flops = 1824.0 * (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2) * 8
-    f64_peak = n_sm * 2 * 2 * 2.032e9 / 1e12
-    roofline_fp64 = {"bound": "alu", "kernel": "dslash_kernel<P64,EPI_CH> (8 RHS)", "unit": "TFLOP/s",
-                     "achieved": f64_flops / (dsl["f64"]["ms"] * 1e-3) / 1e12, "peak": f64_peak,
-                     "peak_kind": "derived: SMs x 2 FP64 FMA/clk x 2 flops x 2.032 GHz",
-                     "algo_flops_per_launch": f64_flops}
-    roofline_fp64["frac"] = roofline_fp64["achieved"] / f64_peak
+    value = rhs_all / (ms_max / 1e3)
+    full_rhs = args.steps * W.rhs_block * world
+    step_stats = list(W.stats)
 
     res = {"metric": "distillation RHS/s at FP64 resid 1e-10 (mixed FP64/FP32 solver)", "value": value,
            "unit": "RHS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
-           "config": {"workload": "16^3x32 mixed-precision distillation, full + domain solves",
-                      "lattice": "16^3x32", "eps": EPS, "kappa": KAPPA, "c_sw": CSW, "n_ev": N_EV,
-                      "domains": "8 x 4", "rhs_per_step": rhs_per_step, "rhs_block": RHS_BLOCK,
-                      "sources": "lowest Laplacian eigenvectors (GPU eigensolver)",
-                      "l2": "inputs larger than L2 (126 MB): each 64-RHS FP32 half-lattice batch vector is "
-                            "403 MB and each FP64 full-lattice one 1.6 GB", "parallelism": "rhs-sharded x%d" % world},
-           "e2e": e2e, "plain_fp64": plain, "mixed_same_sample_rhs_per_s": mixed_same,
-           "speedup_vs_plain": mixed_same / plain["value"], "solvers": solvers, "tuning": tuning,
-           "dslash": dsl, "roofline": roofline, "roofline_fp64": roofline_fp64,
-           "clocks": clk.summary(), "gpu_launches": launches, "eigensolve_s": t_eig,
-           "solver_stats": {"full_iters_per_step": stats["full"][-1][0], "dom_iters_per_step": stats["dom"][-1][0],
-                            "max_true_resid": max(x[1] for x in stats["full"] + stats["dom"]),
-                            "outer_cycles": max(x[2] for x in stats["full"] + stats["dom"])}}
+           "config": {"workload": W.wl["title"], "lattice": "x".join(map(str, W.dims)), "eps": W.wl["eps"],
+                      "kappa": W.wl["kappa"], "c_sw": W.wl["csw"], "n_ev": W.n_ev, "t_src": W.t_src,
+                      "domains": "%d x %s" % (len(W.wl["extents"]), sorted(set(W.wl["extents"]))),
+                      "rhs_block": W.rhs_block, "sources": W.wl["sources"],
+                      "step": "one RHS block: full-operator columns at one source timeslice + domain-operator "
+                              "columns of one source group (multi-site solve)",
+                      "l2": "inputs larger than L2 (126 MB): each FP64 full-lattice batch vector is %.1f GB"
+                            % (W.rhs_block * np.prod(W.dims) * 192 / 1e9),
+                      "parallelism": "rhs-sharded x%d" % world},
+           "gpu_launches": launches, "clocks": clk.summary(),
+           "rates": {"full_rhs_per_s": full_rhs / (ms_max / 1e3),
+                     "domain_rhs_per_s": (rhs_all - full_rhs) / (ms_max / 1e3)},
+           "solver_stats": {"full_iters_per_rhs": statistics.mean(x[1] for x in step_stats if x[0] == "full") / W.rhs_block,
+                            "dom_iters_per_rhs": statistics.mean(x[1] for x in step_stats if x[0] == "dom") / W.rhs_block,
+                            "max_true_resid": max(x[2] for x in step_stats),
+                            "outer_cycles": max(x[3] for x in step_stats)},
+           "setup_s": {"gauge": W.t_gauge, "vectors": W.t_vectors}, "tuning": W.tuning}
+    if not args.no_extras:  # before the end-to-end run, whose host staging buffers stay allocated
+        res.update(extras(W, peak, peak_kind, dev))
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    H = W.host_buffers()
+    W.step(args.warmup, host=H)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    t0 = time.time()
+    rhs_e, h2d, d2h = 0, 0, 0
+    for s in range(args.steps):
+        rhs_e += W.step(args.warmup + s, host=H)
+        bi, bo = W.e2e_bytes(args.warmup + s)
+        h2d, d2h = h2d + bi, d2h + bo
+    torch.cuda.synchronize()
+    e2e_s = dist_max(time.time() - t0, world)
+    e2e = {"value": dist_sum(rhs_e, world) / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": h2d // args.steps,
+           "d2h_bytes_per_step": d2h // args.steps, "steps": args.steps}
+    del H
+
+    res["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline()
+        res["cpu_baseline"], _ = cpu_baseline(W.wl)
     return res
+
+
+def extras(W, peak, peak_kind, dev):
+    """Solvers on one sample, domain extents 8 and 12, and the dslash rooflines (outside the timed
+    region)."""
+    import torch
+    from paper_2609_37049_b300 import Stats, default_params, lqcd
+    out = {}
+    ctx = W.ctx
+    n = W.wl["solver_sample_rhs"]
+    nj = max(1, n // 4)
+    tau1 = torch.zeros((1, W.n_ev, 4, W.n_ev, 4), dtype=torch.complex128, device="cuda")
+
+    def sample(p):
+        ctx.perambulator_cols(W.V[0:1], W.n_ev, [W.t_src[0]], tau1, 0, nj, mode=lqcd.LQCD_MODE_FULL,
+                              sinks=lqcd.LQCD_SINKS_DIAG_SRCV, params=p)  # graphs, buffers
+        torch.cuda.synchronize()
+        t0 = time.time()
+        st = Stats(1, 1)
+        ctx.perambulator_cols(W.V[0:1], W.n_ev, [W.t_src[0]], tau1, 0, nj, mode=lqcd.LQCD_MODE_FULL,
+                              sinks=lqcd.LQCD_SINKS_DIAG_SRCV, params=p, stats=st)
+        torch.cuda.synchronize()
+        return {"rhs_per_s": 4 * nj / (time.time() - t0), "iters_per_rhs": st.total_iters / (4 * nj),
+                "max_true_resid": st.max_true_resid, "fallback": st.fallback, "outer_cycles": st.outer_cycles}
+
+    solvers = {}
+    blk = 4 * nj
+    solvers["plain_fp64_bicgstab"] = sample(default_params(solver=lqcd.LQCD_SOLVER_BICGSTAB64, rhs_block=blk))
+    solvers["mixed_fp32_bicgstab"] = sample(default_params(solver=lqcd.LQCD_SOLVER_MIXED,
+                                                           inner_prec=lqcd.LQCD_PREC_F32, rhs_block=blk))
+    if np.prod(W.dims) <= 24 ** 3 * 48:  # its 16 extra Krylov vectors do not fit beside the 48^3x96 batch
+        solvers["mixed_fgcr_fp16_mr4"] = sample(default_params(solver=lqcd.LQCD_SOLVER_MIXED,
+                                                               inner_prec=lqcd.LQCD_PREC_F16, precond_iters=4,
+                                                               rhs_block=blk))
+    plain = solvers["plain_fp64_bicgstab"]["rhs_per_s"]
+    out["solvers"] = solvers
+    out["solver_sample"] = "full-operator perambulator columns of %d RHS (t=%d, colour vectors 0..%d, 4 spins)" % (
+        4 * nj, W.t_src[0], nj - 1)
+    out["speedup_vs_plain"] = {k: v["rhs_per_s"] / plain for k, v in solvers.items()}
+    # domain extents swept beside the timed tiling: one source group, the first block
+    sweep = {}
+    for ext, tiling in W.wl["sweep"].items():
+        ctx.set_domains(tiling)
+        from paper_2609_37049_b300.shard import source_groups
+        grp = [t for t in source_groups(W.T, tiling)[0] if t in W.slot] or [W.t_src[0]]
+        ks = [W.slot[t] for t in grp]
+        Vg = W.V[ks].contiguous()
+        tg = torch.zeros((len(grp), W.n_ev, 4, W.n_ev, 4), dtype=torch.complex128, device="cuda")
+        ctx.perambulator_cols(Vg, W.n_ev, grp, tg, 0, W.nj, mode=lqcd.LQCD_MODE_DOMAIN,
+                              sinks=lqcd.LQCD_SINKS_DIAG_SRCV, params=W.params)
+        torch.cuda.synchronize()
+        st = Stats(1, 1)
+        t0 = time.time()
+        ctx.perambulator_cols(Vg, W.n_ev, grp, tg, 0, W.nj, mode=lqcd.LQCD_MODE_DOMAIN,
+                              sinks=lqcd.LQCD_SINKS_DIAG_SRCV, params=W.params, stats=st)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        sweep[str(ext)] = {"domains": len(tiling), "sources_in_group": len(grp),
+                           "domain_rhs_per_s": W.rhs_block * len(grp) / dt, "iters_per_rhs": st.total_iters / W.rhs_block,
+                           "max_true_resid": st.max_true_resid}
+        del Vg, tg
+    ctx.set_domains(W.wl["extents"])
+    if sweep:
+        out["domain_sweep"] = sweep
+    # dslash rooflines of the dominant kernel (FP32 hopping + inverse clover at the RHS block)
+    dsl = {}
+    n64 = min(W.rhs_block, 4 if np.prod(W.dims) > 24 ** 3 * 48 else W.rhs_block)
+    for name, prec, nr in (("f32", lqcd.LQCD_PREC_F32, W.rhs_block), ("f64", lqcd.LQCD_PREC_F64, n64)):
+        ms_l, by = ctx.dslash_bench(prec, nr, 10, True)
+        dsl[name] = {"ms": ms_l, "GBs": by / ms_l / 1e6, "bytes": by, "nrhs": nr}
+    achieved = dsl["f32"]["GBs"]
+    v32 = int(W.tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(W.rhs_block), 0))
+    kname = {3: "dslash_sl_kernel", 4: "dslash_pipe_kernel"}.get(v32, "dslash_kernel")
+    out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "traffic": None, "peak_kind": peak_kind,
+                       "kernel": "%s<P32,EPI_CH> (launch variant %d: eo hopping + A^-1, %d RHS)" % (kname, v32,
+                                                                                                  W.rhs_block),
+                       "algo_bytes_per_launch": dsl["f32"]["bytes"]}
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f64_flops = 1824.0 * (np.prod(W.dims) // 2) * n64
+    f64_peak = n_sm * 2 * 2 * 2.032e9 / 1e12
+    out["roofline_fp64"] = {"bound": "alu", "kernel": "dslash_kernel<P64,EPI_CH> (%d RHS)" % n64,
+                            "unit": "TFLOP/s", "achieved": f64_flops / (dsl["f64"]["ms"] * 1e-3) / 1e12,
+                            "peak": f64_peak, "peak_kind": "derived: SMs x 2 FP64 FMA/clk x 2 flops x 2.032 GHz",
+                            "algo_flops_per_launch": f64_flops}
+    out["roofline_fp64"]["frac"] = out["roofline_fp64"]["achieved"] / f64_peak
+    out["dslash"] = dsl
+    return out
+
+
+def profile_dslash(args):
+    """The FP32 / FP16 / FP64 even-odd hopping + inverse-clover kernels of the workload's lattice,
+    a few launches each per launch variant, L2 flushed between launches (small command for ncu)."""
+    import torch
+    from lqcd_inputs import gauge_field
+    from paper_2609_37049_b300 import Context, lqcd
+    wl = WORKLOADS[args.workload]
+    torch.cuda.set_device(0)
+    ctx = Context(wl["dims"])
+    ctx.gauge_upload(gauge_field(wl["dims"], wl["eps"], wl["gauge_seed"]), wl["kappa"], wl["csw"])
+    nr = args.dslash_nrhs or (args.rhs_block or wl["rhs_block"])
+    out = {}
+    for name, prec in (("f32", lqcd.LQCD_PREC_F32), ("f16", lqcd.LQCD_PREC_F16), ("f64", lqcd.LQCD_PREC_F64)):
+        for v in (range(3) if prec == lqcd.LQCD_PREC_F64 else range(5)):
+            if args.dslash_variant >= 0 and v != args.dslash_variant:
+                continue
+            ctx.set_dslash_variant(prec, nr, v)
+            ms, by = ctx.dslash_bench(prec, nr, 3, True)
+            out["%s_v%d" % (name, v)] = {"nrhs": nr, "ms": ms, "GBs": by / ms / 1e6, "algo_bytes": by}
+    print(json.dumps(out), flush=True)
 
 
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     """The oracle as it stands, timed per step on a bounded sample (see cpu_baseline)."""
-    vals = []
+    wl = WORKLOADS[args.workload]
+    vals, setup = [], None
     for _ in range(args.warmup):
-        cpu_baseline(budget_s=5.0)
+        _, setup = cpu_baseline(wl, budget_s=2.0, setup=setup)
     t0 = time.time()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(budget_s=10.0))
+        r, setup = cpu_baseline(wl, budget_s=4.0, setup=setup)
+        vals.append(r)
     total = time.time() - t0
-    v = statistics.median(x["value"] for x in vals)
+    v = statistics.median(x["value"] for x in vals) if vals[0]["value"] else None
     return {"impl": "reference", "metric": "distillation RHS/s at FP64 resid 1e-10 (mixed FP64/FP32 solver)",
             "value": v, "unit": "RHS/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "16^3x32 mixed-precision distillation, full + domain solves"},
+            "config": {"workload": wl["title"]},
             "cpu_baseline": {"value": v, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -493,22 +619,27 @@ def dist_barrier(world):
         _PG.barrier()
 
 
-def dist_max(x, world):
+def _reduce(x, world, op):
     if world > 1 and _PG is not None:
         import torch
         t = torch.tensor([float(x)], device="cuda" if torch.cuda.is_available() else "cpu")
-        _PG.all_reduce(t, op=_PG.ReduceOp.MAX)
+        _PG.all_reduce(t, op=op)
         return float(t.item())
     return x
+
+
+def dist_max(x, world):
+    return _reduce(x, world, _PG.ReduceOp.MAX if _PG is not None else None)
+
+
+def dist_sum(x, world):
+    return _reduce(x, world, _PG.ReduceOp.SUM if _PG is not None else None)
 
 
 def main():
     args = parse()
     if args.profile_dslash:
-        profile_dslash(args.dslash_variant)
-        return
-    if args.uneven_sample:
-        uneven_sample()
+        profile_dslash(args)
         return
     rank, world = dist_init()
     if args.impl == "reference":

@@ -56,7 +56,7 @@ enum {
 enum { LQCD_BC_PERIODIC = 0, LQCD_BC_ANTIPERIODIC = 1, LQCD_BC_OPEN = 2 };
 enum { LQCD_HOST = 0, LQCD_DEVICE = 1 };
 enum { LQCD_MODE_FULL = 0, LQCD_MODE_DOMAIN = 1 };
-enum { LQCD_SINKS_DIAG = 0, LQCD_SINKS_ALL = 1 };
+enum { LQCD_SINKS_DIAG = 0, LQCD_SINKS_ALL = 1, LQCD_SINKS_DIAG_SRCV = 2 };
 
 /* Krylov solvers.  All are judged by the FP64 true residual ||b - D x|| / ||b|| of the
  * unpreconditioned operator (per right-hand side, and per domain for domain solves):
@@ -118,7 +118,10 @@ const char* lqcd_last_error(const lqcd_ctx* ctx);
 
 /* Upload gauge links and set kappa, c_sw (Sec. 3: Wilson-clover).  Builds the clover term A and
  * A^{-1} in FP64 on the GPU and the FP32 / FP16 link and clover copies used by the mixed solvers.
- * links: [V][4][3][3] complex, host or device per `where`.  Errors: INVALID_ARG (NULL). */
+ * links: [V][4][3][3] complex, host or device per `where`.  A new kappa drops the context's
+ * captured solver graphs (they hold kappa by value).  Errors: INVALID_ARG (NULL, non-finite
+ * kappa or c_sw), NAN (a clover block with no inverse, e.g. a NaN or Inf link; the context then
+ * holds no usable gauge field). */
 int lqcd_gauge_upload(lqcd_ctx* ctx, const double* links, int where, double kappa, double c_sw);
 
 /* Tile the time axis by n_dom domains of the given extents, starting at t = 0 (Sec. 2.1; the
@@ -154,7 +157,10 @@ int lqcd_schur_apply(lqcd_ctx* ctx, int prec, const double* in, double* out, int
 
 /* Solve D x = b (full) or D_Lambda x = b (domain; every domain of every RHS converged to tol
  * relative to its own source norm) for nrhs right-hand sides; x is overwritten.  Returns
- * NOT_CONVERGED (x holds the last iterate, stats filled) if tol is not reached. */
+ * NOT_CONVERGED (x holds the last iterate, stats filled) if tol is not reached, and NAN if a
+ * right-hand side (or one domain of it) has a non-finite residual, e.g. a NaN or Inf in its
+ * source: its true_resid entry is NaN, and every other right-hand side is still solved to tol
+ * and written to x (the systems are independent).  NAN outranks NOT_CONVERGED. */
 int lqcd_solve_full(lqcd_ctx* ctx, const double* b, double* x, int nrhs, int where,
                     const lqcd_solve_params* p, lqcd_solve_stats* st);
 int lqcd_solve_domain(lqcd_ctx* ctx, const double* b, double* x, int nrhs, int where,
@@ -168,12 +174,27 @@ int lqcd_solve_domain(lqcd_ctx* ctx, const double* b, double* x, int nrhs, int w
  *   Vt:  [Lt][n_ev][Lx Ly Lz][3] complex colour vectors of every timeslice;
  *   tau: DIAG -> [n_tsrc][n_ev][4][n_ev][4]; ALL -> [n_tsrc][Lt][n_ev][4][n_ev][4] complex,
  *        index order (sink vector i, sink spin alpha, source vector j, source spin beta).
+ *   sinks DIAG_SRCV: as DIAG, but Vt holds only the colour vectors of the source timeslices,
+ *        [n_tsrc][n_ev][Lx Ly Lz][3] in t_src order (no timeslice may repeat); the diagonal
+ *        perambulators need no other timeslice, and at large Lt the full array would not fit.
  * st (may be NULL): only the aggregate fields are filled; st->iters and st->true_resid are
  * not written.
- * Errors: INVALID_ARG (n_ev < 1 or > 3 Lx Ly Lz, t out of range, ALL with DOMAIN). */
+ * Errors: INVALID_ARG (n_ev < 1 or > 3 Lx Ly Lz, t out of range, ALL with DOMAIN, a repeated
+ * timeslice with DIAG_SRCV).  NAN: a non-finite residual (NaN or Inf in the inputs); every
+ * other right-hand side is still solved and written. */
 int lqcd_perambulator(lqcd_ctx* ctx, const double* Vt, int n_ev, const int* t_src, int n_tsrc,
                       int mode, int sinks, int where, double* tau, const lqcd_solve_params* p,
                       lqcd_solve_stats* st);
+
+/* lqcd_perambulator restricted to the source vectors j in [j0, j0 + nj), all four source spins
+ * each (4 nj right-hand sides per source group): the columns (j, beta) of tau with j in that range
+ * are written and every other entry of tau is left as it was (host tau is read back first).
+ * Serves callers that spread the N_ev x 4 right-hand sides of a timeslice over several calls
+ * (checkpointing, sharding, bounded work per call).  Same layouts and errors as
+ * lqcd_perambulator, plus INVALID_ARG when j0 < 0, nj < 1 or j0 + nj > n_ev. */
+int lqcd_perambulator_cols(lqcd_ctx* ctx, const double* Vt, int n_ev, const int* t_src, int n_tsrc,
+                           int mode, int sinks, int j0, int nj, int where, double* tau,
+                           const lqcd_solve_params* p, lqcd_solve_stats* st);
 
 /* Quark loops from diagonal perambulators (Sec. 2 loop definition with the elementals of
  * Sec. 3.2): L_G(t) = sum_i w_i sum_{alpha beta} G_{alpha beta} tau^{ii}_{beta alpha}(t,t) and the

@@ -12,9 +12,24 @@ Recipes (index arithmetic fixed here so both sides draw identical numbers):
   Cholesky-QR applied twice (a Gram-Schmidt-equivalent, deterministic orthonormalisation).
 * spinors: element ``(r, s, spin, colour)`` uses index ``((r*V + s)*4 + spin)*3 + colour``.
 """
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 from .philox import gaussians
+
+
+def _per_timeslice(fn, items):
+    """fn(k, t) for every (k, t) of items, on a thread pool for large fields (numpy releases the
+    interpreter lock in its array kernels); the results do not depend on the scheduling."""
+    items = list(items)
+    if len(items) <= 2:
+        for k, t in items:
+            fn(k, t)
+        return
+    with ThreadPoolExecutor(max_workers=min(len(items), os.cpu_count() or 1)) as ex:
+        list(ex.map(lambda kt: fn(*kt), items))
 
 PURPOSE_GAUGE = 1
 PURPOSE_COLOUR = 2
@@ -54,9 +69,12 @@ def gauge_field(dims, eps, seed):
     Lx, Ly, Lz, Lt = dims
     vol3 = Lx * Ly * Lz
     U = np.empty((Lt, Lz, Ly, Lx, 4, 3, 3), dtype=np.complex128)
-    for t in range(Lt):  # one timeslice at a time bounds the temporary memory
+
+    def one(k, t):  # one timeslice at a time bounds the temporary memory
         ids = (np.uint64(t * vol3 * 4) + np.arange(vol3 * 4, dtype=np.uint64))
         U[t] = _su3_from_ids(seed, PURPOSE_GAUGE, ids, eps).reshape(Lz, Ly, Lx, 4, 3, 3)
+
+    _per_timeslice(one, enumerate(range(Lt)))
     return U
 
 
@@ -94,12 +112,15 @@ def colour_vectors(dims, n_ev, seed, timeslices=None):
     ts = list(range(Lt)) if timeslices is None else list(timeslices)
     out = np.empty((len(ts), n_ev, Lz, Ly, Lx, 3), dtype=np.complex128)
     n = vol3 * 3
-    for k, t in enumerate(ts):
+
+    def one(k, t):
         ids = np.uint64(t * n_ev * n) + np.arange(n_ev * n, dtype=np.uint64)
         g = gaussians(seed, PURPOSE_COLOUR, ids)
         X = ((g[..., 0] + 1j * g[..., 1]) / np.sqrt(2.0)).reshape(n_ev, n)
         X = _cholqr_rows(_cholqr_rows(X))
         out[k] = X.reshape(n_ev, Lz, Ly, Lx, 3)
+
+    _per_timeslice(one, enumerate(ts))
     return out
 
 

@@ -5,6 +5,9 @@ round multiplies counter words 0 and 2 by the published multipliers, mixes the h
 words 1 and 3 and the key, and the key is advanced by the published Weyl increments between
 rounds.  Implemented with numpy uint64 arithmetic on whole index arrays.
 """
+import ctypes
+import os
+
 import numpy as np
 
 _MASK = np.uint64(0xFFFFFFFF)
@@ -37,16 +40,46 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
     return tuple(c.astype(np.uint32) for c in (c0, c1, c2, c3))
 
 
+_LIB = None
+
+
+def _compiled():
+    """The compiled word generator of philox.c (built by lqcd_inputs/build.py), or None."""
+    global _LIB
+    if _LIB is None:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libphilox.so")
+        _LIB = False
+        if os.path.exists(path):
+            lib = ctypes.CDLL(path)
+            lib.philox_words.restype = None
+            lib.philox_words.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_uint32, ctypes.c_uint64,
+                                         ctypes.c_void_p]
+            _LIB = lib
+    return _LIB or None
+
+
+def philox_words(seed, purpose, index):
+    """The four Philox words (uint32 arrays) of counter (index lo, index hi, purpose, 0) and key
+    (seed lo, seed hi): the compiled generator when built, else the numpy rounds above."""
+    index = np.asarray(index, dtype=np.uint64)
+    lib = _compiled()
+    if lib is None or index.size < 4096:
+        seed = int(seed)
+        return philox4x32_10(index & _MASK, index >> np.uint64(32), np.uint64(purpose), 0,
+                             seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    flat = np.ascontiguousarray(index.ravel())
+    out = np.empty((flat.size, 4), dtype=np.uint32)
+    lib.philox_words(flat.ctypes.data, flat.size, int(purpose) & 0xFFFFFFFF, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                     out.ctypes.data)
+    return tuple(out[:, w].reshape(index.shape) for w in range(4))
+
+
 def uniforms(seed, purpose, index):
     """Two uniforms in (0, 1) with 53-bit resolution per index: shape index.shape + (2,).
 
     Counter = (index low word, index high word, purpose, 0); key = (seed low, seed high).
     """
-    index = np.asarray(index, dtype=np.uint64)
-    seed = int(seed)
-    w = philox4x32_10(index & _MASK, index >> np.uint64(32), np.uint64(purpose), 0,
-                      seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
-    w = [x.astype(np.float64) for x in w]
+    w = [x.astype(np.float64) for x in philox_words(seed, purpose, index)]
     # 27 high bits of one word and 26 of the next make a 53-bit integer; +0.5 keeps it off 0 and 1.
     u1 = (np.floor(w[0] / 32.0) * 67108864.0 + np.floor(w[1] / 64.0) + 0.5) / 9007199254740992.0
     u2 = (np.floor(w[2] / 32.0) * 67108864.0 + np.floor(w[3] / 64.0) + 0.5) / 9007199254740992.0

@@ -256,6 +256,12 @@ void add_stats(lqcd_solve_stats* st, const BatchStats& bs, int rhs0, int nb, int
   }
 }
 
+// The more severe of two batch outcomes: a non-finite residual outranks non-convergence.
+int worse(int a, int b) {
+  if (a == LQCD_ERR_NAN || b == LQCD_ERR_NAN) return LQCD_ERR_NAN;
+  return a != LQCD_OK ? a : b;
+}
+
 void reset_stats(lqcd_solve_stats* st) {
   if (!st) return;
   st->n_seg = 1;
@@ -449,6 +455,13 @@ int lqcd_gauge_upload(lqcd_ctx* c, const double* links, int where, double kappa,
     cudaGetLastError();
     return set_error(c, LQCD_ERR_OOM, "gauge_upload: out of device memory");
   }
+  if (kappa != c->kappa) {  // captured Schur launches hold -kappa^2 by value: recapture them
+    cudaStreamSynchronize(c->work);
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    c->graph_kernels.clear();
+  }
+  c->have_gauge = false;
   c->kappa = kappa;
   c->csw = c_sw;
   size_t bytes = (size_t)c->V * 4 * 9 * sizeof(double2);
@@ -568,8 +581,8 @@ static int solve_common(lqcd_ctx* c, const double* b, double* x, int nrhs, int w
     pack_spinor(c->g, db + (size_t)r0 * c->V * 12, eb, nb, c->work);
     BatchStats bs;
     int r = solve_batch(c, eb, ex, nb, domain, q, bs);
-    if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED) return r;
-    if (r != LQCD_OK) rc = r;
+    if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED && r != LQCD_ERR_NAN) return r;
+    rc = worse(rc, r);
     add_stats(st, bs, r0, nb, nseg);
     unpack_spinor(c->g, ex, dx + (size_t)r0 * c->V * 12, nb, c->work);
   }
@@ -577,7 +590,8 @@ static int solve_common(lqcd_ctx* c, const double* b, double* x, int nrhs, int w
   int fo = finish_out(c, x, dx, per * nrhs, where);
   if (fo) return fo;
   if (st) st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (rc != LQCD_OK) set_error(c, rc, "solve: tolerance not reached");
+  if (rc == LQCD_ERR_NAN) set_error(c, rc, "solve: non-finite residual (NaN or Inf in a source or iterate)");
+  else if (rc != LQCD_OK) set_error(c, rc, "solve: tolerance not reached");
   return rc;
 }
 
@@ -591,20 +605,35 @@ int lqcd_solve_domain(lqcd_ctx* c, const double* b, double* x, int nrhs, int whe
   return solve_common(c, b, x, nrhs, where, p, st, 1);
 }
 
-int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src, int n_tsrc, int mode, int sinks,
-                      int where, double* tau, const lqcd_solve_params* p, lqcd_solve_stats* st) {
+// Perambulators of the source vectors j in [j0, j0 + nj) (all four spins each).  sinks:
+// DIAG / ALL with Vt holding every timeslice, DIAG_SRCV with Vt holding only the source
+// timeslices in t_src order.  Columns of tau outside [j0, j0 + nj) are left untouched.
+static int perambulator_impl(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src, int n_tsrc, int mode,
+                             int sinks, int j0, int nj, int where, double* tau, const lqcd_solve_params* p,
+                             lqcd_solve_stats* st) {
   if (!c || !Vt || !t_src || !tau || n_tsrc < 1) return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: NULL");
   const Geom& g = c->g;
   const long L3 = (long)g.Lx * g.Ly * g.Lz;
   if (n_ev < 1 || n_ev > 3 * L3) return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: bad n_ev");
+  if (j0 < 0 || nj < 1 || j0 + nj > n_ev)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: source vector range outside [0, n_ev)");
   if (mode != LQCD_MODE_FULL && mode != LQCD_MODE_DOMAIN)
     return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: bad mode");
-  if (sinks != LQCD_SINKS_DIAG && sinks != LQCD_SINKS_ALL)
+  if (sinks != LQCD_SINKS_DIAG && sinks != LQCD_SINKS_ALL && sinks != LQCD_SINKS_DIAG_SRCV)
     return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: bad sinks");
   if (sinks == LQCD_SINKS_ALL && mode == LQCD_MODE_DOMAIN)
     return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: all sinks only in full mode");
+  if (n_tsrc > g.Lt) return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: more source timeslices than Lt");
   for (int k = 0; k < n_tsrc; k++)
     if (t_src[k] < 0 || t_src[k] >= g.Lt) return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: bad t");
+  const bool vsrc = sinks == LQCD_SINKS_DIAG_SRCV;
+  std::vector<int> vslot(LQCD_MAXT, -1);  // slot of each timeslice in Vt
+  for (int t = 0; t < g.Lt && !vsrc; t++) vslot[t] = t;
+  for (int k = 0; k < n_tsrc && vsrc; k++) {
+    if (vslot[t_src[k]] >= 0)
+      return set_error(c, LQCD_ERR_INVALID_ARG, "perambulator: repeated source timeslice with per-source vectors");
+    vslot[t_src[k]] = k;
+  }
   if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "perambulator: no gauge field uploaded");
   auto t0 = std::chrono::steady_clock::now();
   lqcd_solve_params q = resolve(p);
@@ -627,18 +656,22 @@ int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src,
       groups.push_back(grp);
     }
   }
-  const size_t vbytes = (size_t)g.Lt * n_ev * L3 * 3 * sizeof(double2);
+  const size_t vbytes = (size_t)(vsrc ? n_tsrc : g.Lt) * n_ev * L3 * 3 * sizeof(double2);
   const double2* dV = (const double2*)stage_in(c, Vt, vbytes, where, "h_V");
   const long n_tp = sinks == LQCD_SINKS_ALL ? g.Lt : 1;
   const size_t tau_bytes = (size_t)n_tsrc * n_tp * n_ev * 4 * n_ev * 4 * sizeof(double2);
-  double2* dtau = (double2*)stage_out(c, tau, tau_bytes, where, "h_tau");
+  // host output: untouched columns must survive the round trip through the staging buffer
+  double2* dtau = (double2*)(where == LQCD_DEVICE ? (void*)tau
+                                                  : (nj < n_ev ? (void*)stage_in(c, tau, tau_bytes, where, "h_tau")
+                                                               : stage_out(c, tau, tau_bytes, where, "h_tau")));
   if (!dV || !dtau) return set_error(c, LQCD_ERR_OOM, "perambulator: out of device memory");
-  const int nrhs_total = 4 * n_ev;
+  const int rhs_begin = 4 * j0, rhs_end = 4 * (j0 + nj);
+  const int nrhs_total = rhs_end - rhs_begin;
   const int blk = q.rhs_block > 0 ? q.rhs_block : default_block(nrhs_total);
   const size_t per = (size_t)c->V * 12 * sizeof(double2);
   int* d_jb = (int*)ws_get(c, "p_jb", 2 * blk * sizeof(int));
   unsigned char* d_mask = (unsigned char*)ws_get(c, "p_mask", LQCD_MAXT);
-  int* d_z = (int*)ws_get(c, "p_z", 2 * LQCD_MAXT * sizeof(int));
+  int* d_z = (int*)ws_get(c, "p_z", 3 * LQCD_MAXT * sizeof(int));  // sink t', source slot k, V slot of t
   double2* eb = (double2*)ws_get(c, "eo_b", per * blk);
   double2* ex = (double2*)ws_get(c, "eo_x", per * blk);
   double2* C = (double2*)ws_get(c, "p_C", (size_t)g.Lt * n_ev * 4 * blk * sizeof(double2));
@@ -646,13 +679,12 @@ int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src,
   int rc = LQCD_OK;
   int nseg = domain ? c->seg_dom.nseg : 1;
   std::vector<int> hjb(2 * blk);
-  int rhs_counter = 0;
   for (auto& grp : groups) {
     unsigned char mask[LQCD_MAXT];
     memset(mask, 0, sizeof mask);
     for (int k : grp) mask[t_src[k]] = 1;
     std::vector<int> kz, tz;
-    if (sinks == LQCD_SINKS_DIAG) {
+    if (sinks != LQCD_SINKS_ALL) {
       for (int k : grp) {
         kz.push_back(k);
         tz.push_back(t_src[k]);
@@ -664,16 +696,17 @@ int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src,
       }
     }
     int nz = (int)kz.size();
-    std::vector<int> hz(2 * LQCD_MAXT);
+    std::vector<int> hz(3 * LQCD_MAXT);
     for (int z = 0; z < nz; z++) {
       hz[z] = tz[z];
       hz[LQCD_MAXT + z] = kz[z];
     }
+    for (int t = 0; t < LQCD_MAXT; t++) hz[2 * LQCD_MAXT + t] = vslot[t];
     cudaStreamSynchronize(c->work);
     cudaMemcpyAsync(d_mask, mask, LQCD_MAXT, cudaMemcpyHostToDevice, c->work);
-    cudaMemcpyAsync(d_z, hz.data(), 2 * LQCD_MAXT * sizeof(int), cudaMemcpyHostToDevice, c->work);
-    for (int r0 = 0; r0 < nrhs_total; r0 += blk) {
-      int nb = nrhs_total - r0 < blk ? nrhs_total - r0 : blk;
+    cudaMemcpyAsync(d_z, hz.data(), 3 * LQCD_MAXT * sizeof(int), cudaMemcpyHostToDevice, c->work);
+    for (int r0 = rhs_begin; r0 < rhs_end; r0 += blk) {
+      int nb = rhs_end - r0 < blk ? rhs_end - r0 : blk;
       for (int r = 0; r < nb; r++) {
         hjb[r] = (r0 + r) / 4;
         hjb[blk + r] = (r0 + r) % 4;
@@ -681,20 +714,19 @@ int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src,
       cudaMemcpyAsync(d_jb, hjb.data(), 2 * blk * sizeof(int), cudaMemcpyHostToDevice, c->work);
       {
         PhaseTimer pt(c, "sources");
-        make_sources(g, dV, n_ev, d_jb, d_jb + blk, d_mask, eb, nb, c->work);
+        make_sources(g, dV, n_ev, d_jb, d_jb + blk, d_mask, d_z + 2 * LQCD_MAXT, eb, nb, c->work);
       }
       BatchStats bs;
       int r = solve_batch(c, eb, ex, nb, domain, q, bs);
-      if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED) return r;
-      if (r != LQCD_OK) rc = r;
+      if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED && r != LQCD_ERR_NAN) return r;
+      rc = worse(rc, r);
       add_stats(st, bs, 0, nb, nseg, false);
-      rhs_counter += nb;
       {
         const int ks = project_ksplit(g, n_ev, nb, nz);
         double2* Cp = (double2*)ws_get(c, "p_Cpart", (size_t)ks * nz * n_ev * 4 * nb * sizeof(double2));
         if (!Cp) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
         lqcd::PhaseTimer pt(c, "project");
-        project(g, dV, n_ev, ex, d_z, nz, C, Cp, nb, c->work);
+        project(g, dV, n_ev, ex, d_z, d_z + 2 * LQCD_MAXT, nz, C, Cp, nb, c->work);
       }
       long n = (long)nz * n_ev * 4 * nb;
       k_scatter_tau<<<(n + 255) / 256, 256, 0, c->work>>>(C, nz, n_ev, nb, r0, d_z + LQCD_MAXT, d_z,
@@ -706,8 +738,20 @@ int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src,
   if (fo) return fo;
   cudaStreamSynchronize(c->work);
   if (st) st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (rc != LQCD_OK) set_error(c, rc, "perambulator: tolerance not reached");
+  if (rc == LQCD_ERR_NAN) set_error(c, rc, "perambulator: non-finite residual (NaN or Inf in the colour vectors)");
+  else if (rc != LQCD_OK) set_error(c, rc, "perambulator: tolerance not reached");
   return rc;
+}
+
+int lqcd_perambulator(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src, int n_tsrc, int mode, int sinks,
+                      int where, double* tau, const lqcd_solve_params* p, lqcd_solve_stats* st) {
+  return perambulator_impl(c, Vt, n_ev, t_src, n_tsrc, mode, sinks, 0, n_ev, where, tau, p, st);
+}
+
+int lqcd_perambulator_cols(lqcd_ctx* c, const double* Vt, int n_ev, const int* t_src, int n_tsrc, int mode,
+                           int sinks, int j0, int nj, int where, double* tau, const lqcd_solve_params* p,
+                           lqcd_solve_stats* st) {
+  return perambulator_impl(c, Vt, n_ev, t_src, n_tsrc, mode, sinks, j0, nj, where, tau, p, st);
 }
 
 int lqcd_loops(lqcd_ctx* c, const double* tau, int n_ev, int n_t, const int* gamma_ids, int n_gamma,

@@ -435,9 +435,16 @@ __global__ void k_outer_update(const double* r2, const double* b2, int nsys, dou
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsys) return;
   double bn = b2[i], rn = r2[i];
+  if (!isfinite(bn) || !isfinite(rn)) {  // a non-finite source or residual: report NaN, stop the system
+    rel[i] = __longlong_as_double(0x7ff8000000000000LL);
+    active[i] = 0;
+    delta[i] = 0.5;
+    scale[i] = 1.0;
+    return;
+  }
   double rr = bn > 0 ? sqrt(rn / bn) : 0.0;
   rel[i] = rr;
-  int act = (bn > 0) && (rr > tol) && isfinite(rn);
+  int act = (bn > 0) && (rr > tol);
   if (!first && !active[i]) act = 0;
   active[i] = act;
   // the inner solve must reduce this residual by inner_tol, but no further than needed

@@ -42,9 +42,10 @@ void unpack_spinor(const Geom& g, const double2* eo, double2* lex, int nrhs, cud
 }
 
 // ------------------------------------------------------------------ sources
-// b_r(x) = [srcmask[t] == 1] e_{beta_r} (x) v_{j_r}(t)(xvec); Vt: [Lt][n_ev][L3][3]
+// b_r(x) = [srcmask[t] == 1] e_{beta_r} (x) v_{j_r}(t)(xvec); Vt: [slots][n_ev][L3][3] with the
+// vectors of timeslice t in slot vslot[t]
 __global__ void k_sources(const double2* Vt, int n_ev, const int* jr, const int* br, const unsigned char* srcmask,
-                          double2* b, Geom g, int nrhs) {
+                          const int* vslot, double2* b, Geom g, int nrhs) {
   long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long n = 2 * g.Vh * (long)nrhs;
   if (tid >= n) return;
@@ -62,15 +63,15 @@ __global__ void k_sources(const double2* Vt, int n_ev, const int* jr, const int*
   for (int spin = 0; spin < 4; spin++)
     for (int a = 0; a < 3; a++) {
       double2 v = make_double2(0.0, 0.0);
-      if (on && spin == beta) v = Vt[(((long)t * n_ev + j) * L3 + s3) * 3 + a];
+      if (on && spin == beta) v = Vt[(((long)vslot[t] * n_ev + j) * L3 + s3) * 3 + a];
       out[((spin * 3 + a) * g.Vh + cb) * nrhs + rhs] = v;
     }
 }
 
 void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, const int* br,
-                  const unsigned char* srcmask, double2* b, int nrhs, cudaStream_t st) {
+                  const unsigned char* srcmask, const int* vslot, double2* b, int nrhs, cudaStream_t st) {
   long n = 2 * g.Vh * (long)nrhs;
-  k_sources<<<(n + 255) / 256, 256, 0, st>>>(Vt, n_ev, jr, br, srcmask, b, g, nrhs); lqcd::count_launch();
+  k_sources<<<(n + 255) / 256, 256, 0, st>>>(Vt, n_ev, jr, br, srcmask, vslot, b, g, nrhs); lqcd::count_launch();
 }
 
 // ------------------------------------------------------------------ projection
@@ -83,7 +84,7 @@ void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, con
 #define PBN 32
 #define PBK 16
 __global__ void __launch_bounds__(256) k_project(const double2* Vt, int n_ev, const double2* X, const int* sinks,
-                                                 double2* Cpart, Geom g, int nrhs, int ksplit) {
+                                                 const int* vslot, double2* Cpart, Geom g, int nrhs, int ksplit) {
   __shared__ double2 As[PBK][PBM + 1];
   __shared__ double2 Bs[PBK][PBN + 1];
   const int z = blockIdx.z / ksplit, kpart = blockIdx.z - z * ksplit;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(256) k_project(const double2* Vt, int n_ev, co
   cplx<double> acc[2][2];
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++) acc[i][j] = {0.0, 0.0};
-  const double2* A = Vt + (long)tp * n_ev * K;
+  const double2* A = Vt + (long)vslot[tp] * n_ev * K;
   const long kchunks = (K + PBK - 1) / PBK;
   const long kc0 = kchunks * kpart / ksplit, kc1 = kchunks * (kpart + 1) / ksplit;
   double2* C = Cpart + (long)blockIdx.z * n_ev * N;
@@ -171,11 +172,11 @@ int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks) {
   return (int)ks;
 }
 
-void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, int nsinks, double2* C,
-             double2* Cpart, int nrhs, cudaStream_t st) {
+void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, const int* vslot,
+             int nsinks, double2* C, double2* Cpart, int nrhs, cudaStream_t st) {
   const int ksplit = project_ksplit(g, n_ev, nrhs, nsinks);
   dim3 grid((4 * nrhs + PBN - 1) / PBN, (n_ev + PBM - 1) / PBM, nsinks * ksplit);
-  k_project<<<grid, 256, 0, st>>>(Vt, n_ev, X, sinks, Cpart, g, nrhs, ksplit);
+  k_project<<<grid, 256, 0, st>>>(Vt, n_ev, X, sinks, vslot, Cpart, g, nrhs, ksplit);
   lqcd::count_launch();
   const long per_z = (long)n_ev * 4 * nrhs;
   k_project_sum<<<(per_z * nsinks + 255) / 256, 256, 0, st>>>(Cpart, C, per_z, nsinks, ksplit);

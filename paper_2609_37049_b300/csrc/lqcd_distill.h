@@ -5,12 +5,13 @@
 namespace lqcd {
 void pack_spinor(const Geom& g, const double2* lex, double2* eo, int nrhs, cudaStream_t st);
 void unpack_spinor(const Geom& g, const double2* eo, double2* lex, int nrhs, cudaStream_t st);
+// Vt: [slots][n_ev][L3][3], the colour vectors of timeslice t in slot vslot[t] (device [LQCD_MAXT])
 void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, const int* br,
-                  const unsigned char* srcmask, double2* b, int nrhs, cudaStream_t st);
+                  const unsigned char* srcmask, const int* vslot, double2* b, int nrhs, cudaStream_t st);
 // Cpart: scratch of project_ksplit(...) * nsinks * n_ev * 4 * nrhs complex entries.
 int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks);
-void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, int nsinks, double2* C,
-             double2* Cpart, int nrhs, cudaStream_t st);
+void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, const int* vslot,
+             int nsinks, double2* C, double2* Cpart, int nrhs, cudaStream_t st);
 void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w, double2* L,
            double2* Lt, cudaStream_t st);
 // C [n_gamma][T][n_t], C_avg [n_gamma][T] (may be null): connected correlator from all-sink

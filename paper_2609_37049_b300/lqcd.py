@@ -23,7 +23,7 @@ LQCD_ERR_STATE = 7
 LQCD_BC_PERIODIC, LQCD_BC_ANTIPERIODIC, LQCD_BC_OPEN = 0, 1, 2
 LQCD_HOST, LQCD_DEVICE = 0, 1
 LQCD_MODE_FULL, LQCD_MODE_DOMAIN = 0, 1
-LQCD_SINKS_DIAG, LQCD_SINKS_ALL = 0, 1
+LQCD_SINKS_DIAG, LQCD_SINKS_ALL, LQCD_SINKS_DIAG_SRCV = 0, 1, 2
 LQCD_SOLVER_BICGSTAB64, LQCD_SOLVER_MIXED, LQCD_SOLVER_FGCR_NN = 0, 1, 2
 LQCD_PREC_F64, LQCD_PREC_F32, LQCD_PREC_F16 = 0, 1, 2
 
@@ -35,6 +35,7 @@ EXPORTED = [
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
     "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant", "lqcd_schur_apply",
     "lqcd_conn_correlator", "lqcd_nr_estimator", "lqcd_ape_smear", "lqcd_smeared_links",
+    "lqcd_perambulator_cols",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -117,6 +118,8 @@ def load_library(path=_LIB_PATH):
                                    ctypes.POINTER(lqcd_solve_stats)]),
         "lqcd_perambulator": (ip, [vp, vp, ip, c_int_p, ip, ip, ip, ip, vp,
                                    ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_stats)]),
+        "lqcd_perambulator_cols": (ip, [vp, vp, ip, c_int_p, ip, ip, ip, ip, ip, ip, vp,
+                                        ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_stats)]),
         "lqcd_loops": (ip, [vp, vp, ip, ip, c_int_p, ip, vp, vp, vp, ip]),
         "lqcd_disc_correlator": (ip, [vp, vp, vp, vp, vp, ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, ip]),
         "lqcd_ape_smear": (ip, [vp, ctypes.c_double, ip]),
@@ -298,6 +301,17 @@ class Context:
                                     int(sinks), _where(Vt, tau), _ptr(tau), ctypes.byref(p),
                                     ctypes.byref(st) if st is not None else None)
         return self._check(rc)
+
+    def perambulator_cols(self, Vt, n_ev, t_src, tau, j0, nj, mode=LQCD_MODE_FULL, sinks=LQCD_SINKS_DIAG,
+                          params=None, stats=None, allow=()):
+        """Columns j in [j0, j0 + nj) (all four source spins) of the perambulators; other entries of
+        tau are left as they were."""
+        p = params or default_params()
+        st = stats.c if stats is not None else None
+        rc = _lib.lqcd_perambulator_cols(self.h, _ptr(Vt), int(n_ev), _int_array(t_src), len(t_src), int(mode),
+                                         int(sinks), int(j0), int(nj), _where(Vt, tau), _ptr(tau), ctypes.byref(p),
+                                         ctypes.byref(st) if st is not None else None)
+        return self._check(rc, allow=allow)
 
     def loops(self, tau, n_ev, n_t, gamma_ids, L, Lt, weights=None):
         return self._check(_lib.lqcd_loops(self.h, _ptr(tau), int(n_ev), int(n_t), _int_array(gamma_ids),

@@ -34,6 +34,17 @@ def units_for_step(units, step, rank, world):
     return units[(step * world + rank) % len(units)]
 
 
+def plan_unit(unit, n_full, n_groups, n_blocks):
+    """Work of bench unit `unit` (unit = step * world + rank): the full-operator source timeslice
+    index k (into t_src), the domain source-group index, and the RHS block b (source vectors
+    b * nj .. b * nj + nj - 1, all spins).  Consecutive units walk the timeslices and groups
+    first, then the blocks, so n_full * n_blocks units cover every full-operator right-hand side
+    once and n_groups * n_blocks units every domain right-hand side."""
+    if unit < 0 or min(n_full, n_groups, n_blocks) < 1:
+        raise ValueError("bad unit or sizes")
+    return unit % n_full, unit % n_groups, (unit // max(n_full, n_groups)) % n_blocks
+
+
 def gather_loops(local, rank, world, dist=None):
     """Gather {t: loop values} dictionaries of all ranks on every rank (torch.distributed object
     gather; the identity when world == 1).  Raises if two ranks produced the same timeslice."""

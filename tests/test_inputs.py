@@ -54,3 +54,20 @@ def test_random_fields_shapes():
     assert psi.shape == (3, 4, 2, 2, 2, 4, 3)
     G = random_gauge_transform((2, 2, 2, 4), 3)
     assert np.abs(np.einsum("...ab,...cb->...ac", G, G.conj()) - np.eye(3)).max() < 1e-13
+
+
+def test_compiled_philox_words_equal_the_numpy_rounds():
+    """The compiled generator used for large lattices gives the numpy version's words bit for bit."""
+    import subprocess
+    import sys
+    from lqcd_inputs import philox
+    subprocess.run([sys.executable, os.path.join(os.path.dirname(HERE), "lqcd_inputs", "build.py")], check=True)
+    philox._LIB = None
+    assert philox._compiled() is not None
+    idx = (np.arange(20000, dtype=np.uint64) * np.uint64(2654435761)) ^ np.uint64(0xDEADBEEF12345)
+    for seed, purpose in ((7, 1), (2 ** 40 + 3, 2), (5001, 4)):
+        a = philox.philox_words(seed, purpose, idx)
+        b = philox4x32_10(idx & np.uint64(0xFFFFFFFF), idx >> np.uint64(32), np.uint64(purpose), 0,
+                          seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)

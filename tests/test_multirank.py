@@ -93,3 +93,17 @@ def test_duplicate_timeslice_is_an_error():
             parts[1] = {1: 2.0}
     with pytest.raises(RuntimeError):
         gather_loops({1: 1.0}, 0, 2, FakeDist())
+
+
+def test_plan_unit_covers_every_rhs_block_once():
+    from paper_2609_37049_b300.shard import plan_unit
+    for n_full, n_groups, n_blocks in ((16, 1, 32), (32, 4, 8), (48, 10, 4)):
+        seen_full, seen_dom = set(), set()
+        for u in range(n_full * n_blocks):
+            k, g, b = plan_unit(u, n_full, n_groups, n_blocks)
+            assert 0 <= k < n_full and 0 <= g < n_groups and 0 <= b < n_blocks
+            seen_full.add((k, b))
+            if u < n_groups * n_blocks * (max(n_full, n_groups) // n_groups):
+                seen_dom.add((g, b))
+        assert len(seen_full) == n_full * n_blocks
+        assert len(seen_dom) == n_groups * n_blocks
