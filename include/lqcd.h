@@ -218,6 +218,19 @@ int lqcd_disc_correlator(lqcd_ctx* ctx, const double* L, const double* Lt, const
                          double* dC, double* C_avg, double* dC_avg, int* valid, int* n_valid,
                          double* terms, int where);
 
+/* Averages over source positions restricted to a bulk window, as the paper does on its
+ * open-boundary ensemble (Sec. 3: x0 and y0 both in the bulk, 24a..71a of 96 in Sec. 4):
+ *   C_avg[g][dt]  = mean over y0 with t_lo <= y0 and y0 + dt <= t_hi of C[g][y0 + dt][y0]
+ *                   (no wrap-around: dt = x0 - y0 >= 0 inside the window),
+ *   dC_avg[g][dt] = the same mean over the pairs with valid[y0 + dt][y0] != 0 only,
+ *   n_pairs[dt], n_valid[dt]: the number of pairs in each mean (0 where none; the mean is 0 then).
+ * C, dC: [n_gamma][Lt][Lt] complex indexed [g][x0][y0] and valid [Lt][Lt] as lqcd_disc_correlator
+ * writes them; C_avg, dC_avg: [n_gamma][Lt] complex; n_pairs, n_valid: [Lt] int.
+ * Errors: INVALID_ARG (NULL, n_gamma < 1, not 0 <= t_lo <= t_hi < Lt). */
+int lqcd_window_average(lqcd_ctx* ctx, const double* C, const double* dC, const int* valid, int n_gamma,
+                        int t_lo, int t_hi, double* C_avg, double* dC_avg, int* n_pairs, int* n_valid,
+                        int where);
+
 /* Quark-line connected correlator of Eq. Cfull with distilled quark lines, from all-sink
  * perambulators (lqcd_perambulator with LQCD_SINKS_ALL, full mode):
  *   C[g][x0][k] = - Tr[ Gamma tau(x0, y0) Gamma~ tau(y0, x0) ],  y0 = t_src[k],

@@ -242,3 +242,68 @@ class WilsonClover:
             cols = self.apply(E.reshape(c1 - c0, Lt, Lz, Ly, Lx, 4, 3))
             M[:, c0:c1] = cols.reshape(c1 - c0, n).T
         return M
+
+
+# ----------------------------------------------------------------------------- single sites
+def apply_at_sites(U, kappa, c_sw, psi, sites, bc_t=BC_ANTIPERIODIC, extents=None, t_start=0):
+    """(D psi)(x) at the listed sites only, from the definitions written out per site:
+
+        (D psi)(x) = A(x) psi(x) - kappa sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+                                                 + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ],
+        A(x) = 1 + i kappa c_sw sum_{mu<nu} sigma_{mu nu} (x) (Q_{mu nu}(x) - Q_{mu nu}(x)^dag) / 8,
+
+    with the four clover leaves of Q built from explicit link coordinates, the time boundary phase
+    on the t-hop between Lt-1 and 0, and (extents given) the t-hops between different domains
+    removed.  For lattices too large to build the whole operator; it shares no code with
+    WilsonClover beyond the gamma matrices.  psi: [t, z, y, x, 4, 3]; sites: iterable of (x, y, z, t).
+    Returns [n_sites, 4, 3]."""
+    Lt, Lz, Ly, Lx = U.shape[:4]
+    L = (Lx, Ly, Lz, Lt)
+    g = gammas()
+    one = np.eye(4, dtype=np.complex128)
+    phase = {BC_PERIODIC: 1.0, BC_ANTIPERIODIC: -1.0, BC_OPEN: 0.0}[bc_t]
+    cut = cut_after(extents, Lt, t_start) if extents is not None else np.zeros(Lt, dtype=bool)
+
+    def link(c, mu):
+        return U[c[3] % Lt, c[2] % Lz, c[1] % Ly, c[0] % Lx, mu]
+
+    def step(c, mu, n):
+        d = list(c)
+        d[mu] += n
+        return d
+
+    def dag(M):
+        return M.conj().T
+
+    def leaves(c, mu, nu):
+        xpm, xpn, xmm, xmn = step(c, mu, 1), step(c, nu, 1), step(c, mu, -1), step(c, nu, -1)
+        l1 = link(c, mu) @ link(xpm, nu) @ dag(link(xpn, mu)) @ dag(link(c, nu))
+        l2 = link(c, nu) @ dag(link(step(xpn, mu, -1), mu)) @ dag(link(xmm, nu)) @ link(xmm, mu)
+        l3 = dag(link(xmm, mu)) @ dag(link(step(xmm, nu, -1), nu)) @ link(step(xmm, nu, -1), mu) @ link(xmn, nu)
+        l4 = dag(link(xmn, nu)) @ link(xmn, mu) @ link(step(xpm, nu, -1), nu) @ dag(link(c, mu))
+        return l1 + l2 + l3 + l4
+
+    def spinor(c):
+        return psi[c[3] % Lt, c[2] % Lz, c[1] % Ly, c[0] % Lx]
+
+    out = []
+    for site in sites:
+        c = [int(v) for v in site]
+        A = np.eye(12, dtype=np.complex128)
+        for (mu, nu) in PLANES:
+            Q = leaves(c, mu, nu)
+            F = (Q - dag(Q)) / 8.0
+            A += 1j * kappa * c_sw * np.kron(sigma(mu, nu), F)
+        res = (A @ spinor(c).reshape(12)).reshape(4, 3)
+        for mu in range(4):
+            cf = cb = 1.0
+            if mu == 3:  # forward hop t -> t+1 and backward hop t-1 -> t
+                t, tb = c[3], (c[3] - 1) % Lt
+                cf = (phase if t == Lt - 1 else 1.0) * (0.0 if cut[t] else 1.0)
+                cb = (phase if tb == Lt - 1 else 1.0) * (0.0 if cut[tb] else 1.0)
+            fwd = spinor(step(c, mu, 1)) @ link(c, mu).T  # (U psi)_{s a} = sum_b U_ab psi_{s b}
+            xm = step(c, mu, -1)
+            bwd = spinor(xm) @ link(xm, mu).conj()        # (U^dag psi)_{s a} = sum_b conj(U_ba) psi_{s b}
+            res = res - kappa * (cf * ((one - g[mu]) @ fwd) + cb * ((one + g[mu]) @ bwd))
+        out.append(res)
+    return np.array(out)

@@ -205,6 +205,37 @@ def disc_correlators(L, Lt, Ld, Ltd, extents, vev=True, t_start=0):
                 n_valid=n_valid, terms=terms)
 
 
+def window_average(C, dC, valid, t_lo, t_hi):
+    """Averages over source positions restricted to a bulk window (Sec. 3: source and sink both
+    in t_lo <= x0, y0 <= t_hi, away from the open time boundaries; Sec. 4 quotes 24a..71a):
+        C_avg[g, dt]  = mean over y0 in [t_lo, t_hi - dt] of C[g, y0 + dt, y0]        (no wrap),
+        dC_avg[g, dt] = the same over the pairs with valid[y0 + dt, y0] (distinct domains),
+    with n_pairs[dt] = t_hi - t_lo + 1 - dt and n_valid[dt] the number of valid pairs (0 where no
+    pair exists, the averages then 0), dt = 0 .. T-1."""
+    n_g, T = C.shape[0], C.shape[1]
+    if not 0 <= t_lo <= t_hi < T:
+        raise ValueError("window outside [0, T)")
+    C_avg = np.zeros((n_g, T), dtype=np.complex128)
+    dC_avg = np.zeros((n_g, T), dtype=np.complex128)
+    n_pairs = np.zeros(T, dtype=np.int32)
+    n_valid = np.zeros(T, dtype=np.int32)
+    for dt in range(T):
+        for y0 in range(t_lo, t_hi + 1):
+            x0 = y0 + dt
+            if x0 > t_hi:
+                break
+            C_avg[:, dt] += C[:, x0, y0]
+            n_pairs[dt] += 1
+            if valid[x0, y0]:
+                dC_avg[:, dt] += dC[:, x0, y0]
+                n_valid[dt] += 1
+        if n_pairs[dt]:
+            C_avg[:, dt] /= n_pairs[dt]
+        if n_valid[dt]:
+            dC_avg[:, dt] /= n_valid[dt]
+    return dict(C_avg=C_avg, dC_avg=dC_avg, n_pairs=n_pairs, n_valid=n_valid)
+
+
 def conn_correlator(tau_all, t_src, gamma_ids):
     """C[g, x0, k] = C^(c)(x0, y0 = t_src[k]) and its y0 average C_avg[g, dt] = mean over k of
     C[g, (t_src[k] + dt) mod T, k].  tau_all[k, t', i, a, j, b] = tau(t', t_src[k]) (all sinks);

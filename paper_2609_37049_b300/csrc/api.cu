@@ -883,6 +883,31 @@ int lqcd_disc_correlator(lqcd_ctx* c, const double* L, const double* Lt, const d
   return LQCD_OK;
 }
 
+int lqcd_window_average(lqcd_ctx* c, const double* C, const double* dC, const int* valid, int n_gamma, int t_lo,
+                        int t_hi, double* C_avg, double* dC_avg, int* n_pairs, int* n_valid, int where) {
+  if (!c || !C || !dC || !valid || !C_avg || !dC_avg || !n_pairs || !n_valid || n_gamma < 1)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "window_average: bad arguments");
+  const int T = c->g.Lt;
+  if (t_lo < 0 || t_hi < t_lo || t_hi >= T)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "window_average: window outside [0, Lt)");
+  Scope sc(c);
+  const size_t cb = (size_t)n_gamma * T * T * sizeof(double2), ab = (size_t)n_gamma * T * sizeof(double2);
+  const double2* dCo = (const double2*)stage_in(c, C, cb, where, "w_C");
+  const double2* ddC = (const double2*)stage_in(c, dC, cb, where, "w_dC");
+  const int* dv = (const int*)stage_in(c, valid, (size_t)T * T * sizeof(int), where, "w_valid");
+  double2* dCa = (double2*)stage_out(c, C_avg, ab, where, "w_Ca");
+  double2* ddCa = (double2*)stage_out(c, dC_avg, ab, where, "w_dCa");
+  int* dnp = (int*)stage_out(c, n_pairs, (size_t)T * sizeof(int), where, "w_np");
+  int* dnv = (int*)stage_out(c, n_valid, (size_t)T * sizeof(int), where, "w_nv");
+  if (!dCo || !ddC || !dv || !dCa || !ddCa || !dnp || !dnv) return set_error(c, LQCD_ERR_OOM, "window_average: OOM");
+  window_average(dCo, ddC, dv, n_gamma, T, t_lo, t_hi, dCa, ddCa, dnp, dnv, c->work);
+  if (int e = cuda_check(c, "window_average")) return e;
+  if (int e = finish_out(c, C_avg, dCa, ab, where)) return e;
+  if (int e = finish_out(c, dC_avg, ddCa, ab, where)) return e;
+  if (int e = finish_out(c, n_pairs, dnp, (size_t)T * sizeof(int), where)) return e;
+  return finish_out(c, n_valid, dnv, (size_t)T * sizeof(int), where);
+}
+
 }  // extern "C"
 
 extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_variant, double* best_ms) {

@@ -402,6 +402,40 @@ __global__ void k_corr_avg(const double2* C, const double2* dC, const int* dom, 
   if (g == 0) n_valid[dt] = nv;
 }
 
+// Bulk-window averages: source and sink both in [t_lo, t_hi], x0 = y0 + dt without wrap-around;
+// one thread per (gamma, dt).  n_pairs / n_valid: pairs in the window / of those in distinct domains.
+__global__ void k_window_avg(const double2* C, const double2* dC, const int* valid, int n_g, int T, int t_lo,
+                             int t_hi, double2* C_avg, double2* dC_avg, int* n_pairs, int* n_valid) {
+  const int g = blockIdx.x;
+  const int dt = threadIdx.x;
+  if (dt >= T) return;
+  cplx<double> s = {0, 0}, sd = {0, 0};
+  int np = 0, nv = 0;
+  for (int y0 = t_lo; y0 + dt <= t_hi; y0++) {
+    const int x0 = y0 + dt;
+    const long o = ((long)g * T + x0) * T + y0;
+    s = s + cplx<double>{C[o].x, C[o].y};
+    np++;
+    if (valid[(long)x0 * T + y0]) {
+      sd = sd + cplx<double>{dC[o].x, dC[o].y};
+      nv++;
+    }
+  }
+  C_avg[(long)g * T + dt] = np ? make_double2(s.re / np, s.im / np) : make_double2(0.0, 0.0);
+  dC_avg[(long)g * T + dt] = nv ? make_double2(sd.re / nv, sd.im / nv) : make_double2(0.0, 0.0);
+  if (g == 0) {
+    n_pairs[dt] = np;
+    n_valid[dt] = nv;
+  }
+}
+
+void window_average(const double2* C, const double2* dC, const int* valid, int n_g, int T, int t_lo, int t_hi,
+                    double2* C_avg, double2* dC_avg, int* n_pairs, int* n_valid, cudaStream_t st) {
+  k_window_avg<<<n_g, ((T + 31) / 32) * 32, 0, st>>>(C, dC, valid, n_g, T, t_lo, t_hi, C_avg, dC_avg, n_pairs,
+                                                     n_valid);
+  lqcd::count_launch();
+}
+
 void correlators(const double2* L, const double2* Lt, const double2* Ld, const double2* Ltd, int n_cfg, int n_g,
                  int T, int vev, const int* dom, double2* C, double2* Cdd, double2* dC, double2* C_avg,
                  double2* dC_avg, int* valid, int* n_valid, double2* terms, double2* dL, double2* dLt,

@@ -24,6 +24,10 @@ void correlators(const double2* L, const double2* Lt, const double2* Ld, const d
                  int T, int vev, const int* dom, double2* C, double2* Cdd, double2* dC, double2* C_avg,
                  double2* dC_avg, int* valid, int* n_valid, double2* terms, double2* dL, double2* dLt,
                  cudaStream_t st);
+// Bulk-window averages of C, dC [n_g][T][T] (x0, y0) over t_lo <= y0, y0 + dt <= t_hi; outputs
+// C_avg, dC_avg [n_g][T], n_pairs, n_valid [T].
+void window_average(const double2* C, const double2* dC, const int* valid, int n_g, int T, int t_lo, int t_hi,
+                    double2* C_avg, double2* dC_avg, int* n_pairs, int* n_valid, cudaStream_t st);
 void build_gauge(lqcd_ctx* c, const double2* links_dev, int* bad_dev);
 
 // Per-batch solver statistics (host side).

@@ -35,7 +35,7 @@ EXPORTED = [
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
     "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant", "lqcd_schur_apply",
     "lqcd_conn_correlator", "lqcd_nr_estimator", "lqcd_ape_smear", "lqcd_smeared_links",
-    "lqcd_perambulator_cols",
+    "lqcd_perambulator_cols", "lqcd_window_average",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -121,6 +121,7 @@ def load_library(path=_LIB_PATH):
         "lqcd_perambulator_cols": (ip, [vp, vp, ip, c_int_p, ip, ip, ip, ip, ip, ip, vp,
                                         ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_stats)]),
         "lqcd_loops": (ip, [vp, vp, ip, ip, c_int_p, ip, vp, vp, vp, ip]),
+        "lqcd_window_average": (ip, [vp, vp, vp, vp, ip, ip, ip, vp, vp, vp, vp, ip]),
         "lqcd_disc_correlator": (ip, [vp, vp, vp, vp, vp, ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, ip]),
         "lqcd_ape_smear": (ip, [vp, ctypes.c_double, ip]),
         "lqcd_smeared_links": (ip, [vp, vp, ip]),
@@ -326,6 +327,14 @@ class Context:
             self.h, _ptr(L), _ptr(Lt), _ptr(Ld), _ptr(Ltd), n_cfg, n_g, int(vev), _ptr(out["C"]),
             _ptr(out["Cdd"]), _ptr(out["dC"]), _ptr(out["C_avg"]), _ptr(out["dC_avg"]),
             _ptr(out["valid"], np.int32), _ptr(out["n_valid"], np.int32), _ptr(terms), w))
+
+    def window_average(self, C, dC, valid, t_lo, t_hi, out):
+        """Bulk-window averages: out dict with C_avg, dC_avg (complex [n_gamma, Lt]) and n_pairs,
+        n_valid (int32 [Lt]) over source and sink both in [t_lo, t_hi]."""
+        return self._check(_lib.lqcd_window_average(
+            self.h, _ptr(C), _ptr(dC), _ptr(valid, np.int32), C.shape[0], int(t_lo), int(t_hi), _ptr(out["C_avg"]),
+            _ptr(out["dC_avg"]), _ptr(out["n_pairs"], np.int32), _ptr(out["n_valid"], np.int32),
+            _where(C, dC, valid, out["C_avg"])))
 
     def ape_smear(self, alpha, n_iter):
         """Smear the spatial links (used by laplace_eigs); n_iter = 0 drops the smearing."""

@@ -16,7 +16,7 @@ from tests.lattice_cases import SMALL, ROUGH, gauge
 pytestmark = pytest.mark.gpu
 
 pytest.importorskip("paper_2609_37049_b300")
-from paper_2609_37049_b300 import Context, Stats, default_params, lqcd  # noqa: E402
+from paper_2609_37049_b300 import Context, LqcdError, Stats, default_params, lqcd  # noqa: E402
 
 GAMMAS = [5, 1, 2, 3, 0]  # gamma_5, gamma_x, gamma_y, gamma_z, 1
 
@@ -264,3 +264,60 @@ def test_full_estimator_two_configs():
     scale = np.abs(np.einsum("cgx,cgy->gxy", arr(Lo_), arr(Lto_)) / 2).max()
     for k, ko in (("C", "C"), ("Cdd", "C_dd"), ("dC", "dC"), ("dC_avg", "dC_avg")):
         assert np.abs(g[k] - o[ko]).max() <= 1e-8 * scale, k
+
+
+def test_open_bc_shifted_tiling_window_end_to_end():
+    """The paper's geometry (Sec. 3: open time boundaries, averages over source and sink in the
+    bulk; regions placed around the chosen timeslices, Fig. 1): open-boundary operator, a tiling
+    starting at t = 2 whose last domain wraps, perambulators (full and domain) -> loops -> C, C_LL,
+    dC over two configurations -> bulk-window averages, each stage against the oracle."""
+    from oracle.dirac import BC_OPEN
+    from oracle.distill import window_average
+    case = SMALL
+    T, n_ev = case["dims"][3], case["n_ev"]
+    ext, t0 = [3, 5], 2
+    gids = [5, 0]
+    gpu = {k: [] for k in ("L", "Lt", "Ld", "Ltd")}
+    ora = {k: [] for k in ("L", "Lt", "Ld", "Ltd")}
+    for seed in (1011, 1012):
+        U = gauge(case, seed)
+        lam, V = laplace_eigs(U, n_ev)
+        ctx = Context(case["dims"], bc_t=lqcd.LQCD_BC_OPEN)
+        ctx.gauge_upload(U, case["kappa"], case["c_sw"])
+        ctx.set_domains(ext, t_start=t0)
+        op = WilsonClover(U, case["kappa"], case["c_sw"], bc_t=BC_OPEN)
+        for mode, o, (a, b) in ((lqcd.LQCD_MODE_FULL, op, ("L", "Lt")),
+                                (lqcd.LQCD_MODE_DOMAIN, op.restricted(ext, t0), ("Ld", "Ltd"))):
+            tau = _gpu_tau(ctx, V, n_ev, range(T), mode)
+            want = perambulators(o, V, range(T))
+            assert tau_rel(tau, want) < 1e-9
+            L, Lt = np.zeros((len(gids), T), complex), np.zeros((len(gids), T), complex)
+            ctx.loops(tau, n_ev, T, gids, L, Lt)
+            Lo, Lto = loops(want, gids)
+            assert np.abs(L - Lo).max() <= 1e-9 * np.abs(Lo).max()
+            gpu[a].append(L)
+            gpu[b].append(Lt)
+            ora[a].append(Lo)
+            ora[b].append(Lto)
+    arr = lambda x: np.ascontiguousarray(np.array(x))
+    g = _gpu_corr(ctx, arr(gpu["L"]), arr(gpu["Lt"]), arr(gpu["Ld"]), arr(gpu["Ltd"]), True)
+    o = disc_correlators(arr(ora["L"]), arr(ora["Lt"]), arr(ora["Ld"]), arr(ora["Ltd"]), ext, vev=True, t_start=t0)
+    scale = np.abs(np.einsum("cgx,cgy->gxy", arr(ora["L"]), arr(ora["Lt"])) / 2).max()
+    for k, ko in (("C", "C"), ("Cdd", "C_dd"), ("dC", "dC")):
+        assert np.abs(g[k] - o[ko]).max() <= 1e-8 * scale, k
+    assert np.array_equal(g["valid"], o["valid"])
+    t_lo, t_hi = 1, 6
+    out = dict(C_avg=np.zeros((len(gids), T), complex), dC_avg=np.zeros((len(gids), T), complex),
+               n_pairs=np.zeros(T, np.int32), n_valid=np.zeros(T, np.int32))
+    ctx.window_average(g["C"], g["dC"], g["valid"], t_lo, t_hi, out)
+    w = window_average(o["C"], o["dC"], o["valid"], t_lo, t_hi)
+    assert np.array_equal(out["n_pairs"], w["n_pairs"]) and np.array_equal(out["n_valid"], w["n_valid"])
+    for k in ("C_avg", "dC_avg"):
+        assert np.abs(out[k] - w[k]).max() <= 1e-8 * scale, k
+    # the arithmetic alone, on the oracle's correlators: FP64 round-off
+    ctx.window_average(np.ascontiguousarray(o["C"]), np.ascontiguousarray(o["dC"]),
+                       np.ascontiguousarray(o["valid"].astype(np.int32)), t_lo, t_hi, out)
+    for k in ("C_avg", "dC_avg"):
+        assert np.abs(out[k] - w[k]).max() <= 1e-13 * scale, k
+    with pytest.raises(LqcdError):
+        ctx.window_average(g["C"], g["dC"], g["valid"], 5, 4, out)

@@ -203,3 +203,22 @@ def test_schur_factorisation_of_propagator():
     assert np.abs(Dinv[np.ix_(lam, lam)] - rhs).max() < 1e-11
     # the correction term is what the domain loop leaves out; it is not negligible here
     assert np.abs(Dinv[np.ix_(lam, lam)] - DLi).max() > 1e-6
+
+
+def test_single_site_operator_equals_the_lattice_operator():
+    """apply_at_sites (per-site leaves and hops from explicit coordinates, for lattices too large
+    for the whole-lattice oracle) agrees with WilsonClover on a ragged lattice, for every time
+    boundary condition, with and without a shifted domain tiling."""
+    from lqcd_inputs import gauge_field, random_spinors
+    from oracle.dirac import WilsonClover, apply_at_sites
+    dims = (4, 6, 2, 8)
+    U = gauge_field(dims, 0.4, 11)
+    psi = random_spinors(dims, 1, 12)[0]
+    sites = [(x, y, z, t) for t in range(8) for z in range(2) for y in range(6) for x in range(4)][::5]
+    for bc in (0, 1, 2):
+        for ext, ts in ((None, 0), ([3, 5], 2)):
+            op = WilsonClover(U, 0.13, 1.7, bc, ext, ts)
+            full = op.apply(psi[None])[0]
+            loc = apply_at_sites(U, 0.13, 1.7, psi, sites, bc, ext, ts)
+            ref = np.array([full[t, z, y, x] for (x, y, z, t) in sites])
+            assert np.abs(loc - ref).max() <= 1e-14 * np.abs(ref).max()

@@ -190,3 +190,37 @@ def test_source_average_of_translation_invariant_correlator():
 def test_effective_mass_of_exponential():
     C = 3.0 * np.exp(-0.7 * np.arange(6))
     assert np.allclose(effective_mass(C), 0.7)
+
+
+def test_window_average_closed_forms():
+    """Bulk-window averages (Sec. 3 / Sec. 4 restrict x0, y0 to the bulk): a translation-invariant
+    correlator f(x0 - y0) averages to f(dt) with t_hi - t_lo + 1 - dt pairs; pairs in one domain
+    are excluded from dC only; the full window with a periodic f reproduces the non-wrapping part
+    of the all-y0 average."""
+    from oracle.distill import window_average
+    T, lo, hi = 16, 3, 12
+    f = np.exp(-0.3 * np.arange(T)) + 0.1j * np.arange(T)
+    x0, y0 = np.meshgrid(np.arange(T), np.arange(T), indexing="ij")
+    C = f[(x0 - y0) % T][None].repeat(2, axis=0)
+    C[1] *= 2.0
+    dC = 3.0 * C
+    dom = np.repeat(np.arange(4), 4)
+    valid = (dom[:, None] != dom[None, :]).astype(np.int32)
+    w = window_average(C, dC, valid, lo, hi)
+    n = hi - lo + 1
+    for dt in range(T):
+        assert w["n_pairs"][dt] == max(0, n - dt)
+        if dt < n:
+            assert np.allclose(w["C_avg"][:, dt], [f[dt], 2 * f[dt]])
+        else:
+            assert np.all(w["C_avg"][:, dt] == 0)
+        brute = sum(1 for y in range(lo, hi + 1) if y + dt <= hi and dom[y + dt] != dom[y])
+        assert w["n_valid"][dt] == brute
+        if brute:
+            assert np.allclose(w["dC_avg"][:, dt], [3 * f[dt], 6 * f[dt]])
+    # a pair inside one domain never enters dC: make those entries huge
+    dC2 = dC.copy()
+    dC2[:, valid == 0] = 1e30
+    assert np.allclose(window_average(C, dC2, valid, lo, hi)["dC_avg"], w["dC_avg"])
+    with pytest.raises(ValueError):
+        window_average(C, dC, valid, 5, 4)
