@@ -221,7 +221,7 @@ class Workload:
         import torch
         from lqcd_inputs import colour_vectors, gauge_field
         from paper_2609_37049_b300 import Context, lqcd
-        from paper_2609_37049_b300.shard import source_groups
+        from paper_2609_37049_b300.shard import domain_groups
 
         self.name, self.wl = name, WORKLOADS[name]
         wl = self.wl
@@ -254,10 +254,8 @@ class Workload:
             del Vh
         torch.cuda.synchronize()
         self.t_vectors = time.time() - t0
-        # source groups: one source timeslice per domain, restricted to t_src
-        dom_groups = source_groups(self.T, wl["extents"])
-        tset = set(self.t_src)
-        self.groups = [g2 for g2 in ([t for t in g if t in tset] for g in dom_groups) if g2]
+        # source groups for the multi-site domain solves: at most one source timeslice per domain
+        self.groups = domain_groups(self.t_src, self.T, wl["extents"])
         n_t = len(self.t_src)
         c128 = dict(dtype=torch.complex128, device="cuda")
         self.tau_f = torch.zeros((n_t, self.n_ev, 4, self.n_ev, 4), **c128)
@@ -458,6 +456,8 @@ def run_ours(args, rank, world):
     del H
 
     res["e2e"] = e2e
+    if os.environ.get("LQCD_PHASE_TIMING") == "1":  # diagnostic runs: GPU ms per solver phase
+        res["phase_ms"] = W.ctx.phase_times()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"], _ = cpu_baseline(W.wl)
     return res
@@ -504,8 +504,8 @@ def extras(W, peak, peak_kind, dev):
     sweep = {}
     for ext, tiling in W.wl["sweep"].items():
         ctx.set_domains(tiling)
-        from paper_2609_37049_b300.shard import source_groups
-        grp = [t for t in source_groups(W.T, tiling)[0] if t in W.slot] or [W.t_src[0]]
+        from paper_2609_37049_b300.shard import domain_groups
+        grp = domain_groups(W.t_src, W.T, tiling)[0]
         ks = [W.slot[t] for t in grp]
         Vg = W.V[ks].contiguous()
         tg = torch.zeros((len(grp), W.n_ev, 4, W.n_ev, 4), dtype=torch.complex128, device="cuda")

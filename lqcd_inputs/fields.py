@@ -12,24 +12,16 @@ Recipes (index arithmetic fixed here so both sides draw identical numbers):
   Cholesky-QR applied twice (a Gram-Schmidt-equivalent, deterministic orthonormalisation).
 * spinors: element ``(r, s, spin, colour)`` uses index ``((r*V + s)*4 + spin)*3 + colour``.
 """
-import os
-from concurrent.futures import ThreadPoolExecutor
-
 import numpy as np
 
 from .philox import gaussians
 
 
 def _per_timeslice(fn, items):
-    """fn(k, t) for every (k, t) of items, on a thread pool for large fields (numpy releases the
-    interpreter lock in its array kernels); the results do not depend on the scheduling."""
-    items = list(items)
-    if len(items) <= 2:
-        for k, t in items:
-            fn(k, t)
-        return
-    with ThreadPoolExecutor(max_workers=min(len(items), os.cpu_count() or 1)) as ex:
-        list(ex.map(lambda kt: fn(*kt), items))
+    """fn(k, t) for every (k, t) of items, in order (the compiled generators and BLAS parallelise
+    inside each timeslice)."""
+    for k, t in items:
+        fn(k, t)
 
 PURPOSE_GAUGE = 1
 PURPOSE_COLOUR = 2
@@ -57,6 +49,14 @@ def gell_mann():
 
 
 def _su3_from_ids(seed, purpose, link_ids, eps):
+    from .philox import _compiled
+    lib = _compiled()
+    if lib is not None and link_ids.size >= 1024:  # compiled recipe: Jacobi eigen-decomposition of H
+        ids = np.ascontiguousarray(link_ids, dtype=np.uint64)
+        out = np.empty((ids.size, 3, 3), dtype=np.complex128)
+        lib.su3_links(ids.ctypes.data, ids.size, int(purpose) & 0xFFFFFFFF, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                      float(eps), out.ctypes.data)
+        return out
     g = gaussians(seed, purpose, link_ids[:, None] * 4 + np.arange(4, dtype=np.uint64)[None, :])
     h = g.reshape(link_ids.shape[0], 8)
     H = np.einsum("na,aij->nij", h, gell_mann() / 2.0)
@@ -96,9 +96,10 @@ def random_gauge_transform(dims, seed, eps=1.0):
 
 def _cholqr_rows(X):
     """Orthonormalise the rows of X (n, m) by Cholesky-QR: X <- L^{-1} X with L L^H = X X^H."""
+    from scipy.linalg import solve_triangular
     G = X @ X.conj().T
     L = np.linalg.cholesky(G)
-    return np.linalg.solve(L, X)
+    return solve_triangular(L, X, lower=True)
 
 
 def colour_vectors(dims, n_ev, seed, timeslices=None):

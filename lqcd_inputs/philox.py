@@ -54,6 +54,11 @@ def _compiled():
             lib.philox_words.restype = None
             lib.philox_words.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_uint32, ctypes.c_uint64,
                                          ctypes.c_void_p]
+            lib.gaussian_pairs.restype = None
+            lib.gaussian_pairs.argtypes = lib.philox_words.argtypes
+            lib.su3_links.restype = None
+            lib.su3_links.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_uint32, ctypes.c_uint64,
+                                      ctypes.c_double, ctypes.c_void_p]
             _LIB = lib
     return _LIB or None
 
@@ -87,7 +92,17 @@ def uniforms(seed, purpose, index):
 
 
 def gaussians(seed, purpose, index):
-    """Two independent N(0,1) numbers per index (Box-Muller): shape index.shape + (2,)."""
+    """Two independent N(0,1) numbers per index (Box-Muller): shape index.shape + (2,).
+    Large index arrays use the compiled generator (same recipe; libm's log / cos / sin, so the
+    numbers can differ from numpy's in the last bit)."""
+    index = np.asarray(index, dtype=np.uint64)
+    lib = _compiled()
+    if lib is not None and index.size >= 4096:
+        flat = np.ascontiguousarray(index.ravel())
+        out = np.empty((flat.size, 2), dtype=np.float64)
+        lib.gaussian_pairs(flat.ctypes.data, flat.size, int(purpose) & 0xFFFFFFFF,
+                           int(seed) & 0xFFFFFFFFFFFFFFFF, out.ctypes.data)
+        return out.reshape(index.shape + (2,))
     u = uniforms(seed, purpose, index)
     r = np.sqrt(-2.0 * np.log(u[..., 0]))
     th = 2.0 * np.pi * u[..., 1]

@@ -65,13 +65,15 @@ def tune(ctx, cache=None, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F16, lq
     for prec in precisions:
         variants[str(prec)] = {}
         for n in blocks:
-            # about 20 work vectors of the inner precision per batch plus FP64 outer vectors
-            need = 20 * _spinor_bytes(ctx, prec, n) + 8 * _spinor_bytes(ctx, lqcd.LQCD_PREC_F64, n)
-            if need > memory_budget:
+            # timing a variant needs two vectors of the block; choosing the block as the solver's
+            # width needs its work vectors (about 20 of the inner precision plus FP64 outer ones)
+            # to fit the budget.  A single requested block is tuned whatever its size.
+            if 2 * _spinor_bytes(ctx, prec, n) > memory_budget:
                 continue
             t, ms = ctx.tune_dslash(prec, n)
             variants[str(prec)][str(n)] = t
-            if prec == lqcd.LQCD_PREC_F32:
+            need = 20 * _spinor_bytes(ctx, prec, n) + 8 * _spinor_bytes(ctx, lqcd.LQCD_PREC_F64, n)
+            if prec == lqcd.LQCD_PREC_F32 and (need <= memory_budget or len(blocks) == 1):
                 per_rhs[n] = ms / n
     best = min(per_rhs, key=per_rhs.get) if per_rhs else 64
     choice = {"variant": variants, "rhs_block": int(best),

@@ -22,6 +22,32 @@ def source_groups(Lt, extents, t_start=0):
     return [[int((s + g) % Lt) for s, e in zip(starts, extents) if g < e] for g in range(max(extents))]
 
 
+def domain_groups(t_src, Lt, extents, t_start=0):
+    """Groups of the source timeslices t_src for multi-site domain solves: each group holds at
+    most one timeslice per domain (level k of every domain's list, in t_src order), the grouping
+    the library's domain-mode perambulators use."""
+    extents = [int(e) for e in extents]
+    if sum(extents) != Lt or min(extents) < 1:
+        raise ValueError("extents must tile the time axis")
+    dom = np.empty(Lt, dtype=np.int64)
+    t = int(t_start)
+    for d, e in enumerate(extents):
+        for k in range(e):
+            dom[(t + k) % Lt] = d
+        t += e
+    per = {}
+    for ts in t_src:
+        per.setdefault(int(dom[int(ts)]), []).append(int(ts))
+    groups = []
+    level = 0
+    while True:
+        grp = [per[d][level] for d in sorted(per) if level < len(per[d])]
+        if not grp:
+            return groups
+        groups.append(grp)
+        level += 1
+
+
 def shard(units, rank, world):
     """Units of this rank: round-robin over the list."""
     if not 0 <= rank < world:

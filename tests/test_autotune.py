@@ -32,6 +32,16 @@ def test_tune_writes_cache_and_reload_installs_it(tmp_path):
 
 
 def test_memory_budget_excludes_wide_blocks(tmp_path):
+    """Every block is timed (two vectors fit), but a block whose solver work vectors exceed the
+    budget is not chosen as the RHS width."""
     c = FakeCtx()
     ch = autotune.tune(c, cache=None, precisions=(lqcd.LQCD_PREC_F32,), memory_budget=1 << 30)
-    assert [n for _, n in c.timed] == [16, 32, 64] and ch["rhs_block"] == 64
+    assert [n for _, n in c.timed] == [16, 32, 64, 128] and ch["rhs_block"] == 64
+    assert ch["variant"][str(lqcd.LQCD_PREC_F32)]["128"] == 2
+
+
+def test_single_requested_block_is_tuned_beyond_the_budget():
+    """A caller that fixes the block (the 48^3 x 96 bench, 16 RHS) still gets its launch variant."""
+    c = FakeCtx()
+    ch = autotune.tune(c, cache=None, precisions=(lqcd.LQCD_PREC_F32,), blocks=(64,), memory_budget=200 << 20)
+    assert c.timed == [(lqcd.LQCD_PREC_F32, 64)] and ch["rhs_block"] == 64

@@ -71,3 +71,22 @@ def test_compiled_philox_words_equal_the_numpy_rounds():
                           seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def test_compiled_generators_follow_the_numpy_recipe():
+    """The compiled Box-Muller normals and SU(3) links (Jacobi eigen-decomposition of H) agree with
+    the numpy recipe to round-off, so inputs do not depend on which path drew them."""
+    from lqcd_inputs import philox
+    from lqcd_inputs.fields import _su3_from_ids
+    assert philox._compiled() is not None
+    ids = np.arange(50000, dtype=np.uint64) * np.uint64(3) + np.uint64(77)
+    a = philox.gaussians(91, 2, ids)
+    lib, philox._LIB = philox._LIB, False
+    try:
+        b = philox.gaussians(91, 2, ids)
+        Un = _su3_from_ids(91, 1, ids, 0.6)
+    finally:
+        philox._LIB = lib
+    assert np.abs(a - b).max() < 1e-13
+    Uc = _su3_from_ids(91, 1, ids, 0.6)
+    assert np.abs(Uc - Un).max() < 1e-13
