@@ -47,17 +47,20 @@ WORKLOADS = {
         title="48^3x96 scale run: batched mixed-precision distillation, full + domain solves",
         dims=(48, 48, 48, 96), eps=0.6, kappa=0.126, csw=1.7, n_ev=128, t_src=list(range(0, 96, 6)),
         extents=[4] * 24, sweep={8: [8] * 12, 12: [12] * 8}, gauge_seed=5001, cv_seed=5002,
-        sources="seeded orthonormal colour vectors (Cholesky-QR twice)", rhs_block=16, solver_sample_rhs=4),
+        sources="seeded orthonormal colour vectors (Cholesky-QR twice)", rhs_block=16, pipeline=1,
+        solver_sample_rhs=4),
     "mixed": dict(
         title="16^3x32 mixed-precision distillation, full + domain solves",
         dims=(16, 16, 16, 32), eps=0.5, kappa=0.125, csw=1.6, n_ev=32, t_src=list(range(32)),
         extents=[4] * 8, sweep={}, gauge_seed=2001, cv_seed=2002,
-        sources="lowest Laplacian eigenvectors (GPU eigensolver)", rhs_block=64, solver_sample_rhs=64),
+        sources="lowest Laplacian eigenvectors (GPU eigensolver)", rhs_block=64, pipeline=1,
+        solver_sample_rhs=64),
     "uneven": dict(
         title="24^3x48 batched uneven domains 6/8/10/6/8/10",
         dims=(24, 24, 24, 48), eps=0.5, kappa=0.125, csw=1.6, n_ev=64, t_src=list(range(48)),
         extents=[6, 8, 10, 6, 8, 10], sweep={}, gauge_seed=3001, cv_seed=3002,
-        sources="seeded orthonormal colour vectors (Cholesky-QR twice)", rhs_block=64, solver_sample_rhs=16),
+        sources="seeded orthonormal colour vectors (Cholesky-QR twice)", rhs_block=64, pipeline=1,
+        solver_sample_rhs=16),
 }
 GAMMAS = [5, 0]
 
@@ -70,6 +73,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
     ap.add_argument("--rhs-block", type=int, default=0, help="override the workload's RHS block")
+    ap.add_argument("--pipeline", type=int, default=0, help="override the workload's batches in flight (1 or 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps and e2e (no solver comparison, sweep or roofline)")
@@ -217,7 +221,7 @@ def cpu_baseline(wl, budget_s=20.0, setup=None):
 class Workload:
     """Inputs, context, buffers and the step of one workload on this rank's GPU."""
 
-    def __init__(self, name, rhs_block=0, rank=0, world=1):
+    def __init__(self, name, rhs_block=0, rank=0, world=1, pipeline=0):
         import torch
         from lqcd_inputs import colour_vectors, gauge_field
         from paper_2609_37049_b300 import Context, lqcd
@@ -230,6 +234,7 @@ class Workload:
         self.L3 = self.dims[0] * self.dims[1] * self.dims[2]
         self.n_ev = wl["n_ev"]
         self.rhs_block = rhs_block or wl["rhs_block"]
+        self.pipeline = pipeline or wl["pipeline"]
         self.nj = self.rhs_block // 4
         assert self.rhs_block % 4 == 0 and self.n_ev % self.nj == 0
         self.n_blocks = self.n_ev // self.nj
@@ -283,9 +288,10 @@ class Workload:
         from paper_2609_37049_b300 import autotune, default_params
         lq = self.lqcd
         self.tuning = autotune.tune(self.ctx, cache=os.path.join(tempfile.gettempdir(), "lqcd_tuning.json"),
-                                    precisions=(lq.LQCD_PREC_F32, lq.LQCD_PREC_F64), blocks=(self.rhs_block,))
+                                    precisions=(lq.LQCD_PREC_F32, lq.LQCD_PREC_F64),
+                                    blocks=(self.rhs_block // self.pipeline,))
         self.params = default_params(solver=lq.LQCD_SOLVER_MIXED, inner_prec=lq.LQCD_PREC_F32,
-                                     rhs_block=self.rhs_block)
+                                     rhs_block=self.rhs_block // self.pipeline, pipeline=self.pipeline)
 
     def unit(self, step):
         from paper_2609_37049_b300.shard import plan_unit
@@ -380,7 +386,7 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     peak, peak_kind = peaks()
-    W = Workload(args.workload, args.rhs_block, rank, world)
+    W = Workload(args.workload, args.rhs_block, rank, world, args.pipeline)
     W.tune()
     if args.profile_step:  # one warm step, then one step inside an NVTX range for an ncu launch list
         W.step(0)
@@ -422,7 +428,7 @@ def run_ours(args, rank, world):
            "config": {"workload": W.wl["title"], "lattice": "x".join(map(str, W.dims)), "eps": W.wl["eps"],
                       "kappa": W.wl["kappa"], "c_sw": W.wl["csw"], "n_ev": W.n_ev, "t_src": W.t_src,
                       "domains": "%d x %s" % (len(W.wl["extents"]), sorted(set(W.wl["extents"]))),
-                      "rhs_block": W.rhs_block, "sources": W.wl["sources"],
+                      "rhs_block": W.rhs_block, "batches_in_flight": W.pipeline, "sources": W.wl["sources"],
                       "step": "one RHS block: full-operator columns at one source timeslice + domain-operator "
                               "columns of one source group (multi-site solve)",
                       "l2": "inputs larger than L2 (126 MB): each FP64 full-lattice batch vector is %.1f GB"
@@ -527,17 +533,18 @@ def extras(W, peak, peak_kind, dev):
         out["domain_sweep"] = sweep
     # dslash rooflines of the dominant kernel (FP32 hopping + inverse clover at the RHS block)
     dsl = {}
-    n64 = min(W.rhs_block, 4 if np.prod(W.dims) > 24 ** 3 * 48 else W.rhs_block)
-    for name, prec, nr in (("f32", lqcd.LQCD_PREC_F32, W.rhs_block), ("f64", lqcd.LQCD_PREC_F64, n64)):
+    nbat = W.rhs_block // W.pipeline  # right-hand sides of one launch
+    n64 = min(nbat, 4 if np.prod(W.dims) > 24 ** 3 * 48 else nbat)
+    for name, prec, nr in (("f32", lqcd.LQCD_PREC_F32, nbat), ("f64", lqcd.LQCD_PREC_F64, n64)):
         ms_l, by = ctx.dslash_bench(prec, nr, 10, True)
         dsl[name] = {"ms": ms_l, "GBs": by / ms_l / 1e6, "bytes": by, "nrhs": nr}
     achieved = dsl["f32"]["GBs"]
-    v32 = int(W.tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(W.rhs_block), 0))
+    v32 = int(W.tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(nbat), 0))
     kname = {3: "dslash_sl_kernel", 4: "dslash_pipe_kernel"}.get(v32, "dslash_kernel")
     out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "traffic": None, "peak_kind": peak_kind,
                        "kernel": "%s<P32,EPI_CH> (launch variant %d: eo hopping + A^-1, %d RHS)" % (kname, v32,
-                                                                                                  W.rhs_block),
+                                                                                                  nbat),
                        "algo_bytes_per_launch": dsl["f32"]["bytes"]}
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     f64_flops = 1824.0 * (np.prod(W.dims) // 2) * n64

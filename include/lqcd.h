@@ -66,7 +66,11 @@ enum { LQCD_SINKS_DIAG = 0, LQCD_SINKS_ALL = 1, LQCD_SINKS_DIAG_SRCV = 2 };
  *                           by FP16-storage BiCGStab sweeps (inner_prec = LQCD_PREC_F16);
  *   LQCD_SOLVER_FGCR_NN:    FP64 defect correction around FP32 flexible GCR preconditioned by the
  *                           loaded gauge-covariant network (lqcd_nn_load); falls back to MIXED
- *                           when no network is loaded or it fails to reduce the residual. */
+ *                           when no network is loaded or it fails to reduce the residual.
+ * With use_graph = 1 a batch's whole solve (defect-correction cycles and inner iterations) is one
+ * CUDA graph whose loops run on the device (conditional WHILE nodes): no host round trip until the
+ * batch ends.  Where the driver refuses such a graph, the library drives the cycles from the host,
+ * replaying captured chunks of check_every inner iterations. */
 enum {
   LQCD_SOLVER_BICGSTAB64 = 0,
   LQCD_SOLVER_MIXED = 1,
@@ -87,6 +91,10 @@ typedef struct {
   int gcr_nkrylov;   /* flexible GCR restart length; 0 -> 8 */
   int precond_iters; /* FP16 MR preconditioner sweeps per application; 0 -> 6; < 0: no preconditioner
                         (plain FP32 GCR inside the defect correction, for comparisons) */
+  int pipeline;      /* right-hand-side batches in flight at once: 1 or 2; 0 -> 1.  With 2, a call
+                        of several batches keeps two sets of work vectors (twice the solver memory)
+                        on two streams, so one batch's FP64 true residual runs beside the next
+                        batch's FP32 iterations; results are the same as with 1 */
 } lqcd_solve_params;
 
 typedef struct {
@@ -101,6 +109,8 @@ typedef struct {
   double max_true_resid;    /* largest final true relative residual */
   double seconds;           /* wall time of the call */
   int fallback;             /* 1 if FGCR_NN fell back to MIXED */
+  int device_loops;         /* batches that ran as one graph with device-side loops (the rest were
+                               driven from the host) */
 } lqcd_solve_stats;
 
 /* Fill *p with the defaults (tol 1e-10, BiCGStab64, graphs on). */
@@ -345,7 +355,7 @@ int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, 
  * of that precision and RHS count uses it.  Variants 0 / 1 / 2: direct loads with register caps
  * of 128 / 80 / 64 per thread (4 / 6 / 8 resident 128-thread blocks per SM); 3: links rebuilt and
  * clover copied once per site into shared memory, 32-bit indexing, register cap 80 (FP32 and
- * FP16, nrhs a power of two in [16, 128]); 4: the neighbour spinors staged in shared memory by
+ * FP16, nrhs a power of two in [8, 128]); 4: the neighbour spinors staged in shared memory by
  * bulk asynchronous copies 3 hops ahead (FP32 and FP16, nrhs a multiple of 32).  Where a variant does
  * not apply it runs as variant 0.  FP64 has variants 0 / 1 / 2 with register caps 128 / 255 / 168.  All variants compute the same arithmetic in the
  * same order.  lqcd_set_dslash_variant

@@ -52,12 +52,10 @@ void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes) {
   if (it != c->ws.end() && it->second.second >= bytes) return it->second.first;
   if (it != c->ws.end()) {
     cudaStreamSynchronize(c->work);
+    if (c->slot_stream) cudaStreamSynchronize(c->slot_stream);
     cudaFree(it->second.first);
     c->ws.erase(it);
-    // graphs captured on the old buffer are stale
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
-    c->graph_kernels.clear();
+    drop_graphs(c);  // graphs captured on the old buffer are stale
   }
   void* p = nullptr;
   if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
@@ -66,6 +64,16 @@ void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes) {
   }
   c->ws[name] = {p, bytes < 256 ? 256 : bytes};
   return p;
+}
+
+void drop_graphs(lqcd_ctx* c) {
+  if (c->work) cudaStreamSynchronize(c->work);
+  if (c->slot_stream) cudaStreamSynchronize(c->slot_stream);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  c->graph_kernels.clear();
+  for (auto& kv : c->loop_graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->loop_graphs.clear();
 }
 
 void* pinned_get(lqcd_ctx* c, size_t bytes) {
@@ -156,6 +164,21 @@ struct Scope {
   }
 };
 
+// Work-vector slots of a call: slot 1's stream starts after the work stream's queued work, and
+// the work stream (hence the caller's stream) waits for slot 1 at the end of the call.
+int n_slots(lqcd_ctx* c, const lqcd_solve_params& q, int n_batches) {
+  if (q.pipeline < 2 || n_batches < 2 || q.solver == LQCD_SOLVER_FGCR_NN) return 1;
+  cudaStream_t s1 = slot_stream(c, 1);
+  cudaEventRecord(c->ev_slot, c->work);
+  cudaStreamWaitEvent(s1, c->ev_slot, 0);
+  return 2;
+}
+void join_slots(lqcd_ctx* c, int nslots) {
+  if (nslots < 2) return;
+  cudaEventRecord(c->ev_slot, c->slot_stream);
+  cudaStreamWaitEvent(c->work, c->ev_slot, 0);
+}
+
 int cuda_check(lqcd_ctx* c, const char* where) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(c, LQCD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
@@ -243,6 +266,7 @@ void add_stats(lqcd_solve_stats* st, const BatchStats& bs, int rhs0, int nb, int
   if (bs.cycles > st->outer_cycles) st->outer_cycles = bs.cycles;
   st->dslash_calls += bs.dslash;
   st->fallback |= bs.fallback;
+  st->device_loops += bs.device_loops;
   for (int r = 0; r < nb; r++) {
     int it = 0;
     for (int s = 0; s < nseg; s++) {
@@ -271,6 +295,7 @@ void reset_stats(lqcd_solve_stats* st) {
   st->max_true_resid = 0;
   st->seconds = 0;
   st->fallback = 0;
+  st->device_loops = 0;
 }
 
 __global__ void k_scatter_tau(const double2* C, int nsinks, int n_ev, int nrhs, int rhs0, const int* kt_of_z,
@@ -310,6 +335,7 @@ void lqcd_default_params(lqcd_solve_params* p) {
   p->check_every = 8;
   p->gcr_nkrylov = 8;
   p->precond_iters = 6;
+  p->pipeline = 1;
 }
 
 int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
@@ -414,8 +440,13 @@ int lqcd_destroy(lqcd_ctx* c) {
   if (!c) return LQCD_OK;
   if (c->work) cudaStreamSynchronize(c->work);
   flush_phase_times(c);
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  drop_graphs(c);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
+  for (void* p : c->slot_pinned)
+    if (p) cudaFreeHost(p);
+  if (c->slot_stream) cudaStreamDestroy(c->slot_stream);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev_slot) cudaEventDestroy(c->ev_slot);
   void* bufs[] = {c->U64, c->U32, c->U16, c->Usm, c->A64, c->Ainv64, c->Ainv32, c->Ainv16, c->A32,
                   c->d_tc_full, c->d_tc_dom, c->d_seg_full, c->d_seg_dom, c->d_gamma, c->d_coord,
                   c->nn_weights, c->nn_w16, c->nn_m, c->nn_v};
@@ -455,12 +486,7 @@ int lqcd_gauge_upload(lqcd_ctx* c, const double* links, int where, double kappa,
     cudaGetLastError();
     return set_error(c, LQCD_ERR_OOM, "gauge_upload: out of device memory");
   }
-  if (kappa != c->kappa) {  // captured Schur launches hold -kappa^2 by value: recapture them
-    cudaStreamSynchronize(c->work);
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
-    c->graph_kernels.clear();
-  }
+  if (kappa != c->kappa) drop_graphs(c);  // captured Schur launches hold -kappa^2 by value: recapture them
   c->have_gauge = false;
   c->kappa = kappa;
   c->csw = c_sw;
@@ -573,19 +599,42 @@ static int solve_common(lqcd_ctx* c, const double* b, double* x, int nrhs, int w
   const int blk = q.rhs_block > 0 ? q.rhs_block : default_block(nrhs);
   int rc = LQCD_OK;
   const int nseg = domain ? c->seg_dom.nseg : 1;
-  for (int r0 = 0; r0 < nrhs; r0 += blk) {
-    int nb = nrhs - r0 < blk ? nrhs - r0 : blk;
-    double2* eb = (double2*)ws_get(c, "eo_b", per * nb);
-    double2* ex = (double2*)ws_get(c, "eo_x", per * nb);
-    if (!eb || !ex) return set_error(c, LQCD_ERR_OOM, "solve: out of device memory");
-    pack_spinor(c->g, db + (size_t)r0 * c->V * 12, eb, nb, c->work);
+  const int nbatch = (nrhs + blk - 1) / blk;
+  const int nsl = n_slots(c, q, nbatch);
+  struct Pending {
+    BatchHandle h;
+    int r0 = -1, nb = 0;
+    double2* ex = nullptr;
+  } pend[2];
+  // finish the batch of a slot: stats, and its solution unpacked on the slot's stream
+  auto finish = [&](Pending& pd) -> int {
+    if (pd.r0 < 0) return LQCD_OK;
     BatchStats bs;
-    int r = solve_batch(c, eb, ex, nb, domain, q, bs);
+    int r = solve_batch_finish(c, pd.h, bs);
     if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED && r != LQCD_ERR_NAN) return r;
     rc = worse(rc, r);
-    add_stats(st, bs, r0, nb, nseg);
-    unpack_spinor(c->g, ex, dx + (size_t)r0 * c->V * 12, nb, c->work);
+    add_stats(st, bs, pd.r0, pd.nb, nseg);
+    pd.r0 = -1;
+    return LQCD_OK;
+  };
+  for (int k = 0; k < nbatch; k++) {
+    const int s = k % nsl, r0 = k * blk;
+    const int nb = nrhs - r0 < blk ? nrhs - r0 : blk;
+    if (int e = finish(pend[s])) return e;
+    cudaStream_t ss = slot_stream(c, s);
+    double2* eb = (double2*)ws_get(c, s ? "eo_b#1" : "eo_b", per * nb);
+    double2* ex = (double2*)ws_get(c, s ? "eo_x#1" : "eo_x", per * nb);
+    if (!eb || !ex) return set_error(c, LQCD_ERR_OOM, "solve: out of device memory");
+    pack_spinor(c->g, db + (size_t)r0 * c->V * 12, eb, nb, ss);
+    if (int e = solve_batch_enqueue(c, s, eb, ex, nb, domain, q, pend[s].h)) return e;
+    unpack_spinor(c->g, ex, dx + (size_t)r0 * c->V * 12, nb, ss);
+    pend[s].r0 = r0;
+    pend[s].nb = nb;
+    pend[s].ex = ex;
   }
+  for (int s = 0; s < nsl; s++)
+    if (int e = finish(pend[s])) return e;
+  join_slots(c, nsl);
   if (int e = cuda_check(c, "solve")) return e;
   int fo = finish_out(c, x, dx, per * nrhs, where);
   if (fo) return fo;
@@ -669,16 +718,41 @@ static int perambulator_impl(lqcd_ctx* c, const double* Vt, int n_ev, const int*
   const int nrhs_total = rhs_end - rhs_begin;
   const int blk = q.rhs_block > 0 ? q.rhs_block : default_block(nrhs_total);
   const size_t per = (size_t)c->V * 12 * sizeof(double2);
-  int* d_jb = (int*)ws_get(c, "p_jb", 2 * blk * sizeof(int));
-  unsigned char* d_mask = (unsigned char*)ws_get(c, "p_mask", LQCD_MAXT);
-  int* d_z = (int*)ws_get(c, "p_z", 3 * LQCD_MAXT * sizeof(int));  // sink t', source slot k, V slot of t
-  double2* eb = (double2*)ws_get(c, "eo_b", per * blk);
-  double2* ex = (double2*)ws_get(c, "eo_x", per * blk);
-  double2* C = (double2*)ws_get(c, "p_C", (size_t)g.Lt * n_ev * 4 * blk * sizeof(double2));
-  if (!d_jb || !d_mask || !d_z || !eb || !ex || !C) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
+  const int nseg = domain ? c->seg_dom.nseg : 1;
+  const int nbatch = (int)groups.size() * ((nrhs_total + blk - 1) / blk);
+  const int nsl = n_slots(c, q, nbatch);
+  // per-slot buffers: sources, solutions, tables, projection scratch
+  struct Slot {
+    int* jb;
+    unsigned char* mask;
+    int* z;
+    double2 *eb, *ex, *C;
+    BatchHandle h;
+    bool busy = false;
+  } sl[2];
+  for (int s = 0; s < nsl; s++) {
+    const std::string sfx = s ? "#1" : "";
+    sl[s].jb = (int*)ws_get(c, "p_jb" + sfx, 2 * blk * sizeof(int));
+    sl[s].mask = (unsigned char*)ws_get(c, "p_mask" + sfx, LQCD_MAXT);
+    sl[s].z = (int*)ws_get(c, "p_z" + sfx, 3 * LQCD_MAXT * sizeof(int));  // sink t', source slot k, V slot of t
+    sl[s].eb = (double2*)ws_get(c, "eo_b" + sfx, per * blk);
+    sl[s].ex = (double2*)ws_get(c, "eo_x" + sfx, per * blk);
+    sl[s].C = (double2*)ws_get(c, "p_C" + sfx, (size_t)g.Lt * n_ev * 4 * blk * sizeof(double2));
+    if (!sl[s].jb || !sl[s].mask || !sl[s].z || !sl[s].eb || !sl[s].ex || !sl[s].C)
+      return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
+  }
   int rc = LQCD_OK;
-  int nseg = domain ? c->seg_dom.nseg : 1;
-  std::vector<int> hjb(2 * blk);
+  auto finish = [&](Slot& S) -> int {
+    if (!S.busy) return LQCD_OK;
+    BatchStats bs;
+    int r = solve_batch_finish(c, S.h, bs);
+    S.busy = false;
+    if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED && r != LQCD_ERR_NAN) return r;
+    rc = worse(rc, r);
+    add_stats(st, bs, 0, (int)bs.iters.size() / nseg, nseg, false);
+    return LQCD_OK;
+  };
+  int kb = 0;
   for (auto& grp : groups) {
     unsigned char mask[LQCD_MAXT];
     memset(mask, 0, sizeof mask);
@@ -702,38 +776,37 @@ static int perambulator_impl(lqcd_ctx* c, const double* Vt, int n_ev, const int*
       hz[LQCD_MAXT + z] = kz[z];
     }
     for (int t = 0; t < LQCD_MAXT; t++) hz[2 * LQCD_MAXT + t] = vslot[t];
-    cudaStreamSynchronize(c->work);
-    cudaMemcpyAsync(d_mask, mask, LQCD_MAXT, cudaMemcpyHostToDevice, c->work);
-    cudaMemcpyAsync(d_z, hz.data(), 3 * LQCD_MAXT * sizeof(int), cudaMemcpyHostToDevice, c->work);
-    for (int r0 = rhs_begin; r0 < rhs_end; r0 += blk) {
-      int nb = rhs_end - r0 < blk ? rhs_end - r0 : blk;
+    for (int r0 = rhs_begin; r0 < rhs_end; r0 += blk, kb++) {
+      const int s = kb % nsl;
+      Slot& S = sl[s];
+      if (int e = finish(S)) return e;  // the slot's previous batch (its queued work is ordered anyway)
+      cudaStream_t ss = slot_stream(c, s);
+      const int nb = rhs_end - r0 < blk ? rhs_end - r0 : blk;
+      std::vector<int> hjb(2 * blk);
       for (int r = 0; r < nb; r++) {
         hjb[r] = (r0 + r) / 4;
         hjb[blk + r] = (r0 + r) % 4;
       }
-      cudaMemcpyAsync(d_jb, hjb.data(), 2 * blk * sizeof(int), cudaMemcpyHostToDevice, c->work);
-      {
-        PhaseTimer pt(c, "sources");
-        make_sources(g, dV, n_ev, d_jb, d_jb + blk, d_mask, d_z + 2 * LQCD_MAXT, eb, nb, c->work);
-      }
-      BatchStats bs;
-      int r = solve_batch(c, eb, ex, nb, domain, q, bs);
-      if (r != LQCD_OK && r != LQCD_ERR_NOT_CONVERGED && r != LQCD_ERR_NAN) return r;
-      rc = worse(rc, r);
-      add_stats(st, bs, 0, nb, nseg, false);
-      {
-        const int ks = project_ksplit(g, n_ev, nb, nz);
-        double2* Cp = (double2*)ws_get(c, "p_Cpart", (size_t)ks * nz * n_ev * 4 * nb * sizeof(double2));
-        if (!Cp) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
-        lqcd::PhaseTimer pt(c, "project");
-        project(g, dV, n_ev, ex, d_z, d_z + 2 * LQCD_MAXT, nz, C, Cp, nb, c->work);
-      }
+      // pageable sources: the copies complete (staged) before these calls return
+      cudaMemcpyAsync(S.mask, mask, LQCD_MAXT, cudaMemcpyHostToDevice, ss);
+      cudaMemcpyAsync(S.z, hz.data(), 3 * LQCD_MAXT * sizeof(int), cudaMemcpyHostToDevice, ss);
+      cudaMemcpyAsync(S.jb, hjb.data(), 2 * blk * sizeof(int), cudaMemcpyHostToDevice, ss);
+      make_sources(g, dV, n_ev, S.jb, S.jb + blk, S.mask, S.z + 2 * LQCD_MAXT, S.eb, nb, ss);
+      if (int e = solve_batch_enqueue(c, s, S.eb, S.ex, nb, domain, q, S.h)) return e;
+      S.busy = true;
+      const int ks = project_ksplit(g, n_ev, nb, nz);
+      double2* Cp = (double2*)ws_get(c, s ? "p_Cpart#1" : "p_Cpart", (size_t)ks * nz * n_ev * 4 * nb * sizeof(double2));
+      if (!Cp) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
+      project(g, dV, n_ev, S.ex, S.z, S.z + 2 * LQCD_MAXT, nz, S.C, Cp, nb, ss);
       long n = (long)nz * n_ev * 4 * nb;
-      k_scatter_tau<<<(n + 255) / 256, 256, 0, c->work>>>(C, nz, n_ev, nb, r0, d_z + LQCD_MAXT, d_z,
-                                                          sinks == LQCD_SINKS_ALL, g.Lt, dtau); lqcd::count_launch();
+      k_scatter_tau<<<(n + 255) / 256, 256, 0, ss>>>(S.C, nz, n_ev, nb, r0, S.z + LQCD_MAXT, S.z,
+                                                     sinks == LQCD_SINKS_ALL, g.Lt, dtau); lqcd::count_launch();
       if (int e = cuda_check(c, "perambulator")) return e;
     }
   }
+  for (int s = 0; s < nsl; s++)
+    if (int e = finish(sl[s])) return e;
+  join_slots(c, nsl);
   int fo = finish_out(c, tau, dtau, tau_bytes, where);
   if (fo) return fo;
   cudaStreamSynchronize(c->work);

@@ -429,6 +429,38 @@ __global__ void k_count_active(const int* active, int n, int* count) {
   if (threadIdx.x == 0) count[0] = sm[0];
 }
 
+// Condition of a device-side solver loop (a WHILE node of a CUDA graph): counts the active systems
+// and sets the node's condition.  ctr: [0] inner iterations summed over cycles, [1] defect-correction
+// cycles, [2] inner chunks run.  mode 0: before the cycles (any active); 1: end of a cycle
+// (ctr[1]++; any active and ctr[1] < max_outer and ctr[0] < max_iter); 2: before an inner loop (any
+// active and ctr[0] < max_iter); 3: end of an inner chunk (ctr[0] += chunk, ctr[2]++; same test).
+__global__ void k_loop_cond(const int* active, int n, int* ctr, int mode, int chunk, int max_outer, int max_iter,
+                            cudaGraphConditionalHandle h) {
+  __shared__ int sm[256];
+  int s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += active[i] ? 1 : 0;
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k >= 1; k >>= 1) {
+    if (threadIdx.x < k) sm[threadIdx.x] += sm[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x) return;
+  const int any = sm[0] > 0;
+  unsigned go = any;
+  if (mode == 1) {
+    ctr[1] += 1;
+    go = any && ctr[1] < max_outer && ctr[0] < max_iter;
+  } else if (mode == 2) {
+    go = any && ctr[0] < max_iter;
+  } else if (mode == 3) {
+    ctr[0] += chunk;
+    ctr[2] += 1;
+    go = any && ctr[0] < max_iter;
+  }
+  cudaGraphSetConditional(h, go);
+}
+
 // outer-loop bookkeeping: r2 -> active, inner delta and scale per system
 __global__ void k_outer_update(const double* r2, const double* b2, int nsys, double tol, double inner_tol,
                                int* active, double* delta, double* scale, double* rel, int first) {
@@ -544,6 +576,12 @@ void outer_update(const double* r2, const double* b2, int nsys, double tol, doub
                   double* delta, double* scale, double* rel, int first, cudaStream_t st) {
   k_outer_update<<<(nsys + 127) / 128, 128, 0, st>>>(r2, b2, nsys, tol, inner_tol, active, delta, scale, rel,
                                                      first); lqcd::count_launch();
+}
+
+void loop_cond(const int* active, int n, int* ctr, int mode, int chunk, int max_outer, int max_iter,
+               cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_loop_cond<<<1, 256, 0, st>>>(active, n, ctr, mode, chunk, max_outer, max_iter, h);
+  lqcd::count_launch();
 }
 
 void recip(const double* a, double* b, int n, cudaStream_t st) {

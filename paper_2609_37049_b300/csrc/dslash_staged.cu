@@ -274,10 +274,10 @@ LQCD_D void hop_dir_sl(const DslashParams& pr, int s, int cmu, int Lmu, int smu,
   }
 }
 
-constexpr int kMaxSites = 8;  // sites per 128-thread block: nrhs >= 16
+constexpr int kMaxSites = 16;  // sites per 128-thread block: nrhs >= 8
 
 // Blocks of 128 threads = S = 128 / nrhs sites x nrhs right-hand sides (nrhs a power of two in
-// [16, 128]); block b holds sites b S .. b S + S - 1.
+// [8, 128]); block b holds sites b S .. b S + S - 1.
 template <int P, int EPI, int RED, int MINB>
 __global__ void __launch_bounds__(128, MINB) dslash_sl_kernel(const DslashParams pr) {
   __shared__ float4 slink[kMaxSites][8][5];  // [site][hop: 2 mu (fwd), 2 mu + 1 (bwd)][link]
@@ -465,7 +465,7 @@ bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, i
     return launch_p<P16>(pr, epi, red, blocks, tpb, red_shm, 3, st);
   }
   // staged links and clover: 128-thread blocks of 128 / nrhs whole sites, 32-bit indices
-  if (nr < 16 || nr > 128 || (nr & (nr - 1)) != 0 || tpb != 128) return false;
+  if (nr < 8 || nr > 128 || (nr & (nr - 1)) != 0 || tpb != 128) return false;
   if (pr.g.Vh % (128 / nr) != 0 || blocks * (128 / nr) != pr.g.Vh) return false;
   if (12 * pr.g.Vh * nr >= (1L << 31)) return false;
   if (prec == P32) return launch_sl_e<P32, 6>(pr, epi, red, blocks, red_shm, st);

@@ -92,4 +92,7 @@ int nn_train(lqcd_ctx* c, int n_pairs, int epochs, int batch, double lr, int dom
 void outer_update(const double* r2, const double* b2, int nsys, double tol, double inner_tol, int* active,
                   double* delta, double* scale, double* rel, int first, cudaStream_t st);
 void recip(const double* a, double* b, int n, cudaStream_t st);
+// Device-side loop condition of a CUDA-graph WHILE node (see k_loop_cond in blas.cu).
+void loop_cond(const int* active, int n, int* ctr, int mode, int chunk, int max_outer, int max_iter,
+               cudaGraphConditionalHandle h, cudaStream_t st);
 }  // namespace lqcd

@@ -1,5 +1,7 @@
 // Host launchers of the layout and distillation kernels (distill.cu) and the solver driver.
 #pragma once
+#include <memory>
+
 #include "lqcd_internal.h"
 
 namespace lqcd {
@@ -37,12 +39,26 @@ struct BatchStats {
   int cycles = 0;
   long long dslash = 0;
   int fallback = 0;
+  int device_loops = 0;  // 1 if the batch ran as one graph with device-side loops
 };
 
 // Solve D x = b (domain = 0) or D_Lambda x = b (domain = 1) for nrhs right-hand sides held in
-// the full even-odd FP64 layout on the device.  Returns LQCD_OK or LQCD_ERR_NOT_CONVERGED.
+// the full even-odd FP64 layout on the device.  Returns LQCD_OK, LQCD_ERR_NOT_CONVERGED or
+// LQCD_ERR_NAN (a non-finite residual), with bs filled in every case.
 int solve_batch(lqcd_ctx* c, const double2* b, double2* x, int nrhs, int domain, const lqcd_solve_params& p,
                 BatchStats& bs);
+// The same in two steps, so two batches can be in flight: enqueue on the stream of work-vector
+// slot `slot` (0: the context's work stream, 1: its second stream) -- one graph launch with
+// device-side loops where the driver supports it, else the host-driven loop, which returns when
+// the batch is done -- and finish (wait for the batch, decode its residuals and iterations).
+struct BatchHandle {
+  std::shared_ptr<void> batch;
+};
+int solve_batch_enqueue(lqcd_ctx* c, int slot, const double2* b, double2* x, int nrhs, int domain,
+                        const lqcd_solve_params& p, BatchHandle& h);
+int solve_batch_finish(lqcd_ctx* c, BatchHandle& h, BatchStats& bs);
+// The stream of work-vector slot `slot` (created on first use).
+cudaStream_t slot_stream(lqcd_ctx* c, int slot);
 // Lowest n_ev eigenpairs of the covariant 3D Laplacian on every timeslice (laplace.cu);
 // Vout [Lt][n_ev][L3][3] and lam_out [Lt][n_ev] are device pointers.
 int laplace_eigs(lqcd_ctx* c, int n_ev, double2* Vout, double* lam_out_dev, double tol, int max_iter,

@@ -152,6 +152,21 @@ struct lqcd_ctx {
   // instantiated CUDA graphs of Krylov iteration chunks, keyed by buffers and shape
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<cudaGraphExec_t, long long> graph_kernels;  // kernel nodes per instantiated graph
+  // whole solves captured with device-side loops (conditional WHILE nodes), keyed like `graphs`:
+  // the executable and its kernel nodes outside the loops, per cycle and per inner chunk
+  struct LoopGraph {
+    cudaGraphExec_t exec;
+    long long nk_init, nk_cycle, nk_chunk;
+  };
+  std::map<std::string, LoopGraph> loop_graphs;
+  bool loop_graphs_unavailable = false;  // set when the driver refused a conditional graph
+  // a second right-hand-side batch in flight (pipelined perambulators): slot 1's stream (slot 0
+  // is `work`), an event to order it, and per-slot pinned buffers for the batch read-back
+  cudaStream_t slot_stream = 0;
+  cudaStream_t cap_stream = 0;  // capture of the loop bodies
+  cudaEvent_t ev_slot = 0;
+  void* slot_pinned[2] = {nullptr, nullptr};
+  size_t slot_pinned_bytes[2] = {0, 0};
   // Clifford table on the device: [16][2][4][4] complex (Gamma, Gamma-tilde)
   double2* d_gamma = nullptr;
   // packed site coordinates x | y << 8 | z << 16 | t << 24 per parity: [2][Vh]
@@ -200,6 +215,8 @@ namespace lqcd {
 void count_launch(long long n = 1);
 void set_capturing(bool on);
 void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes);
+// Destroy every captured solver graph (buffers or operator scalars they hold changed).
+void drop_graphs(lqcd_ctx* c);
 void* pinned_get(lqcd_ctx* c, size_t bytes);
 int set_error(lqcd_ctx* c, int code, const std::string& msg);
 // smear.cu: spatial APE smearing of the uploaded links into c->Usm; unpack to [V][3][3][3]

@@ -79,14 +79,14 @@ class lqcd_solve_params(ctypes.Structure):
                 ("inner_prec", ctypes.c_int), ("rhs_block", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("gcr_nkrylov", ctypes.c_int),
-                ("precond_iters", ctypes.c_int)]
+                ("precond_iters", ctypes.c_int), ("pipeline", ctypes.c_int)]
 
 
 class lqcd_solve_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.POINTER(ctypes.c_int)), ("true_resid", ctypes.POINTER(ctypes.c_double)),
                 ("n_seg", ctypes.c_int), ("outer_cycles", ctypes.c_int), ("total_iters", ctypes.c_longlong),
                 ("dslash_calls", ctypes.c_longlong), ("max_true_resid", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("fallback", ctypes.c_int)]
+                ("seconds", ctypes.c_double), ("fallback", ctypes.c_int), ("device_loops", ctypes.c_int)]
 
 
 class LqcdError(RuntimeError):

@@ -37,15 +37,15 @@ def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "probe.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lqcd.h"\n'
                    'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lqcd_solve_params),'
-                   ' sizeof(lqcd_solve_stats), offsetof(lqcd_solve_params, precond_iters),'
-                   ' offsetof(lqcd_solve_stats, fallback)); return 0;}\n')
+                   ' sizeof(lqcd_solve_stats), offsetof(lqcd_solve_params, pipeline),'
+                   ' offsetof(lqcd_solve_stats, device_loops)); return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     assert int(out[0]) == ctypes.sizeof(lqcd.lqcd_solve_params)
     assert int(out[1]) == ctypes.sizeof(lqcd.lqcd_solve_stats)
-    assert int(out[2]) == lqcd.lqcd_solve_params.precond_iters.offset
-    assert int(out[3]) == lqcd.lqcd_solve_stats.fallback.offset
+    assert int(out[2]) == lqcd.lqcd_solve_params.pipeline.offset
+    assert int(out[3]) == lqcd.lqcd_solve_stats.device_loops.offset
 
 
 def test_default_params():

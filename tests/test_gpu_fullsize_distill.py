@@ -207,6 +207,8 @@ def test_scale_solve_residual_at_sampled_sites(scale):
         res = np.array([br[t, z, y, x_] for (x_, y, z, t) in sites]) - Dx
         assert np.sqrt((np.abs(res) ** 2).sum(axis=(1, 2))).max() <= 1.02e-10 * np.linalg.norm(br)
         del xr, br
+    del b, x
+    torch.cuda.empty_cache()  # the library allocates its own work vectors beside torch's cache
 
 
 @pytest.mark.parametrize("mode", [lqcd.LQCD_MODE_FULL, lqcd.LQCD_MODE_DOMAIN])
@@ -231,6 +233,7 @@ def test_scale_perambulator_block(scale, mode):
                               stats=st)
         assert st.max_true_resid <= 1e-10
         taus[name] = tau.cpu().numpy()[:, :, :, :4, :]
+        del tau
     for k in range(len(t_src)):
         a, b = taus["mixed"][k], taus["plain"][k]
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-9
