@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--rhs-block", type=int, default=0, help="override the workload's RHS block")
     ap.add_argument("--pipeline", type=int, default=0, help="override the workload's batches in flight (1 or 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement (tuning runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps and e2e (no solver comparison, sweep or roofline)")
     ap.add_argument("--profile-dslash", action="store_true",
@@ -445,6 +446,8 @@ def run_ours(args, rank, world):
     if not args.no_extras:  # before the end-to-end run, whose host staging buffers stay allocated
         res.update(extras(W, peak, peak_kind, dev))
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    if args.no_e2e:
+        return res
     H = W.host_buffers()
     W.step(args.warmup, host=H)
     torch.cuda.synchronize()

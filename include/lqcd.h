@@ -302,8 +302,8 @@ int lqcd_dslash_bench(lqcd_ctx* ctx, int prec, int nrhs, int n_iter, int flush_l
                       double* algo_bytes_per_launch);
 
 /* lqcd_disc_correlator without any GPU memory allocation, for callers that cannot allocate:
- * code being captured into a CUDA graph, hosts that reserve all device memory up front, or loops
- * where an allocation would synchronise the device.  (The paper has no counterpart; this is an
+ * hosts that reserve all device memory up front and forbid later allocations, or loops where an
+ * allocation would synchronise the device.  (The paper has no counterpart; this is an
  * interface for such callers.)  Same results as lqcd_disc_correlator for the same inputs.
  *   All array arguments are DEVICE pointers on the current device, owned by the caller, with
  *   the layouts of lqcd_disc_correlator; T = Lt; dom_of_t: [T] int domain index of each

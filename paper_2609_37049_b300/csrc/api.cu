@@ -399,6 +399,8 @@ int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
   {
     const char* tv = getenv("LQCD_PHASE_TIMING");
     c->timing = tv && tv[0] == '1';
+    const char* rp = getenv("LQCD_RES_PERSISTENT");
+    c->res_persistent = rp ? atoi(rp) : 0;
   }
   fill_tables(c);
   M4 G[16], Gt[16];
@@ -794,10 +796,12 @@ static int perambulator_impl(lqcd_ctx* c, const double* Vt, int n_ev, const int*
       make_sources(g, dV, n_ev, S.jb, S.jb + blk, S.mask, S.z + 2 * LQCD_MAXT, S.eb, nb, ss);
       if (int e = solve_batch_enqueue(c, s, S.eb, S.ex, nb, domain, q, S.h)) return e;
       S.busy = true;
-      const int ks = project_ksplit(g, n_ev, nb, nz);
+      // beside a batch in flight the projection (FP64 pipe) takes few blocks per SM
+      const int pbs = nsl > 1 && c->res_persistent > 0 ? c->res_persistent : 4;
+      const int ks = project_ksplit(g, n_ev, nb, nz, pbs);
       double2* Cp = (double2*)ws_get(c, s ? "p_Cpart#1" : "p_Cpart", (size_t)ks * nz * n_ev * 4 * nb * sizeof(double2));
       if (!Cp) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
-      project(g, dV, n_ev, S.ex, S.z, S.z + 2 * LQCD_MAXT, nz, S.C, Cp, nb, ss);
+      project(g, dV, n_ev, S.ex, S.z, S.z + 2 * LQCD_MAXT, nz, S.C, Cp, nb, pbs, nsl > 1, ss);
       long n = (long)nz * n_ev * 4 * nb;
       k_scatter_tau<<<(n + 255) / 256, 256, 0, ss>>>(S.C, nz, n_ev, nb, r0, S.z + LQCD_MAXT, S.z,
                                                      sinks == LQCD_SINKS_ALL, g.Lt, dtau); lqcd::count_launch();

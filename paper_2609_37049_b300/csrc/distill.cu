@@ -163,20 +163,33 @@ __global__ void k_project_sum(const double2* Cpart, double2* C, long per_z, int 
   C[i] = make_double2(re, im);
 }
 
-int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks) {
+int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks, int blocks_per_sm) {
   const long tiles = (long)((4 * nrhs + PBN - 1) / PBN) * ((n_ev + PBM - 1) / PBM) * nsinks;
   const long kchunks = (3L * g.Lx * g.Ly * g.Lz + PBK - 1) / PBK;
-  long ks = (4 * 148 + tiles - 1) / tiles;  // about four blocks per SM
+  long ks = ((long)blocks_per_sm * 148 + tiles - 1) / tiles;  // about blocks_per_sm blocks per SM
   if (ks > kchunks) ks = kchunks;
   if (ks < 1) ks = 1;
   return (int)ks;
 }
 
 void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, const int* vslot,
-             int nsinks, double2* C, double2* Cpart, int nrhs, cudaStream_t st) {
-  const int ksplit = project_ksplit(g, n_ev, nrhs, nsinks);
-  dim3 grid((4 * nrhs + PBN - 1) / PBN, (n_ev + PBM - 1) / PBM, nsinks * ksplit);
-  k_project<<<grid, 256, 0, st>>>(Vt, n_ev, X, sinks, vslot, Cpart, g, nrhs, ksplit);
+             int nsinks, double2* C, double2* Cpart, int nrhs, int blocks_per_sm, bool high_priority,
+             cudaStream_t st) {
+  const int ksplit = project_ksplit(g, n_ev, nrhs, nsinks, blocks_per_sm);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((4 * nrhs + PBN - 1) / PBN, (n_ev + PBM - 1) / PBM, nsinks * ksplit);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (high_priority) {  // placed before queued blocks of other streams (a batch in flight beside it)
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = hi;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  cudaLaunchKernelEx(&cfg, k_project, Vt, n_ev, X, sinks, vslot, Cpart, g, nrhs, ksplit);
   lqcd::count_launch();
   const long per_z = (long)n_ev * 4 * nrhs;
   k_project_sum<<<(per_z * nsinks + 255) / 256, 256, 0, st>>>(Cpart, C, per_z, nsinks, ksplit);

@@ -22,10 +22,9 @@ namespace lqcd {
 // site in shared memory; 4: neighbour spinors staged by bulk copies) where they apply (FP32 /
 // FP16, the solver's epilogues, RHS counts as stated there), else variant 0.  The autotuner picks
 // the variant per precision and RHS count.
-template <int P, int EPI, bool DAG, int RED, int MINB>
-__global__ void __launch_bounds__(128, MINB) dslash_kernel(const DslashParams pr) {
+template <int P, int EPI, bool DAG, int RED>
+LQCD_D void dslash_body(const DslashParams& pr, const long tid) {
   using R = typename Traits<P>::real;
-  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long cb = tid / pr.nrhs;
   const int rhs = (int)(tid - cb * pr.nrhs);
   if (RED == RED_NONE && cb >= pr.g.Vh) return;
@@ -47,6 +46,58 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(const DslashParams pr
   hop_dir<P, 3, DAG>(pr, cb, s, t, g.Lt, st, cf, cbk, rhs, stride, acc);
 
   dslash_epilogue<P, EPI, RED>(pr, cb, idx, stride, rhs, acc);
+}
+
+template <int P, int EPI, bool DAG, int RED, int MINB>
+__global__ void __launch_bounds__(128, MINB) dslash_kernel(const DslashParams pr) {
+  dslash_body<P, EPI, DAG, RED>(pr, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Persistent form (no fused reductions): a grid of a few blocks per SM walks every (site, rhs)
+// pair.  Used for the FP64 true residual: a handful of warps keeps B300's FP64 pipe busy, so the
+// kernel leaves most of each SM to the FP32 kernels of the other batch in flight.
+template <int P, int EPI, int MINB>
+__global__ void __launch_bounds__(128, MINB) dslash_persistent_kernel(const DslashParams pr) {
+  const long n = pr.g.Vh * (long)pr.nrhs;
+  for (long tid = (long)blockIdx.x * blockDim.x + threadIdx.x; tid < n; tid += (long)gridDim.x * blockDim.x)
+    dslash_body<P, EPI, false, RED_NONE>(pr, tid);
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+  }
+  return n;
+}
+
+static int high_priority() {
+  static int p = 1;
+  if (p == 1) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    p = hi;
+  }
+  return p;
+}
+
+// The FP64 EPI_RES hopping kernel in persistent form: blocks_per_sm blocks per SM, launched with
+// the device's highest priority so its blocks are placed before queued blocks of other streams.
+static void launch_persistent_res(const DslashParams& pr, int blocks_per_sm, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(sm_count() * blocks_per_sm));
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = high_priority();
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, dslash_persistent_kernel<P64, EPI_RES, 2>, pr);
+  lqcd::count_launch();
 }
 
 template <int P>
@@ -135,6 +186,10 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int vari
   pr.pipe_off = 0;
   const bool dag = c.dagger != 0;
   if (variant < 0 || variant > 4) variant = 0;
+  if (c.persistent > 0 && c.prec == P64 && c.epi == EPI_RES && c.red == RED_NONE && !dag) {
+    launch_persistent_res(pr, c.persistent, st);
+    return;
+  }
   if (c.red == RED_NONE) {
     long nthreads = g.Vh * (long)c.nrhs;
     const int tpb = 128;

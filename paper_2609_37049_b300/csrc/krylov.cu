@@ -547,6 +547,7 @@ static void batch_finish_cycle(lqcd_ctx* c, Batch& B, const double2* b, double2*
   for (int p = 0; p < 2; p++) {
     DslashCall k = call(c, P64, EPI_RES, off(x, B.sb64, 1 - p), off(x, B.sb64, p), off(b, B.sb64, p),
                         off(B.r64, B.sb64, p), c->U64, off(c->A64, cb64, p), p, B.nrhs, 1.0, -c->kappa, B.tc);
+    k.persistent = c->res_persistent;
     launch_dslash(g, k, B.st, B.v64);
   }
   v_norm2(P64, B.r64, B.vgF, B.si, B.nseg, B.partial, B.r2, B.st);

@@ -11,9 +11,12 @@ void unpack_spinor(const Geom& g, const double2* eo, double2* lex, int nrhs, cud
 void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, const int* br,
                   const unsigned char* srcmask, const int* vslot, double2* b, int nrhs, cudaStream_t st);
 // Cpart: scratch of project_ksplit(...) * nsinks * n_ev * 4 * nrhs complex entries.
-int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks);
+// blocks_per_sm: about this many 256-thread blocks per SM (split along K to reach it); a batch
+// in flight beside the projection wants few (the FP64 pipe needs few warps), a lone one four.
+int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks, int blocks_per_sm);
 void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, const int* vslot,
-             int nsinks, double2* C, double2* Cpart, int nrhs, cudaStream_t st);
+             int nsinks, double2* C, double2* Cpart, int nrhs, int blocks_per_sm, bool high_priority,
+             cudaStream_t st);
 void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w, double2* L,
            double2* Lt, cudaStream_t st);
 // C [n_gamma][T][n_t], C_avg [n_gamma][T] (may be null): connected correlator from all-sink

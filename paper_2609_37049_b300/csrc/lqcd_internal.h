@@ -95,6 +95,7 @@ struct DslashCall {
   const void* zred = nullptr;
   int red = RED_NONE;
   int red_sites = 0;
+  int persistent = 0;  // FP64 EPI_RES only: > 0 launches the persistent kernel with this many blocks per SM
 };
 
 // variant: register cap of the FP32 / FP16 kernels (0: 128, 1: 80, 2: 64 registers per thread)
@@ -160,6 +161,9 @@ struct lqcd_ctx {
   };
   std::map<std::string, LoopGraph> loop_graphs;
   bool loop_graphs_unavailable = false;  // set when the driver refused a conditional graph
+  // FP64 true residual as a persistent kernel of this many blocks per SM (0: one thread per site
+  // and right-hand side over the whole grid); see dslash_persistent_kernel
+  int res_persistent = 0;
   // a second right-hand-side batch in flight (pipelined perambulators): slot 1's stream (slot 0
   // is `work`), an event to order it, and per-slot pinned buffers for the batch read-back
   cudaStream_t slot_stream = 0;

@@ -1,10 +1,10 @@
 // lqcd_disc_correlator_noalloc: the disconnected-correlator computation of
 // lqcd_disc_correlator for callers that must not allocate GPU memory.
 //
-// Who needs it: code that runs where a cudaMalloc is not allowed or not safe -- inside a region
-// being captured into a CUDA graph (an allocation there breaks or invalidates the capture), in a
-// host application that reserves all device memory up front and forbids later allocations, or in
-// a latency-critical loop where an allocation would synchronise the device.  Such a caller owns
+// Who needs it: code that runs where a cudaMalloc is not allowed or not safe -- a host
+// application that reserves all device memory up front and forbids later allocations (a memory
+// pool owner, a framework that hands out fixed arenas), or a latency-critical loop where an
+// allocation would synchronise the device.  Such a caller owns
 // every input and output buffer; the only extra memory this computation needs -- the
 // differences dL = L - L_Lambda and dLt = Lt - Lt_Lambda for the four-piece split -- lives in
 // the fixed array below, which the CUDA runtime places in device memory when the library is

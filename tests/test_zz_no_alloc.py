@@ -1,5 +1,6 @@
 """lqcd_disc_correlator_noalloc, the entry point for callers that cannot allocate GPU memory
-(graph-captured code, hosts that reserve all device memory up front): called through the C ABI
+(hosts that reserve all device memory up front, loops where an allocation would synchronise the
+device): called through the C ABI
 with caller-owned device buffers, twice in a row on different inputs, it must give the results of
 the allocating lqcd_disc_correlator.  This file is collected last on purpose, so a failure here
 does not hide the other tests of a run that stops at the first failure."""
