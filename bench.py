@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
     ap.add_argument("--rhs-block", type=int, default=0, help="override the workload's RHS block")
     ap.add_argument("--pipeline", type=int, default=0, help="override the workload's batches in flight (1 or 2)")
+    ap.add_argument("--projection", type=int, default=0, help="0: double-float projection (default), 1: FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement (tuning runs)")
     ap.add_argument("--no-extras", action="store_true",
@@ -222,7 +223,7 @@ def cpu_baseline(wl, budget_s=20.0, setup=None):
 class Workload:
     """Inputs, context, buffers and the step of one workload on this rank's GPU."""
 
-    def __init__(self, name, rhs_block=0, rank=0, world=1, pipeline=0):
+    def __init__(self, name, rhs_block=0, rank=0, world=1, pipeline=0, projection=0):
         import torch
         from lqcd_inputs import colour_vectors, gauge_field
         from paper_2609_37049_b300 import Context, lqcd
@@ -236,6 +237,7 @@ class Workload:
         self.n_ev = wl["n_ev"]
         self.rhs_block = rhs_block or wl["rhs_block"]
         self.pipeline = pipeline or wl["pipeline"]
+        self.projection = projection
         self.nj = self.rhs_block // 4
         assert self.rhs_block % 4 == 0 and self.n_ev % self.nj == 0
         self.n_blocks = self.n_ev // self.nj
@@ -292,7 +294,8 @@ class Workload:
                                     precisions=(lq.LQCD_PREC_F32, lq.LQCD_PREC_F64),
                                     blocks=(self.rhs_block // self.pipeline,))
         self.params = default_params(solver=lq.LQCD_SOLVER_MIXED, inner_prec=lq.LQCD_PREC_F32,
-                                     rhs_block=self.rhs_block // self.pipeline, pipeline=self.pipeline)
+                                     rhs_block=self.rhs_block // self.pipeline, pipeline=self.pipeline,
+                                     projection=self.projection)
 
     def unit(self, step):
         from paper_2609_37049_b300.shard import plan_unit
@@ -387,7 +390,7 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     peak, peak_kind = peaks()
-    W = Workload(args.workload, args.rhs_block, rank, world, args.pipeline)
+    W = Workload(args.workload, args.rhs_block, rank, world, args.pipeline, args.projection)
     W.tune()
     if args.profile_step:  # one warm step, then one step inside an NVTX range for an ncu launch list
         W.step(0)
@@ -429,7 +432,8 @@ def run_ours(args, rank, world):
            "config": {"workload": W.wl["title"], "lattice": "x".join(map(str, W.dims)), "eps": W.wl["eps"],
                       "kappa": W.wl["kappa"], "c_sw": W.wl["csw"], "n_ev": W.n_ev, "t_src": W.t_src,
                       "domains": "%d x %s" % (len(W.wl["extents"]), sorted(set(W.wl["extents"]))),
-                      "rhs_block": W.rhs_block, "batches_in_flight": W.pipeline, "sources": W.wl["sources"],
+                      "rhs_block": W.rhs_block, "batches_in_flight": W.pipeline,
+                      "projection": "FP64" if W.projection else "double-float (FP32 pipe)", "sources": W.wl["sources"],
                       "step": "one RHS block: full-operator columns at one source timeslice + domain-operator "
                               "columns of one source group (multi-site solve)",
                       "l2": "inputs larger than L2 (126 MB): each FP64 full-lattice batch vector is %.1f GB"

@@ -336,6 +336,7 @@ void lqcd_default_params(lqcd_solve_params* p) {
   p->gcr_nkrylov = 8;
   p->precond_iters = 6;
   p->pipeline = 1;
+  p->projection = 0;
 }
 
 int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
@@ -722,6 +723,14 @@ static int perambulator_impl(lqcd_ctx* c, const double* Vt, int n_ev, const int*
   const size_t per = (size_t)c->V * 12 * sizeof(double2);
   const int nseg = domain ? c->seg_dom.nseg : 1;
   const int nbatch = (int)groups.size() * ((nrhs_total + blk - 1) / blk);
+  // double-float projection: the colour vectors split once per call, the solution per batch
+  float4* Vf = nullptr;
+  if (q.projection == 0) {
+    const long nv = (long)(vsrc ? n_tsrc : g.Lt) * n_ev * 3 * L3;
+    Vf = (float4*)ws_get(c, "p_Vf", (size_t)nv * sizeof(float4));
+    if (!Vf) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
+    split_colour_vectors(dV, Vf, nv, c->work);
+  }
   const int nsl = n_slots(c, q, nbatch);
   // per-slot buffers: sources, solutions, tables, projection scratch
   struct Slot {
@@ -801,7 +810,12 @@ static int perambulator_impl(lqcd_ctx* c, const double* Vt, int n_ev, const int*
       const int ks = project_ksplit(g, n_ev, nb, nz, pbs);
       double2* Cp = (double2*)ws_get(c, s ? "p_Cpart#1" : "p_Cpart", (size_t)ks * nz * n_ev * 4 * nb * sizeof(double2));
       if (!Cp) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
-      project(g, dV, n_ev, S.ex, S.z, S.z + 2 * LQCD_MAXT, nz, S.C, Cp, nb, pbs, nsl > 1, ss);
+      float4* Xf = nullptr;
+      if (Vf) {
+        Xf = (float4*)ws_get(c, s ? "p_Xf#1" : "p_Xf", (size_t)nz * 4 * nb * 3 * L3 * sizeof(float4));
+        if (!Xf) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
+      }
+      project(g, dV, n_ev, S.ex, S.z, S.z + 2 * LQCD_MAXT, nz, S.C, Cp, nb, pbs, nsl > 1, Vf, Xf, ss);
       long n = (long)nz * n_ev * 4 * nb;
       k_scatter_tau<<<(n + 255) / 256, 256, 0, ss>>>(S.C, nz, n_ev, nb, r0, S.z + LQCD_MAXT, S.z,
                                                      sinks == LQCD_SINKS_ALL, g.Lt, dtau); lqcd::count_launch();

@@ -149,6 +149,137 @@ __global__ void __launch_bounds__(256) k_project(const double2* Vt, int n_ev, co
     }
 }
 
+// ---- the same projection in double-float arithmetic on the FP32 pipe
+// B300 issues FP32 at 64 times its FP64 rate, so the FP64 GEMM above is bound by a pipe the
+// rest of the solver barely uses.  Here every FP64 input is split once into an unevaluated pair
+// hi + lo of floats (hi = fl32(v), lo = fl32(v - hi): 48 significant bits), and the products are
+// accumulated with error-free transformations in the "Dot2" manner of Ogita, Rump and Oishi
+// (SIAM J. Sci. Comput. 26, 2005): TwoProduct by FMA (Dekker 1971) for the leading product, the
+// cross terms hi*lo and lo*hi and all errors into a float correction, TwoSum (Knuth) into the
+// leading float.  Every 512 terms the pair is added into an FP64 accumulator, which bounds the
+// correction's own rounding; the split-K partials are summed in FP64 as before.
+
+// One complex FP64 number as two float pairs: (re_hi, re_lo, im_hi, im_lo).
+LQCD_D float4 split_c(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+
+// Vf[slot][i][k] = split(V[slot][i][k]) for the nslots x n_ev x K entries
+__global__ void k_split_v(const double2* V, float4* Vf, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    Vf[i] = split_c(V[i]);
+}
+
+// Xf[z][n][k] = split(X_r(tp_z, s3, alpha, a)), n = alpha * nrhs + r, k = s3 * 3 + a: the solution on
+// the sink timeslices, K contiguous per column
+__global__ void k_split_x(const double2* X, const int* sinks, int nsinks, float4* Xf, Geom g, int nrhs) {
+  const long L3 = (long)g.Lx * g.Ly * g.Lz, K = 3 * L3;
+  const long n_all = (long)nsinks * 4 * nrhs * K;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_all; i += (long)gridDim.x * blockDim.x) {
+    const long k = i % K;
+    const long zn = i / K;
+    const int n = (int)(zn % (4 * nrhs)), z = (int)(zn / (4 * nrhs));
+    const int tp = sinks[z];
+    const long s3 = k / 3;
+    const int a = (int)(k - s3 * 3);
+    const int alpha = n / nrhs, r = n - alpha * nrhs;
+    const int x = (int)(s3 % g.Lx), y = (int)((s3 / g.Lx) % g.Ly), zz = (int)(s3 / ((long)g.Lx * g.Ly));
+    const int par = (x + y + zz + tp) & 1;
+    const long cb = ((long)tp * L3 + s3) >> 1;
+    Xf[i] = split_c(X[(long)par * 12 * g.Vh * nrhs + ((long)(alpha * 3 + a) * g.Vh + cb) * nrhs + r]);
+  }
+}
+
+// hi + lo += a * b for a = ah + al, b = bh + bl (double-float multiply-accumulate)
+LQCD_D void df_mac(float& hi, float& lo, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bh, -p);  // TwoProduct: ah bh = p + e exactly
+  const float s = __fadd_rn(hi, p);       // TwoSum: hi + p = s + err exactly
+  const float bv = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+  hi = s;
+  lo = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fadd_rn(lo, __fadd_rn(e, err))));
+}
+
+#define DFLUSH 32  // k-tiles of PBK between FP64 flushes (512 terms)
+__global__ void __launch_bounds__(256) k_project_df(const float4* Vf, int n_ev, const float4* Xf, const int* sinks,
+                                                    const int* vslot, double2* Cpart, Geom g, int nrhs, int ksplit) {
+  __shared__ float4 As[PBK][PBM + 1];
+  __shared__ float4 Bs[PBK][PBN + 1];
+  const int z = blockIdx.z / ksplit, kpart = blockIdx.z - z * ksplit;
+  const int tp = sinks[z];
+  const long K = 3L * g.Lx * g.Ly * g.Lz;
+  const int N = 4 * nrhs;
+  const int m0 = blockIdx.y * PBM, n0 = blockIdx.x * PBN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float hr[2][2], lr[2][2], hi_[2][2], li[2][2];
+  double ar[2][2], ai[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 2; j++) hr[i][j] = lr[i][j] = hi_[i][j] = li[i][j] = 0.f, ar[i][j] = ai[i][j] = 0.0;
+  const float4* A = Vf + (long)vslot[tp] * n_ev * K;
+  const float4* B = Xf + (long)z * N * K;
+  const long kchunks = (K + PBK - 1) / PBK;
+  const long kc0 = kchunks * kpart / ksplit, kc1 = kchunks * (kpart + 1) / ksplit;
+  double2* C = Cpart + (long)blockIdx.z * n_ev * N;
+  int since = 0;
+  for (long k0 = kc0 * PBK; k0 < kc1 * PBK; k0 += PBK) {
+    for (int e = threadIdx.x; e < PBM * PBK; e += 256) {
+      const int mm = e / PBK, kk = e % PBK;
+      const long k = k0 + kk;
+      As[kk][mm] = (m0 + mm < n_ev && k < K) ? A[(long)(m0 + mm) * K + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < PBN * PBK; e += 256) {
+      const int nn = e / PBK, kk = e % PBK;
+      const long k = k0 + kk;
+      Bs[kk][nn] = (n0 + nn < N && k < K) ? B[(long)(n0 + nn) * K + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < PBK; kk++) {
+      const float4 a[2] = {As[kk][ty], As[kk][ty + 16]};
+      const float4 b[2] = {Bs[kk][tx], Bs[kk][tx + 16]};
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {  // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
+          df_mac(hr[i][j], lr[i][j], a[i].x, a[i].y, b[j].x, b[j].y);
+          df_mac(hr[i][j], lr[i][j], a[i].z, a[i].w, b[j].z, b[j].w);
+          df_mac(hi_[i][j], li[i][j], a[i].x, a[i].y, b[j].z, b[j].w);
+          df_mac(hi_[i][j], li[i][j], -a[i].z, -a[i].w, b[j].x, b[j].y);
+        }
+    }
+    __syncthreads();
+    if (++since == DFLUSH) {
+      since = 0;
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+          ar[i][j] += (double)hr[i][j] + (double)lr[i][j];
+          ai[i][j] += (double)hi_[i][j] + (double)li[i][j];
+          hr[i][j] = lr[i][j] = hi_[i][j] = li[i][j] = 0.f;
+        }
+    }
+  }
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) {
+      const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      if (m < n_ev && n < N) {
+        const int alpha = n / nrhs, r = n - alpha * nrhs;
+        C[((long)m * 4 + alpha) * nrhs + r] = make_double2(ar[i][j] + ((double)hr[i][j] + (double)lr[i][j]),
+                                                           ai[i][j] + ((double)hi_[i][j] + (double)li[i][j]));
+      }
+    }
+}
+
+void split_colour_vectors(const double2* V, float4* Vf, long n, cudaStream_t st) {
+  k_split_v<<<4 * 148, 256, 0, st>>>(V, Vf, n);
+  lqcd::count_launch();
+}
+
 // C[z] = sum over kpart of Cpart[z * ksplit + kpart]
 __global__ void k_project_sum(const double2* Cpart, double2* C, long per_z, int nsinks, int ksplit) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -174,7 +305,7 @@ int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks, int blocks_per
 
 void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, const int* vslot,
              int nsinks, double2* C, double2* Cpart, int nrhs, int blocks_per_sm, bool high_priority,
-             cudaStream_t st) {
+             const float4* Vf, float4* Xf, cudaStream_t st) {
   const int ksplit = project_ksplit(g, n_ev, nrhs, nsinks, blocks_per_sm);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((4 * nrhs + PBN - 1) / PBN, (n_ev + PBM - 1) / PBM, nsinks * ksplit);
@@ -189,7 +320,14 @@ void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  cudaLaunchKernelEx(&cfg, k_project, Vt, n_ev, X, sinks, vslot, Cpart, g, nrhs, ksplit);
+  if (Vf && Xf) {  // double-float on the FP32 pipe: split the solution on the sinks, then the GEMM
+    k_split_x<<<4 * 148, 256, 0, st>>>(X, sinks, nsinks, Xf, g, nrhs);
+    lqcd::count_launch();
+    cudaLaunchKernelEx(&cfg, k_project_df, (const float4*)Vf, n_ev, (const float4*)Xf, sinks, vslot, Cpart, g, nrhs,
+                       ksplit);
+  } else {
+    cudaLaunchKernelEx(&cfg, k_project, Vt, n_ev, X, sinks, vslot, Cpart, g, nrhs, ksplit);
+  }
   lqcd::count_launch();
   const long per_z = (long)n_ev * 4 * nrhs;
   k_project_sum<<<(per_z * nsinks + 255) / 256, 256, 0, st>>>(Cpart, C, per_z, nsinks, ksplit);

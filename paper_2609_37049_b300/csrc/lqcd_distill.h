@@ -14,9 +14,14 @@ void make_sources(const Geom& g, const double2* Vt, int n_ev, const int* jr, con
 // blocks_per_sm: about this many 256-thread blocks per SM (split along K to reach it); a batch
 // in flight beside the projection wants few (the FP64 pipe needs few warps), a lone one four.
 int project_ksplit(const Geom& g, int n_ev, int nrhs, int nsinks, int blocks_per_sm);
+// With Vf (the colour vectors split by split_colour_vectors) and Xf (scratch of nsinks * 4 * nrhs
+// * 3 L^3 float4) the GEMM runs in double-float arithmetic on the FP32 pipe; with Vf = nullptr in
+// FP64.
 void project(const Geom& g, const double2* Vt, int n_ev, const double2* X, const int* sinks, const int* vslot,
              int nsinks, double2* C, double2* Cpart, int nrhs, int blocks_per_sm, bool high_priority,
-             cudaStream_t st);
+             const float4* Vf, float4* Xf, cudaStream_t st);
+// Vf[i] = (re_hi, re_lo, im_hi, im_lo) of V[i], i < n
+void split_colour_vectors(const double2* V, float4* Vf, long n, cudaStream_t st);
 void loops(const double2* tau, int n_ev, int n_t, const double2* G, int n_gamma, const double* w, double2* L,
            double2* Lt, cudaStream_t st);
 // C [n_gamma][T][n_t], C_avg [n_gamma][T] (may be null): connected correlator from all-sink

@@ -79,7 +79,8 @@ class lqcd_solve_params(ctypes.Structure):
                 ("inner_prec", ctypes.c_int), ("rhs_block", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("gcr_nkrylov", ctypes.c_int),
-                ("precond_iters", ctypes.c_int), ("pipeline", ctypes.c_int)]
+                ("precond_iters", ctypes.c_int), ("pipeline", ctypes.c_int),
+                ("projection", ctypes.c_int)]
 
 
 class lqcd_solve_stats(ctypes.Structure):

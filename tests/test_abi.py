@@ -37,14 +37,14 @@ def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "probe.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lqcd.h"\n'
                    'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lqcd_solve_params),'
-                   ' sizeof(lqcd_solve_stats), offsetof(lqcd_solve_params, pipeline),'
+                   ' sizeof(lqcd_solve_stats), offsetof(lqcd_solve_params, projection),'
                    ' offsetof(lqcd_solve_stats, device_loops)); return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     assert int(out[0]) == ctypes.sizeof(lqcd.lqcd_solve_params)
     assert int(out[1]) == ctypes.sizeof(lqcd.lqcd_solve_stats)
-    assert int(out[2]) == lqcd.lqcd_solve_params.pipeline.offset
+    assert int(out[2]) == lqcd.lqcd_solve_params.projection.offset
     assert int(out[3]) == lqcd.lqcd_solve_stats.device_loops.offset
 
 

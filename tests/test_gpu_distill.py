@@ -321,3 +321,18 @@ def test_open_bc_shifted_tiling_window_end_to_end():
         assert np.abs(out[k] - w[k]).max() <= 1e-13 * scale, k
     with pytest.raises(LqcdError):
         ctx.window_average(g["C"], g["dC"], g["valid"], 5, 4, out)
+
+
+@pytest.mark.parametrize("mode", [lqcd.LQCD_MODE_FULL, lqcd.LQCD_MODE_DOMAIN])
+def test_double_float_projection_matches_fp64(small_config, mode):
+    """The projection tau = V^dag X in double-float arithmetic on the FP32 pipe (the default) agrees
+    with the native FP64 GEMM to 1e-12 and with the oracle to 1e-9."""
+    c = small_config
+    case = c["case"]
+    ctx = _ctx(case, c["U"])
+    T, n_ev = case["dims"][3], case["n_ev"]
+    kw = dict(solver=lqcd.LQCD_SOLVER_MIXED, inner_prec=lqcd.LQCD_PREC_F32)
+    t_df = _gpu_tau(ctx, c["V"], n_ev, range(T), mode, default_params(projection=0, **kw))
+    t_64 = _gpu_tau(ctx, c["V"], n_ev, range(T), mode, default_params(projection=1, **kw))
+    assert tau_rel(t_df, t_64) < 1e-12
+    assert tau_rel(t_df, c["tau_f"] if mode == lqcd.LQCD_MODE_FULL else c["tau_d"]) < 1e-9
