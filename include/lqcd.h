@@ -341,13 +341,21 @@ int lqcd_nn_set_weights(lqcd_ctx* ctx, const float* w);  /* host, 2 * lqcd_nn_nu
 int lqcd_nn_get_weights(lqcd_ctx* ctx, float* w);
 /* out = network(in) with the FP32 master weights. */
 int lqcd_nn_apply(lqcd_ctx* ctx, const float* in, float* out, int nsamp, int domain, int where);
+/* out = network(in) on the inference path the FGCR preconditioner uses: the BF16 weight copy and
+ * BF16-rounded activations, channel mixing on the tensor cores (tcgen05, FP32 accumulation in
+ * tensor memory), transports on the CUDA cores in FP32.  Same layouts as lqcd_nn_apply.  Errors as
+ * lqcd_nn_apply, plus TIMEOUT (a tensor-core completion wait ran out of its iteration limit). */
+int lqcd_nn_apply_tc(lqcd_ctx* ctx, const float* in, float* out, int nsamp, int domain, int where);
 /* Loss sum |N(in) - target|^2 / sum |target|^2 over all sites (even_only = 1: even sites) and its
  * gradient dL/dconj(W) (host, 2 * lqcd_nn_num_weights() floats; may be NULL). */
 int lqcd_nn_loss_grad(lqcd_ctx* ctx, const float* in, const float* target, int nsamp, int domain, int even_only,
                       int where, double* loss, float* grad);
-/* Train on n_pairs (r, e) pairs of the even-odd Schur system M e = r generated by the plain FP64
- * solver from random r (seeded): `epochs` passes of Adam (learning rate lr) over batches of `batch`
- * pairs, loss over even sites; loss_hist[epochs] (may be NULL) receives the mean loss per epoch.
+/* Train on n_pairs (r, e) pairs of the even-odd Schur system M e = r generated from random r
+ * (seeded) by the solver without the network (FP64 defect correction around FP32 BiCGStab, true
+ * residual 1e-8): pools of pairs that fit a quarter of the free device memory are generated in
+ * turn, and each pool gets `epochs` passes of Adam (learning rate lr) over batches of `batch`
+ * pairs, loss over even sites; loss_hist[epochs] (may be NULL) receives the mean loss per epoch
+ * (averaged over the pools).
  * Starts from the weights set before (lqcd_nn_set_weights).  Afterwards LQCD_SOLVER_FGCR_NN uses
  * the network.  Errors: STATE (no weights or no gauge field), OOM. */
 int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, int domain, unsigned seed,

@@ -1080,9 +1080,25 @@ extern "C" int lqcd_nn_apply(lqcd_ctx* c, const float* in, float* out, int nsamp
   const float2* di = (const float2*)stage_in(c, in, bytes, where, "nn_in");
   float2* dout = (float2*)stage_out(c, out, bytes, where, "nn_out");
   if (!di || !dout) return set_error(c, LQCD_ERR_OOM, "nn_apply: OOM");
-  if (int rc = nn_apply_lex(c, di, dout, nsamp, domain)) return rc;
+  if (int rc = nn_apply_lex(c, di, dout, nsamp, domain, false)) return rc;
   if (int e = cuda_check(c, "nn_apply")) return e;
   return finish_out(c, out, dout, bytes, where);
+}
+
+extern "C" int lqcd_nn_apply_tc(lqcd_ctx* c, const float* in, float* out, int nsamp, int domain, int where) {
+  if (!c || !in || !out || nsamp < 1) return set_error(c, LQCD_ERR_INVALID_ARG, "nn_apply_tc: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "nn_apply_tc: no gauge field uploaded");
+  Scope sc(c);
+  const size_t bytes = (size_t)c->V * 12 * nsamp * sizeof(float2);
+  const float2* di = (const float2*)stage_in(c, in, bytes, where, "nn_in");
+  float2* dout = (float2*)stage_out(c, out, bytes, where, "nn_out");
+  if (!di || !dout) return set_error(c, LQCD_ERR_OOM, "nn_apply_tc: OOM");
+  if (int rc = nn_apply_lex(c, di, dout, nsamp, domain, true)) return rc;
+  if (int e = cuda_check(c, "nn_apply_tc")) return e;
+  if (int e = finish_out(c, out, dout, bytes, where)) return e;
+  cudaStreamSynchronize(c->work);
+  if (nn_tc_timeouts(true)) return set_error(c, LQCD_ERR_TIMEOUT, "nn_apply_tc: a tensor-core wait ran out");
+  return LQCD_OK;
 }
 
 extern "C" int lqcd_nn_loss_grad(lqcd_ctx* c, const float* in, const float* target, int nsamp, int domain,

@@ -84,7 +84,10 @@ void nn_precondition(lqcd_ctx* c, const Inner& in, const void* r, void* z, const
                      const double* ipscale, cudaStream_t st);
 int nn_set_weights(lqcd_ctx* c, const float* w_host);
 int nn_get_weights(lqcd_ctx* c, float* w_host);
-int nn_apply_lex(lqcd_ctx* c, const float2* in_dev, float2* out_dev, int N, int domain);
+// tc: the inference path (BF16 weights and activations, channel mixing on the tensor cores)
+int nn_apply_lex(lqcd_ctx* c, const float2* in_dev, float2* out_dev, int N, int domain, bool tc);
+// tensor-core layer waits that ran out of their iteration limit since the last reset
+int nn_tc_timeouts(bool reset);
 int nn_loss_grad_lex(lqcd_ctx* c, const float2* in_dev, const float2* tgt_dev, int N, int domain, int even_only,
                      double* loss, float* grad_host);
 int nn_train(lqcd_ctx* c, int n_pairs, int epochs, int batch, double lr, int domain, unsigned seed,

@@ -20,6 +20,7 @@
 
 #include "lqcd_blas.h"
 #include "lqcd_distill.h"
+#include "tc_bf16.cuh"
 
 namespace lqcd {
 
@@ -160,6 +161,214 @@ __global__ void k_nn_layer(const float2* in, float2* out, const WT* W, NNGeo G) 
   for (int o = 0; o < COUT; o++)
 #pragma unroll
     for (int a = 0; a < 3; a++) out[((long)(o * 3 + a) * V + se) * G.N + n] = make_float2(acc[o][a].re, acc[o][a].im);
+}
+
+// ------------------------------------------------------------------ tensor-core layer (inference)
+// The same layer with the channel mixing on the tensor cores (tcgen05, BF16 operands, FP32
+// accumulation in tensor memory).  The mixing is a GEMM whose rows are (site, sample, colour)
+// -- the weights do not mix colours -- with K = (re / im part, path, input channel) and N =
+// (re / im part, output channel):
+//   A[row][(0, p, c)] = Re (T_p h_c)[a],  A[row][(1, p, c)] = Im (T_p h_c)[a],
+//   B[o][(0, p, c)] = Re W[p][o][c],  B[o][(1, p, c)] = -Im W,  B[C_out + o][(0, p, c)] = Im W,
+//   B[C_out + o][(1, p, c)] = Re W,   D[row][o] = Re out_o[a],  D[row][C_out + o] = Im out_o[a].
+// A CTA of 128 threads covers 42 (site, sample) pairs x 3 colours (rows 126, 127 are zero); each
+// thread transports one colour of its pair (the three threads of a pair read the same neighbour
+// channels and link, mostly from L1) and writes its A row to shared memory in the canonical
+// K-major layout; one thread issues the K / 16 MMAs (M = 128, N = 16).
+constexpr int kNNPairs = 42;
+constexpr int kNNWaitLimit = 1 << 22;
+__device__ int g_nn_tc_timeouts;
+
+template <int CIN>
+constexpr int nn_tc_k() {
+  return (2 * NN_PATHS * CIN + 15) / 16 * 16;
+}
+
+// (T_p h_c)(x)[a] for every input channel c: one colour of the transported channels of one path.
+template <int C>
+LQCD_D bool path_colour(const NNGeo& G, const float2* h, int p, int par, long cb, int x, int y, int z, int t, int n,
+                        int a, cplx<float> (&th)[C]) {
+  const Geom& g = G.g;
+  const long V = 2 * g.Vh;
+  const long s = x + (long)g.Lx * (y + (long)g.Ly * (z + (long)g.Lz * t));
+  long sn = s;
+  int coef = 1;
+  const int mu = (p - 1) & 3;
+  const bool fwd = p >= 1 && p <= 4;
+  if (p != 0) {
+    const int cm = mu == 0 ? x : (mu == 1 ? y : (mu == 2 ? z : t));
+    const int Lm = mu == 0 ? g.Lx : (mu == 1 ? g.Ly : (mu == 2 ? g.Lz : g.Lt));
+    const long sm = mu == 0 ? 1 : (mu == 1 ? g.Lx : (mu == 2 ? (long)g.Lx * g.Ly : (long)g.Lx * g.Ly * g.Lz));
+    if (fwd) {
+      sn = s + ((cm + 1 == Lm) ? sm * (1 - Lm) : sm);
+      if (mu == 3) coef = __ldg(G.tc + t);
+    } else {
+      sn = s + ((cm == 0) ? sm * (Lm - 1) : -sm);
+      if (mu == 3) coef = __ldg(G.tc + (t == 0 ? g.Lt - 1 : t - 1));
+    }
+    if (coef == 0) return false;
+  }
+  const int npar = p == 0 ? par : 1 - par;
+  const long nse = (long)npar * g.Vh + (sn >> 1);
+  if (p == 0) {
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+      const float2 v = __ldg(h + ((long)(c * 3 + a) * V + nse) * G.N + n);
+      th[c] = {v.x, v.y};
+    }
+    return true;
+  }
+  cplx<float> u[3][3];
+  if (fwd)
+    load_link<P32>(G.U, g.Vh, mu, par, cb, u);
+  else
+    load_link<P32>(G.U, g.Vh, mu, 1 - par, sn >> 1, u);
+  const float cf = (float)coef;
+#pragma unroll
+  for (int c = 0; c < C; c++) {
+    cplx<float> acc = {0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const float2 v = __ldg(h + ((long)(c * 3 + b) * V + nse) * G.N + n);
+      const cplx<float> hv = {v.x, v.y};
+      acc = fwd ? cfma(u[a][b], hv, acc) : cjfma(u[b][a], hv, acc);
+    }
+    th[c] = cf * acc;
+  }
+  return true;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_nn_layer_tc(const float2* in, float2* out, const __nv_bfloat162* W,
+                                                     NNGeo G) {
+  constexpr int K = nn_tc_k<CIN>();
+  constexpr int KH = NN_PATHS * CIN;  // offset of the imaginary parts in K
+  extern __shared__ __align__(128) unsigned char nn_sm[];
+  unsigned char* sA = nn_sm;                 // 128 x K bf16
+  unsigned char* sB = nn_sm + 128 * K * 2;   // 16 x K bf16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 16 * K * 2);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long V = 2 * G.g.Vh;
+  const long npairs = V * G.N;
+  // weights -> B (zero where N or K is padding)
+  for (int e = tid; e < 16 * K; e += 128) {
+    const int j = e / K, k = e - j * K;
+    float v = 0.f;
+    if (j < 2 * COUT && k < 2 * KH) {
+      const int part = k / KH, pc = k - part * KH, pth = pc / CIN, c = pc - pth * CIN;
+      const int o = j % COUT, im_out = j / COUT;
+      const float2 w = __bfloat1622float2(W[(pth * COUT + o) * CIN + c]);
+      v = im_out == 0 ? (part == 0 ? w.x : -w.y) : (part == 0 ? w.y : w.x);
+    }
+    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j, k, K)) = __float2bfloat16(v);
+  }
+  // this thread's row: pair q, colour a
+  const int lp = tid / 3, a = tid - 3 * lp;
+  const long q = (long)blockIdx.x * kNNPairs + lp;
+  const bool valid = tid < 3 * kNNPairs && q < npairs;
+  long se = 0;
+  int n = 0;
+  if (valid) {
+    se = q / G.N;
+    n = (int)(q - se * G.N);
+    int par, x, y, z, t;
+    long cb;
+    nn_site(G, se, par, cb, x, y, z, t);
+#pragma unroll 1
+    for (int p = 0; p < NN_PATHS; p++) {
+      cplx<float> th[CIN];
+      if (!path_colour<CIN>(G, in, p, par, cb, x, y, z, t, n, a, th)) {
+#pragma unroll
+        for (int c = 0; c < CIN; c++) th[c] = {0.f, 0.f};
+      }
+#pragma unroll
+      for (int c = 0; c < CIN; c++) {
+        *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(tid, p * CIN + c, K)) = __float2bfloat16(th[c].re);
+        *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(tid, KH + p * CIN + c, K)) =
+            __float2bfloat16(th[c].im);
+      }
+    }
+    for (int k = 2 * KH; k < K; k++)
+      *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(tid, k, K)) = __float2bfloat16(0.f);
+  } else {
+    for (int k = 0; k < K; k++)
+      *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(tid, k, K)) = __float2bfloat16(0.f);
+  }
+  if (warp == 0) tc::tmem_alloc(tbase, 32);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  tc::fence_proxy_async();
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tbase;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 16);
+    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+    for (int ks = 0; ks < K / 16; ks++)
+      tc::mma_bf16(tmem, tc::smem_desc(a0 + ks * 256, 128, (K / 8) * 128),
+                   tc::smem_desc(b0 + ks * 256, 128, (K / 8) * 128), idesc, ks > 0);
+    tc::mma_commit(mbar);
+  }
+  const bool ok = tc::mbar_wait(mbar, 0, kNNWaitLimit);
+  tc::fence_after_sync();
+  if (ok) {
+    float v[16];
+    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
+    if (valid) {
+#pragma unroll
+      for (int o = 0; o < COUT; o++) out[((long)(o * 3 + a) * V + se) * G.N + n] = make_float2(v[o], v[COUT + o]);
+    }
+  } else if (tid == 0) {
+    atomicAdd(&g_nn_tc_timeouts, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
+template <int CIN, int COUT>
+static size_t nn_tc_smem() {
+  constexpr int K = nn_tc_k<CIN>();
+  return (size_t)128 * K * 2 + (size_t)16 * K * 2 + 16;
+}
+
+template <int CIN, int COUT>
+static void tc_launch(const float2* in, float2* out, const __nv_bfloat162* W, const NNGeo& G, cudaStream_t st) {
+  static bool opened = false;
+  const size_t shm = nn_tc_smem<CIN, COUT>();
+  if (!opened) {
+    cudaFuncSetAttribute(k_nn_layer_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    opened = true;
+  }
+  const long npairs = 2 * G.g.Vh * (long)G.N;
+  const long blocks = (npairs + kNNPairs - 1) / kNNPairs;
+  k_nn_layer_tc<CIN, COUT><<<blocks, 128, shm, st>>>(in, out, W, G);
+  count_launch();
+}
+
+static void layer_launch_tc(int l_in, int l_out, const float2* in, float2* out, const __nv_bfloat162* W,
+                            const NNGeo& G, cudaStream_t st) {
+  if (l_in == 4 && l_out == 8)
+    tc_launch<4, 8>(in, out, W, G, st);
+  else if (l_in == 8 && l_out == 8)
+    tc_launch<8, 8>(in, out, W, G, st);
+  else if (l_in == 8 && l_out == 4)
+    tc_launch<8, 4>(in, out, W, G, st);
+  else
+    tc_launch<4, 4>(in, out, W, G, st);
+}
+
+int nn_tc_timeouts(bool reset) {
+  int n = 0;
+  cudaMemcpyFromSymbol(&n, g_nn_tc_timeouts, sizeof(n));
+  if (reset && n) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_nn_tc_timeouts, &z, sizeof(z));
+  }
+  return n;
 }
 
 // T[p][k][se][n] = (T_p in)[k] for every path (training: the weight gradient needs them)
@@ -477,14 +686,16 @@ int nn_get_weights(lqcd_ctx* c, float* w_host) {
 // Network on NN-layout fields (N samples); bf16 = 1 uses the inference weights.  a, b: ping-pong
 // buffers of 8 channels; the result is in the returned pointer (4 channels).
 static float2* nn_forward(lqcd_ctx* c, const float2* h0, float2* a, float2* b, int N, int domain, bool bf16,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool tc = false) {
   NNGeo G = nn_geo(c, N, domain);
   const float2* cur = h0;
   float2* bufs[2] = {a, b};
   for (int l = 0; l < NN_LAYERS; l++) {
     float2* out = bufs[l & 1];
     const int off = nn_layer_offset(l);
-    if (bf16)
+    if (tc)
+      layer_launch_tc(NN_W[l], NN_W[l + 1], cur, out, (const __nv_bfloat162*)c->nn_w16 + off, G, st);
+    else if (bf16)
       layer_launch<__nv_bfloat162>(NN_W[l], NN_W[l + 1], cur, out, (const __nv_bfloat162*)c->nn_w16 + off, G, st);
     else
       layer_launch<float2>(NN_W[l], NN_W[l + 1], cur, out, (const float2*)c->nn_weights + off, G, st);
@@ -507,7 +718,7 @@ void nn_precondition(lqcd_ctx* c, const Inner& in, const void* r, void* z, const
   k_nn_from_spinor<<<(n + 255) / 256, 256, 0, st>>>(r, h0, g, N, in.si, in.nseg, pscale);
   count_launch();
   const int domain = in.tc == c->d_tc_dom && c->d_tc_dom != c->d_tc_full;
-  float2* out = nn_forward(c, h0, a, b, N, domain, true, st);
+  float2* out = nn_forward(c, h0, a, b, N, domain, true, st, true);
   k_nn_to_spinor<<<(g.Vh * N + 255) / 256, 256, 0, st>>>(out, z, g, N, in.si, in.nseg, ipscale);
   count_launch();
 }
@@ -610,7 +821,7 @@ static int nn_step(lqcd_ctx* c, const float2* h0, const float2* tgt, int N, int 
   return LQCD_OK;
 }
 
-int nn_apply_lex(lqcd_ctx* c, const float2* in_dev, float2* out_dev, int N, int domain) {
+int nn_apply_lex(lqcd_ctx* c, const float2* in_dev, float2* out_dev, int N, int domain, bool tc) {
   if (!c->nn_weights) return set_error(c, LQCD_ERR_STATE, "nn: no weights");
   const long VN = 2 * c->g.Vh * (long)N;
   float2* h0 = (float2*)ws_get(c, "nn_h0", (size_t)12 * VN * sizeof(float2));
@@ -619,7 +830,7 @@ int nn_apply_lex(lqcd_ctx* c, const float2* in_dev, float2* out_dev, int N, int 
   if (!h0 || !a || !b) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
   k_nn_lex<<<(VN + 255) / 256, 256, 0, c->work>>>(in_dev, h0, c->g, N, 1, c->d_coord);
   count_launch();
-  float2* out = nn_forward(c, h0, a, b, N, domain, false, c->work);
+  float2* out = nn_forward(c, h0, a, b, N, domain, tc, c->work, tc);
   k_nn_lex<<<(VN + 255) / 256, 256, 0, c->work>>>(out, out_dev, c->g, N, 0, c->d_coord);
   count_launch();
   return LQCD_OK;
@@ -648,50 +859,64 @@ int nn_train(lqcd_ctx* c, int n_pairs, int epochs, int batch, double lr, int dom
   if (!nn_ensure(c)) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
   const long V = 2 * g.Vh;
   const int nb_pairs = (n_pairs + batch - 1) / batch;
-  n_pairs = nb_pairs * batch;
-  // pair storage in NN layout (FP32): inputs and targets, batch-major
+  // Pairs are generated in pools that fit a quarter of the free device memory (a 32^3 x 64 pair
+  // in the network layout is 400 MB, so 2000 of them cannot be resident at once): each pool is
+  // generated by the solver, trained on for `epochs` passes, and replaced by the next.
   const size_t per_batch = (size_t)12 * V * batch * sizeof(float2);
-  float2* R = (float2*)ws_get(c, "nn_pairs_r", per_batch * nb_pairs);
-  float2* E = (float2*)ws_get(c, "nn_pairs_e", per_batch * nb_pairs);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const int pool = std::max(1, std::min(nb_pairs, (int)(free_b / 4 / (2 * per_batch))));
+  float2* R = (float2*)ws_get(c, "nn_pairs_r", per_batch * pool);
+  float2* E = (float2*)ws_get(c, "nn_pairs_e", per_batch * pool);
   double2* b64 = (double2*)ws_get(c, "nn_b64", (size_t)2 * spinor_bytes(g, P64, batch));
   double2* x64 = (double2*)ws_get(c, "nn_x64", (size_t)2 * spinor_bytes(g, P64, batch));
   double2* r64 = (double2*)ws_get(c, "nn_r64", (size_t)2 * spinor_bytes(g, P64, batch));
   void* f32 = ws_get(c, "nn_f32", spinor_bytes(g, P32, batch));
   if (!R || !E || !b64 || !x64 || !r64 || !f32) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory (pairs)");
+  // the solver without the network: FP64 defect correction around FP32 BiCGStab, true residual 1e-8
   lqcd_solve_params p;
   lqcd_default_params(&p);
-  p.solver = LQCD_SOLVER_BICGSTAB64;
+  p.solver = LQCD_SOLVER_MIXED;
+  p.inner_prec = LQCD_PREC_F32;
   p.tol = 1e-8;
   const size_t sb64 = spinor_bytes(g, P64, batch);
   VGeom vgH = make_vgeom(g, batch, 1);
-  for (int k = 0; k < nb_pairs; k++) {
-    k_nn_random_even<<<(2 * g.Vh * batch + 255) / 256, 256, 0, st>>>(r64, g, batch, seed + 7919u * k);
-    count_launch();
-    cudaMemsetAsync(b64, 0, 2 * sb64, st);
-    launch_clover_only(g, P64, c->A64, r64, b64, batch, st);  // b_e = A_ee r_e
-    BatchStats bs;
-    int rc = solve_batch(c, b64, x64, batch, domain, p, bs);
-    if (rc != LQCD_OK) return rc;
-    // even halves to NN layout (odd zero)
-    v_convert(P64, P32, r64, f32, vgH, nullptr, 1, nullptr, st);
-    k_nn_from_spinor<<<(V * batch + 255) / 256, 256, 0, st>>>(f32, R + (size_t)k * 12 * V * batch, g, batch, nullptr, 1,
-                                                             nullptr);
-    v_convert(P64, P32, x64, f32, vgH, nullptr, 1, nullptr, st);
-    k_nn_from_spinor<<<(V * batch + 255) / 256, 256, 0, st>>>(f32, E + (size_t)k * 12 * V * batch, g, batch, nullptr, 1,
-                                                             nullptr);
-    count_launch(2);
-  }
-  for (int ep = 0; ep < epochs; ep++) {
-    double acc = 0;
-    for (int k = 0; k < nb_pairs; k++) {
-      double L = 0;
-      int rc = nn_step(c, R + (size_t)k * 12 * V * batch, E + (size_t)k * 12 * V * batch, batch, domain, 1, &L,
-                       nullptr, true, (float)lr);
+  std::vector<double> ep_sum(epochs, 0.0);
+  int rounds = 0;
+  for (int k0 = 0; k0 < nb_pairs; k0 += pool, rounds++) {
+    const int nk = std::min(pool, nb_pairs - k0);
+    for (int kk = 0; kk < nk; kk++) {
+      const int k = k0 + kk;
+      k_nn_random_even<<<(2 * g.Vh * batch + 255) / 256, 256, 0, st>>>(r64, g, batch, seed + 7919u * k);
+      count_launch();
+      cudaMemsetAsync(b64, 0, 2 * sb64, st);
+      launch_clover_only(g, P64, c->A64, r64, b64, batch, st);  // b_e = A_ee r_e
+      BatchStats bs;
+      int rc = solve_batch(c, b64, x64, batch, domain, p, bs);
       if (rc != LQCD_OK) return rc;
-      acc += L;
+      // even halves to NN layout (odd zero)
+      v_convert(P64, P32, r64, f32, vgH, nullptr, 1, nullptr, st);
+      k_nn_from_spinor<<<(V * batch + 255) / 256, 256, 0, st>>>(f32, R + (size_t)kk * 12 * V * batch, g, batch,
+                                                               nullptr, 1, nullptr);
+      v_convert(P64, P32, x64, f32, vgH, nullptr, 1, nullptr, st);
+      k_nn_from_spinor<<<(V * batch + 255) / 256, 256, 0, st>>>(f32, E + (size_t)kk * 12 * V * batch, g, batch,
+                                                               nullptr, 1, nullptr);
+      count_launch(2);
     }
-    if (loss_hist) loss_hist[ep] = acc / nb_pairs;
+    for (int ep = 0; ep < epochs; ep++) {
+      double acc = 0;
+      for (int kk = 0; kk < nk; kk++) {
+        double L = 0;
+        int rc = nn_step(c, R + (size_t)kk * 12 * V * batch, E + (size_t)kk * 12 * V * batch, batch, domain, 1, &L,
+                         nullptr, true, (float)lr);
+        if (rc != LQCD_OK) return rc;
+        acc += L;
+      }
+      ep_sum[ep] += acc / nk;
+    }
   }
+  if (loss_hist)
+    for (int ep = 0; ep < epochs; ep++) loss_hist[ep] = ep_sum[ep] / rounds;
   return LQCD_OK;
 }
 

@@ -35,7 +35,7 @@ EXPORTED = [
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
     "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant", "lqcd_schur_apply",
     "lqcd_conn_correlator", "lqcd_nr_estimator", "lqcd_ape_smear", "lqcd_smeared_links",
-    "lqcd_perambulator_cols", "lqcd_window_average",
+    "lqcd_perambulator_cols", "lqcd_window_average", "lqcd_nn_apply_tc",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -140,6 +140,7 @@ def load_library(path=_LIB_PATH):
         "lqcd_nn_set_weights": (ip, [vp, vp]),
         "lqcd_nn_get_weights": (ip, [vp, vp]),
         "lqcd_nn_apply": (ip, [vp, vp, vp, ip, ip, ip]),
+        "lqcd_nn_apply_tc": (ip, [vp, vp, vp, ip, ip, ip]),
         "lqcd_nn_loss_grad": (ip, [vp, vp, vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_double), vp]),
         "lqcd_nn_train": (ip, [vp, ip, ip, ip, ctypes.c_double, ip, ctypes.c_uint, vp]),
     }
@@ -382,6 +383,12 @@ class Context:
     def nn_apply(self, x, out, domain=False):
         return self._check(_lib.lqcd_nn_apply(self.h, _ptr(x, np.complex64), _ptr(out, np.complex64), x.shape[0],
                                               int(domain), _where(x, out)))
+
+    def nn_apply_tc(self, x, out, domain=False):
+        """The inference path of the preconditioner: BF16 weights and activations, channel mixing on
+        the tensor cores, FP32 accumulation."""
+        return self._check(_lib.lqcd_nn_apply_tc(self.h, _ptr(x, np.complex64), _ptr(out, np.complex64), x.shape[0],
+                                                 int(domain), _where(x, out)))
 
     def nn_loss_grad(self, x, target, domain=False, even_only=False):
         loss = ctypes.c_double()

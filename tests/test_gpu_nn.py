@@ -47,6 +47,27 @@ def test_forward_matches_oracle(domain):
     assert np.abs(out - ref).max() / np.abs(ref).max() < 2e-5
 
 
+@pytest.mark.parametrize("domain", [False, True])
+def test_tensor_core_forward_within_bf16_bound(domain):
+    """The inference path (BF16 weights and activations, tcgen05 channel mixing, FP32 accumulation)
+    against the FP64 oracle with the same weights: BF16 keeps 8 significant bits, so each layer's
+    inputs carry about 2^-9 relative rounding; over four layers the outputs stay within 2% of the
+    largest output entry and 1% in the Frobenius norm."""
+    case = ROUGH
+    U = gauge(case, 81)
+    ctx = _ctx(case, U)
+    Ws = [np.asarray(W, np.complex64).astype(np.complex128) for W in nn.init_weights(7, 0.3)]
+    ctx.nn_set_weights(Ws)
+    x = _fields(case, 5, 9)
+    out = np.zeros_like(x)
+    ctx.nn_apply_tc(x, out, domain=domain)
+    Ue = fermion_links(U, BC_ANTIPERIODIC, case["extents"] if domain else None)
+    ref = nn.forward(Ws, Ue, x.astype(np.complex128))[-1]
+    assert np.abs(out - ref).max() <= 2e-2 * np.abs(ref).max()
+    assert np.linalg.norm(out - ref) <= 1e-2 * np.linalg.norm(ref)
+    assert np.linalg.norm(out - ref) > 0  # BF16 rounding is visible: this is not the FP32 path
+
+
 @pytest.mark.parametrize("even_only", [False, True])
 def test_loss_and_gradient_match_oracle(even_only):
     case = ROUGH
