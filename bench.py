@@ -61,6 +61,12 @@ WORKLOADS = {
         extents=[6, 8, 10, 6, 8, 10], sweep={}, gauge_seed=3001, cv_seed=3002,
         sources="seeded orthonormal colour vectors (Cholesky-QR twice)", rhs_block=64, pipeline=1,
         solver_sample_rhs=16),
+    "learned": dict(
+        title="32^3x64 learned preconditioner: flexible GCR with the gauge-covariant network",
+        dims=(32, 32, 32, 64), eps=0.6, kappa=0.126, csw=1.7, n_ev=64, t_src=list(range(0, 64, 4)),
+        extents=[4] * 16, sweep={}, gauge_seed=4001, cv_seed=4002,
+        sources="seeded orthonormal colour vectors (Cholesky-QR twice)", rhs_block=16, pipeline=1,
+        solver_sample_rhs=16, learned=dict(pairs=2000, batch=4, epochs=2, lr=2e-3, seed=41)),
 }
 GAMMAS = [5, 0]
 
@@ -296,6 +302,22 @@ class Workload:
         self.params = default_params(solver=lq.LQCD_SOLVER_MIXED, inner_prec=lq.LQCD_PREC_F32,
                                      rhs_block=self.rhs_block // self.pipeline, pipeline=self.pipeline,
                                      projection=self.projection)
+        self.training = None
+        if self.wl.get("learned"):  # train the network on solver-generated pairs, then solve with it
+            import torch
+            L = self.wl["learned"]
+            self.ctx.nn_set_weights(lq.nn_initial_weights(5, 0.05))
+            torch.cuda.synchronize()
+            t0 = time.time()
+            hist = self.ctx.nn_train(n_pairs=L["pairs"], epochs=L["epochs"], batch=L["batch"], lr=L["lr"],
+                                     seed=L["seed"])
+            torch.cuda.synchronize()
+            self.training = {"pairs": L["pairs"], "batch": L["batch"], "epochs": L["epochs"], "lr": L["lr"],
+                             "seconds": time.time() - t0, "loss_per_epoch": [float(h) for h in hist],
+                             "pairs_from": "the solver without the network (FP64 defect correction around FP32 "
+                                           "BiCGStab, true residual 1e-8), random even-site r"}
+            self.params = default_params(solver=lq.LQCD_SOLVER_FGCR_NN, rhs_block=self.rhs_block,
+                                         projection=self.projection)
 
     def unit(self, step):
         from paper_2609_37049_b300.shard import plan_unit
@@ -447,6 +469,9 @@ def run_ours(args, rank, world):
                             "max_true_resid": max(x[2] for x in step_stats),
                             "outer_cycles": max(x[3] for x in step_stats)},
            "setup_s": {"gauge": W.t_gauge, "vectors": W.t_vectors}, "tuning": W.tuning}
+    if W.training:
+        res["training"] = W.training
+        res["metric"] = "distillation RHS/s at FP64 resid 1e-10 (learned-preconditioned FGCR)"
     if not args.no_extras:  # before the end-to-end run, whose host staging buffers stay allocated
         res.update(extras(W, peak, peak_kind, dev))
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -508,6 +533,10 @@ def extras(W, peak, peak_kind, dev):
         solvers["mixed_fgcr_fp16_mr4"] = sample(default_params(solver=lqcd.LQCD_SOLVER_MIXED,
                                                                inner_prec=lqcd.LQCD_PREC_F16, precond_iters=4,
                                                                rhs_block=blk))
+    if W.training:
+        solvers["mixed_fgcr_learned"] = sample(default_params(solver=lqcd.LQCD_SOLVER_FGCR_NN, rhs_block=blk))
+        solvers["mixed_fgcr_none"] = sample(default_params(solver=lqcd.LQCD_SOLVER_FGCR_NN, precond_iters=-1,
+                                                           rhs_block=blk))
     plain = solvers["plain_fp64_bicgstab"]["rhs_per_s"]
     out["solvers"] = solvers
     out["solver_sample"] = "full-operator perambulator columns of %d RHS (t=%d, colour vectors 0..%d, 4 spins)" % (

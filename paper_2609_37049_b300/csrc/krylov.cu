@@ -759,7 +759,7 @@ int solve_batch_enqueue(lqcd_ctx* c, int slot, const double2* b, double2* x, int
   Batch& B = *static_cast<Batch*>(h.batch.get());
   if (int rc = plan_batch(c, slot, nrhs, domain, prm, B)) return rc;
   const bool use_graph = prm.use_graph != 0;
-  if (use_graph && !c->loop_graphs_unavailable && !c->timing && B.pkind != PREC_NN) {
+  if (use_graph && !c->loop_graphs_unavailable && !c->timing) {
     char key[512];
     snprintf(key, sizeof key, "loop:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%p", slot, B.P,
              nrhs, domain, B.nseg, B.chunk, B.tol, B.inner_tol, B.max_iter, B.max_outer, B.in.variant, B.v64,

@@ -336,13 +336,27 @@ static size_t nn_tc_smem() {
 }
 
 template <int CIN, int COUT>
+static void tc_open() {
+  cudaFuncSetAttribute(k_nn_layer_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)nn_tc_smem<CIN, COUT>());
+}
+
+// Raise the shared-memory limit of every tensor-core layer instantiation once, before any launch
+// (and so before any stream capture).
+static void tc_open_all() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  tc_open<4, 8>();
+  tc_open<8, 8>();
+  tc_open<8, 4>();
+  tc_open<4, 4>();
+}
+
+template <int CIN, int COUT>
 static void tc_launch(const float2* in, float2* out, const __nv_bfloat162* W, const NNGeo& G, cudaStream_t st) {
-  static bool opened = false;
+  tc_open_all();
   const size_t shm = nn_tc_smem<CIN, COUT>();
-  if (!opened) {
-    cudaFuncSetAttribute(k_nn_layer_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    opened = true;
-  }
   const long npairs = 2 * G.g.Vh * (long)G.N;
   const long blocks = (npairs + kNNPairs - 1) / kNNPairs;
   k_nn_layer_tc<CIN, COUT><<<blocks, 128, shm, st>>>(in, out, W, G);
@@ -726,6 +740,7 @@ void nn_precondition(lqcd_ctx* c, const Inner& in, const void* r, void* z, const
 // Reserve the three NN-layout work fields used by nn_precondition for a batch of nrhs (outside
 // graph capture).
 int nn_reserve(lqcd_ctx* c, int nrhs) {
+  tc_open_all();
   const size_t fb = (size_t)24 * 2 * c->g.Vh * nrhs * sizeof(float2);
   for (int i = 0; i < 3; i++) {
     c->nn_buf[i] = ws_get(c, "nn_buf" + std::to_string(i), fb);
