@@ -10,13 +10,14 @@ t = 0, 6, ..., 90; 24 time domains of extent 4 (extents 8 and 12 measured beside
 Gamma = {gamma_5, 1}.  Synthetic data; it stands in for the paper's 96 x 32^3 ensemble with its
 200 Laplacian eigenvectors.
 
-One step = the whole hot path for one RHS block (rhs_block right-hand sides: rhs_block / 4 source
-colour vectors x 4 spins):
-  full-operator perambulator columns of that block at one source timeslice   rhs_block RHS
-  domain-operator columns of the same block for one source group (one source timeslice per
-  domain) as one multi-site solve                        rhs_block x (domains served) RHS
+One step = the whole hot path for one RHS block of each operator (rhs_block right-hand sides:
+rhs_block / 4 source colour vectors x 4 spins):
+  full-operator perambulator columns of a block at one source timeslice   rhs_block RHS
+  domain-operator columns of a block for one source group (one source timeslice per domain) as
+  one multi-site solve                                   rhs_block x (domains served) RHS
   loops of both, and the full / factorised / subtracted correlators of the configuration.
-Consecutive steps walk the source timeslices, then the blocks.  Every solve reaches FP64 true
+Consecutive steps walk the full operator's source timeslices, then its blocks, and the domain
+operator's groups, then its blocks, so no step repeats the work of an earlier one.  Every solve reaches FP64 true
 residual <= 1e-10 (FP64 defect correction around FP32 BiCGStab).
 metric value = RHS solved per second (full + domain; each domain of a multi-site solve counts
 once), inputs resident in HBM.
@@ -324,7 +325,7 @@ class Workload:
         return plan_unit(step * self.world + self.rank, len(self.t_src), len(self.groups), self.n_blocks)
 
     def rhs_of_unit(self, u):
-        k, g, b = u
+        k, bf, g, bd = u
         return self.rhs_block + self.rhs_block * len(self.groups[g])
 
     def step(self, s, host=None):
@@ -332,8 +333,7 @@ class Workload:
         Returns the right-hand sides solved."""
         from paper_2609_37049_b300 import Stats
         lq = self.lqcd
-        k, g, b = u = self.unit(s)
-        j0 = b * self.nj
+        k, bf, g, bd = u = self.unit(s)
         grp = self.groups[g]
         B = self if host is None else None
         V = self.V if B else host["V"]
@@ -344,12 +344,12 @@ class Workload:
         if host is not None:
             self.ctx.gauge_upload(host["U"], self.wl["kappa"], self.wl["csw"])
         st = Stats(1, 1)
-        self.ctx.perambulator_cols(V[k:k + 1], self.n_ev, [self.t_src[k]], tau_f[k:k + 1], j0, self.nj,
+        self.ctx.perambulator_cols(V[k:k + 1], self.n_ev, [self.t_src[k]], tau_f[k:k + 1], bf * self.nj, self.nj,
                                    mode=lq.LQCD_MODE_FULL, sinks=lq.LQCD_SINKS_DIAG_SRCV, params=self.params,
                                    stats=st)
         self.stats.append(("full", st.total_iters, st.max_true_resid, st.outer_cycles))
         st = Stats(1, 1)
-        self.ctx.perambulator_cols(Vg, self.n_ev, grp, tau_g, j0, self.nj, mode=lq.LQCD_MODE_DOMAIN,
+        self.ctx.perambulator_cols(Vg, self.n_ev, grp, tau_g, bd * self.nj, self.nj, mode=lq.LQCD_MODE_DOMAIN,
                                    sinks=lq.LQCD_SINKS_DIAG_SRCV, params=self.params, stats=st)
         self.stats.append(("dom", st.total_iters, st.max_true_resid, st.outer_cycles))
         # loops of the timeslices this step touched, then the correlators of the configuration
@@ -391,7 +391,7 @@ class Workload:
 
     def e2e_bytes(self, s):
         """Host<->device bytes of one end-to-end step (counted from the arrays the calls copy)."""
-        k, g, b = self.unit(s)
+        k, bf, g, bd = self.unit(s)
         vslice = self.n_ev * self.L3 * 3 * 16
         tau1 = self.n_ev * 4 * self.n_ev * 4 * 16
         grp = len(self.groups[g])

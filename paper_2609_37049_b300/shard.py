@@ -62,13 +62,15 @@ def units_for_step(units, step, rank, world):
 
 def plan_unit(unit, n_full, n_groups, n_blocks):
     """Work of bench unit `unit` (unit = step * world + rank): the full-operator source timeslice
-    index k (into t_src), the domain source-group index, and the RHS block b (source vectors
-    b * nj .. b * nj + nj - 1, all spins).  Consecutive units walk the timeslices and groups
-    first, then the blocks, so n_full * n_blocks units cover every full-operator right-hand side
-    once and n_groups * n_blocks units every domain right-hand side."""
+    index k (into t_src) with its RHS block bf, and the domain source-group index g with its RHS
+    block bd (block b = source vectors b * nj .. b * nj + nj - 1, all spins).  The full work walks
+    the timeslices first, then the blocks, so n_full * n_blocks consecutive units cover every
+    full-operator right-hand side once; the domain work walks the groups, then the blocks, so
+    n_groups * n_blocks consecutive units cover every domain right-hand side once.  Returns
+    (k, bf, g, bd)."""
     if unit < 0 or min(n_full, n_groups, n_blocks) < 1:
         raise ValueError("bad unit or sizes")
-    return unit % n_full, unit % n_groups, (unit // max(n_full, n_groups)) % n_blocks
+    return unit % n_full, (unit // n_full) % n_blocks, unit % n_groups, (unit // n_groups) % n_blocks
 
 
 def gather_loops(local, rank, world, dist=None):

@@ -98,12 +98,69 @@ def test_duplicate_timeslice_is_an_error():
 def test_plan_unit_covers_every_rhs_block_once():
     from paper_2609_37049_b300.shard import plan_unit
     for n_full, n_groups, n_blocks in ((16, 1, 32), (32, 4, 8), (48, 10, 4)):
-        seen_full, seen_dom = set(), set()
-        for u in range(n_full * n_blocks):
-            k, g, b = plan_unit(u, n_full, n_groups, n_blocks)
-            assert 0 <= k < n_full and 0 <= g < n_groups and 0 <= b < n_blocks
-            seen_full.add((k, b))
-            if u < n_groups * n_blocks * (max(n_full, n_groups) // n_groups):
-                seen_dom.add((g, b))
-        assert len(seen_full) == n_full * n_blocks
-        assert len(seen_dom) == n_groups * n_blocks
+        full = [plan_unit(u, n_full, n_groups, n_blocks)[:2] for u in range(n_full * n_blocks)]
+        dom = [plan_unit(u, n_full, n_groups, n_blocks)[2:] for u in range(n_groups * n_blocks)]
+        assert len(set(full)) == n_full * n_blocks
+        assert len(set(dom)) == n_groups * n_blocks
+
+
+def _fake_unit(unit, t_src, groups, n_blocks):
+    """Stand-in for one bench step's GPU work on unit `unit` (the plan of bench.py): the loops of
+    the full-operator block at one source timeslice and of the domain-operator block of one group."""
+    from paper_2609_37049_b300.shard import plan_unit
+    k, bf, g, bd = plan_unit(unit, len(t_src), len(groups), n_blocks)
+    out = {("f", t_src[k], bf): np.array([np.sin(t_src[k] + 0.1 * bf), np.cos(bf)])}
+    if unit < len(groups) * n_blocks:  # the domain work repeats after every group and block was done
+        for t in groups[g]:
+            out[("d", t, bd)] = np.array([np.cos(t - 0.3 * bd), np.sin(2 * bd + t)])
+    return out
+
+
+def _bench_worker(rank, world, port, steps, t_src, groups, n_blocks, out_q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local = {}
+    for s in range(steps):
+        for key, v in _fake_unit(s * world + rank, t_src, groups, n_blocks).items():
+            assert key not in local  # a rank never repeats a unit within the run
+            local[key] = v
+    merged = gather_loops(local, rank, world, dist)
+    if rank == 0:
+        out_q.put({k: v.tolist() for k, v in merged.items()})
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_step_plan_gathered_over_two_ranks_equals_one_rank():
+    """bench.py under torchrun: rank r runs unit s * world + r in step s (weak scaling, no exchange
+    during the steps); gathering the per-rank loops afterwards gives exactly the single-rank run of
+    twice the steps, and n_full * n_blocks units cover every full-operator block once."""
+    from paper_2609_37049_b300.shard import domain_groups
+    t_src = list(range(0, 96, 6))
+    groups = domain_groups(t_src, 96, [8] * 12)
+    n_blocks = 4
+    steps = len(t_src) * n_blocks // 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_worker, args=(r, 2, port, steps, t_src, groups, n_blocks, q))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    single = {}
+    for u in range(2 * steps):
+        for key, v in _fake_unit(u, t_src, groups, n_blocks).items():
+            single[key] = v
+    assert set(got) == set(single)
+    for key, v in single.items():
+        assert np.allclose(got[key], v)
+    full = sorted((t, b) for (kind, t, b) in single if kind == "f")
+    assert full == sorted((t, b) for t in t_src for b in range(n_blocks))
+    dom = sorted((t, b) for (kind, t, b) in single if kind == "d")
+    assert dom == sorted((t, b) for g in groups for t in g for b in range(n_blocks))
