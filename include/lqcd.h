@@ -350,6 +350,12 @@ int lqcd_nn_apply_tc(lqcd_ctx* ctx, const float* in, float* out, int nsamp, int 
  * gradient dL/dconj(W) (host, 2 * lqcd_nn_num_weights() floats; may be NULL). */
 int lqcd_nn_loss_grad(lqcd_ctx* ctx, const float* in, const float* target, int nsamp, int domain, int even_only,
                       int where, double* loss, float* grad);
+/* The same loss and gradient computed by the BF16 training kernels that lqcd_nn_train runs:
+ * forward and backward-data layers on the tensor cores (BF16 weights and activations, FP32
+ * accumulation), transported activations stored in BF16 for the weight gradient (FP32
+ * accumulation).  Agrees with lqcd_nn_loss_grad to BF16 rounding. */
+int lqcd_nn_loss_grad_bf16(lqcd_ctx* ctx, const float* in, const float* target, int nsamp, int domain,
+                           int even_only, int where, double* loss, float* grad);
 /* Train on n_pairs (r, e) pairs of the even-odd Schur system M e = r generated from random r
  * (seeded) by the solver without the network (FP64 defect correction around FP32 BiCGStab, true
  * residual 1e-8): pools of pairs that fit a quarter of the free device memory are generated in

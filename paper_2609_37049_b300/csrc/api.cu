@@ -49,20 +49,42 @@ void set_global_error(const std::string& msg) { g_create_error = msg; }
 
 void* ws_get(lqcd_ctx* c, const std::string& name, size_t bytes) {
   auto it = c->ws.find(name);
-  if (it != c->ws.end() && it->second.second >= bytes) return it->second.first;
+  if (it != c->ws.end() && it->second.bytes >= bytes) {
+    it->second.gen = c->ws_gen;
+    return it->second.p;
+  }
   if (it != c->ws.end()) {
     cudaStreamSynchronize(c->work);
     if (c->slot_stream) cudaStreamSynchronize(c->slot_stream);
-    cudaFree(it->second.first);
+    cudaFree(it->second.p);
     c->ws.erase(it);
     drop_graphs(c);  // graphs captured on the old buffer are stale
   }
+  const size_t sz = bytes < 256 ? 256 : bytes;
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
+  if (cudaMalloc(&p, sz) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    // Short of memory: free the buffers that only earlier calls used (another solver's or block
+    // size's work vectors), then try once more.
+    bool freed = false;
+    for (auto& kv : c->ws)
+      if (kv.second.gen != c->ws_gen) freed = true;
+    if (!freed) return nullptr;
+    drop_graphs(c);
+    for (auto i = c->ws.begin(); i != c->ws.end();) {
+      if (i->second.gen != c->ws_gen) {
+        cudaFree(i->second.p);
+        i = c->ws.erase(i);
+      } else {
+        ++i;
+      }
+    }
+    if (cudaMalloc(&p, sz) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
   }
-  c->ws[name] = {p, bytes < 256 ? 256 : bytes};
+  c->ws[name] = {p, sz, c->ws_gen};
   return p;
 }
 
@@ -155,6 +177,7 @@ void clifford(M4 out[16], M4 tilde[16]) {
 struct Scope {
   lqcd_ctx* c;
   explicit Scope(lqcd_ctx* ctx) : c(ctx) {
+    c->ws_gen++;
     cudaEventRecord(c->ev_user, c->user_stream);
     cudaStreamWaitEvent(c->work, c->ev_user, 0);
   }
@@ -444,7 +467,7 @@ int lqcd_destroy(lqcd_ctx* c) {
   if (c->work) cudaStreamSynchronize(c->work);
   flush_phase_times(c);
   drop_graphs(c);
-  for (auto& kv : c->ws) cudaFree(kv.second.first);
+  for (auto& kv : c->ws) cudaFree(kv.second.p);
   for (void* p : c->slot_pinned)
     if (p) cudaFreeHost(p);
   if (c->slot_stream) cudaStreamDestroy(c->slot_stream);
@@ -1111,7 +1134,23 @@ extern "C" int lqcd_nn_loss_grad(lqcd_ctx* c, const float* in, const float* targ
   const float2* di = (const float2*)stage_in(c, in, bytes, where, "nn_in");
   const float2* dt = (const float2*)stage_in(c, target, bytes, where, "nn_tgt");
   if (!di || !dt) return set_error(c, LQCD_ERR_OOM, "nn_loss_grad: OOM");
-  return nn_loss_grad_lex(c, di, dt, nsamp, domain, even_only, loss, grad);
+  return nn_loss_grad_lex(c, di, dt, nsamp, domain, even_only, loss, grad, false);
+}
+
+extern "C" int lqcd_nn_loss_grad_bf16(lqcd_ctx* c, const float* in, const float* target, int nsamp, int domain,
+                                      int even_only, int where, double* loss, float* grad) {
+  if (!c || !in || !target || !loss || nsamp < 1)
+    return set_error(c, LQCD_ERR_INVALID_ARG, "nn_loss_grad_bf16: bad arguments");
+  if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "nn_loss_grad_bf16: no gauge field uploaded");
+  Scope sc(c);
+  const size_t bytes = (size_t)c->V * 12 * nsamp * sizeof(float2);
+  const float2* di = (const float2*)stage_in(c, in, bytes, where, "nn_in");
+  const float2* dt = (const float2*)stage_in(c, target, bytes, where, "nn_tgt");
+  if (!di || !dt) return set_error(c, LQCD_ERR_OOM, "nn_loss_grad_bf16: OOM");
+  int rc = nn_loss_grad_lex(c, di, dt, nsamp, domain, even_only, loss, grad, true);
+  if (rc == LQCD_OK && nn_tc_timeouts(true))
+    return set_error(c, LQCD_ERR_TIMEOUT, "nn_loss_grad_bf16: a tensor-core wait ran out");
+  return rc;
 }
 
 extern "C" int lqcd_nn_train(lqcd_ctx* c, int n_pairs, int epochs, int batch, double lr, int domain, unsigned seed,

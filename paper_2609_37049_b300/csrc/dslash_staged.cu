@@ -289,16 +289,9 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl_kernel(const DslashParams
   const int cb0 = blockIdx.x * S;
   const int Vh = (int)g.Vh;
   const int sy = g.Lx, sz = g.Lx * g.Ly, sw = sz * g.Lz;
-  // Staging is done by the warps that use it: a group of gsz threads (one warp, or the nrhs / 32
-  // warps of one site) stages the links and clover of its own sg sites and waits only for itself
-  // (warp sync or a named barrier), so no warp waits for the staging of another group's sites.
-  const int gsz = nr > 32 ? nr : 32;
-  const int grp = threadIdx.x / gsz, gl = threadIdx.x - grp * gsz;
-  const int sg = gsz >> lg, site0 = grp * sg;
-
-  for (int j = gl; j < 26 * sg; j += gsz) {
-    if (j < 8 * sg) {  // link j & 7 of site j >> 3, third row rebuilt once
-      const int site = site0 + (j >> 3), k = j & 7, c = cb0 + site;
+  for (int j = threadIdx.x; j < 26 * S; j += 128) {
+    if (j < 8 * S) {  // link j & 7 of site j >> 3, third row rebuilt once
+      const int site = j >> 3, k = j & 7, c = cb0 + site;
       if (c < Vh) {
         const int mu = k >> 1;
         int lcb = c, par = pr.out_par;
@@ -324,7 +317,7 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl_kernel(const DslashParams
         L[4] = make_float4(u[2][2].re, u[2][2].im, 0.f, 0.f);
       }
     } else {  // clover chunk e of site q / 18
-      const int q = j - 8 * sg, sq = q / 18, e = q - sq * 18, site = site0 + sq, c = cb0 + site;
+      const int q = j - 8 * S, site = q / 18, e = q - site * 18, c = cb0 + site;
       if (c < Vh) {
         if constexpr (P == P32) {
           sclov[site][e] = __ldg(reinterpret_cast<const float4*>(pr.C) + (long)e * Vh + c);
@@ -340,10 +333,7 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl_kernel(const DslashParams
   const int cb = tid >> lg;
   const int rhs = tid & (nr - 1);
   const unsigned cw = cb < Vh ? __ldg(pr.coord + cb) : 0u;  // issued before the barrier
-  if (gsz == 32)
-    __syncwarp();
-  else
-    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(gsz) : "memory");
+  __syncthreads();
 
   if (RED == RED_NONE && cb >= Vh) return;
   const int sl = threadIdx.x >> lg;

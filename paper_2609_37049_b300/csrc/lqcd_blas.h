@@ -89,7 +89,7 @@ int nn_apply_lex(lqcd_ctx* c, const float2* in_dev, float2* out_dev, int N, int 
 // tensor-core layer waits that ran out of their iteration limit since the last reset
 int nn_tc_timeouts(bool reset);
 int nn_loss_grad_lex(lqcd_ctx* c, const float2* in_dev, const float2* tgt_dev, int N, int domain, int even_only,
-                     double* loss, float* grad_host);
+                     double* loss, float* grad_host, bool bf16);
 int nn_train(lqcd_ctx* c, int n_pairs, int epochs, int batch, double lr, int domain, unsigned seed,
              double* loss_hist);
 void outer_update(const double* r2, const double* b2, int nsys, double tol, double inner_tol, int* active,

@@ -142,8 +142,16 @@ struct lqcd_ctx {
   lqcd::SegInfo seg_full, seg_dom;
   lqcd::SegInfo* d_seg_full = nullptr;  // device copies
   lqcd::SegInfo* d_seg_dom = nullptr;
-  // workspace: grow-only device buffers by name
-  std::map<std::string, std::pair<void*, size_t>> ws;
+  // workspace: device buffers by name, grown on demand; gen is the API call that last used the
+  // buffer (ws_gen counts calls), so that a call short of memory can free buffers only earlier
+  // calls used.
+  struct WsBuf {
+    void* p;
+    size_t bytes;
+    unsigned long gen;
+  };
+  std::map<std::string, WsBuf> ws;
+  unsigned long ws_gen = 0;
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
   std::string err;

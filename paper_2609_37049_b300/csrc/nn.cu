@@ -83,12 +83,15 @@ LQCD_D bool path_vectors(const NNGeo& G, const float2* h, int p, int par, long c
   }
   const int npar = p == 0 ? par : 1 - par;
   const long nse = (long)npar * g.Vh + (sn >> 1);
+  const long VN = V * G.N;  // stride between the channel-colour planes
+  const float2* hp = h + nse * G.N + n;
   cplx<float> hv[C][3];
 #pragma unroll
   for (int c = 0; c < C; c++)
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      float2 v = __ldg(h + ((long)(c * 3 + a) * V + nse) * G.N + n);
+      const float2 v = __ldg(hp);
+      hp += VN;
       hv[c][a] = {v.x, v.y};
     }
   if (p == 0) {
@@ -103,15 +106,22 @@ LQCD_D bool path_vectors(const NNGeo& G, const float2* h, int p, int par, long c
     load_link<P32>(G.U, g.Vh, mu, par, cb, u);
   else
     load_link<P32>(G.U, g.Vh, mu, 1 - par, sn >> 1, u);
-  const float cf = (float)coef;
+  // the backward hop's U^dag and the time-boundary sign, once on the link, so that every path
+  // runs the same product below
+  cplx<float> w[3][3];
+  const float sg = coef < 0 ? -1.f : 1.f;
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+      w[a][b] = fwd ? cplx<float>{sg * u[a][b].re, sg * u[a][b].im} : cplx<float>{sg * u[b][a].re, -sg * u[b][a].im};
 #pragma unroll
   for (int c = 0; c < C; c++)
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      cplx<float> acc = {0.f, 0.f};
-#pragma unroll
-      for (int b = 0; b < 3; b++) acc = acc + (fwd ? u[a][b] * hv[c][b] : cjmul(u[b][a], hv[c][b]));
-      th[c][a] = cf * acc;
+      cplx<float> acc = w[a][0] * hv[c][0];
+      acc = cfma(w[a][1], hv[c][1], acc);
+      th[c][a] = cfma(w[a][2], hv[c][2], acc);
     }
   return true;
 }
@@ -165,188 +175,269 @@ __global__ void k_nn_layer(const float2* in, float2* out, const WT* W, NNGeo G) 
 
 // ------------------------------------------------------------------ tensor-core layer (inference)
 // The same layer with the channel mixing on the tensor cores (tcgen05, BF16 operands, FP32
-// accumulation in tensor memory).  The mixing is a GEMM whose rows are (site, sample, colour)
-// -- the weights do not mix colours -- with K = (re / im part, path, input channel) and N =
-// (re / im part, output channel):
-//   A[row][(0, p, c)] = Re (T_p h_c)[a],  A[row][(1, p, c)] = Im (T_p h_c)[a],
-//   B[o][(0, p, c)] = Re W[p][o][c],  B[o][(1, p, c)] = -Im W,  B[C_out + o][(0, p, c)] = Im W,
-//   B[C_out + o][(1, p, c)] = Re W,   D[row][o] = Re out_o[a],  D[row][C_out + o] = Im out_o[a].
-// A CTA of 128 threads covers 42 (site, sample) pairs x 3 colours (rows 126, 127 are zero); each
-// thread transports one colour of its pair (the three threads of a pair read the same neighbour
-// channels and link, mostly from L1) and writes its A row to shared memory in the canonical
-// K-major layout; one thread issues the K / 16 MMAs (M = 128, N = 16).
-constexpr int kNNPairs = 42;
+// accumulation in tensor memory).  The mixing is a GEMM per colour a whose rows are the
+// (site, sample) pairs -- the weights do not mix colours -- with K = (path, re / im part, input
+// channel) and N = (re / im part, output channel):
+//   A_a[q][(p, 0, c)] = Re (T_p h_c)(q)[a],  A_a[q][(p, 1, c)] = Im (T_p h_c)(q)[a],
+//   B[o][(p, 0, c)] = Re W[p][o][c],  B[o][(p, 1, c)] = -Im W,  B[C_out + o][(p, 0, c)] = Im W,
+//   B[C_out + o][(p, 1, c)] = Re W,   D_a[q][o] = Re out_o(q)[a],  D_a[q][C_out + o] = Im out_o(q)[a].
+//
+// Persistent, warp-specialised CTA of 160 threads over tiles of 128 pairs:
+//   warps 0-3 (one thread per pair, row = thread) transport every input channel along one path
+//     chunk (one path for C_in = 8, two for C_in = 4: 16 K columns per colour) and write the three
+//     colours' rows into a ring of kRing chunk buffers; after the tile's last chunk they read the
+//     FP32 result rows out of tensor memory and store them;
+//   warp 4 allocates tensor memory and, one lane, issues the three MMAs (M = 128, N = 16, K = 16)
+//     of each staged chunk, accumulating into one of two tensor-memory result buffers (so the
+//     next tile's MMAs overlap the previous tile's read-out).
+// Hand-offs are mbarriers: full[s] (128 producer arrivals) / empty[s] (MMA completion) per ring
+// slot, dfull[d] (MMA completion) / dempty[d] (128 producer arrivals) per result buffer.  Every wait has an
+// iteration limit; a wait that runs out raises a CTA flag that stops every loop, the kernel
+// counts it in g_nn_tc_timeouts, waits (bounded) for its MMAs in flight and frees its tensor
+// memory before returning.
+constexpr int kNNTile = 128;                      // pairs per tile (MMA M)
+constexpr int kRing = 4;                          // staged chunks in flight
+constexpr int kChunkColour = kNNTile * 16 * 2;    // bytes of one colour's 128 x 16 BF16 chunk
+constexpr int kChunkBytes = 3 * kChunkColour;     // one ring slot
 constexpr int kNNWaitLimit = 1 << 22;
+constexpr int kNNThreads = 160;
 __device__ int g_nn_tc_timeouts;
 
 template <int CIN>
+constexpr int nn_tc_chunks() {
+  return CIN == 8 ? NN_PATHS : (NN_PATHS + 1) / 2;
+}
+template <int CIN>
 constexpr int nn_tc_k() {
-  return (2 * NN_PATHS * CIN + 15) / 16 * 16;
+  return 16 * nn_tc_chunks<CIN>();
 }
 
-// (T_p h_c)(x)[a] for every input channel c: one colour of the transported channels of one path.
-template <int C>
-LQCD_D bool path_colour(const NNGeo& G, const float2* h, int p, int par, long cb, int x, int y, int z, int t, int n,
-                        int a, cplx<float> (&th)[C]) {
-  const Geom& g = G.g;
-  const long V = 2 * g.Vh;
-  const long s = x + (long)g.Lx * (y + (long)g.Ly * (z + (long)g.Lz * t));
-  long sn = s;
-  int coef = 1;
-  const int mu = (p - 1) & 3;
-  const bool fwd = p >= 1 && p <= 4;
-  if (p != 0) {
-    const int cm = mu == 0 ? x : (mu == 1 ? y : (mu == 2 ? z : t));
-    const int Lm = mu == 0 ? g.Lx : (mu == 1 ? g.Ly : (mu == 2 ? g.Lz : g.Lt));
-    const long sm = mu == 0 ? 1 : (mu == 1 ? g.Lx : (mu == 2 ? (long)g.Lx * g.Ly : (long)g.Lx * g.Ly * g.Lz));
-    if (fwd) {
-      sn = s + ((cm + 1 == Lm) ? sm * (1 - Lm) : sm);
-      if (mu == 3) coef = __ldg(G.tc + t);
-    } else {
-      sn = s + ((cm == 0) ? sm * (Lm - 1) : -sm);
-      if (mu == 3) coef = __ldg(G.tc + (t == 0 ? g.Lt - 1 : t - 1));
-    }
-    if (coef == 0) return false;
-  }
-  const int npar = p == 0 ? par : 1 - par;
-  const long nse = (long)npar * g.Vh + (sn >> 1);
-  if (p == 0) {
-#pragma unroll
-    for (int c = 0; c < C; c++) {
-      const float2 v = __ldg(h + ((long)(c * 3 + a) * V + nse) * G.N + n);
-      th[c] = {v.x, v.y};
-    }
-    return true;
-  }
-  cplx<float> u[3][3];
-  if (fwd)
-    load_link<P32>(G.U, g.Vh, mu, par, cb, u);
-  else
-    load_link<P32>(G.U, g.Vh, mu, 1 - par, sn >> 1, u);
-  const float cf = (float)coef;
-#pragma unroll
-  for (int c = 0; c < C; c++) {
-    cplx<float> acc = {0.f, 0.f};
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-      const float2 v = __ldg(h + ((long)(c * 3 + b) * V + nse) * G.N + n);
-      const cplx<float> hv = {v.x, v.y};
-      acc = fwd ? cfma(u[a][b], hv, acc) : cjfma(u[b][a], hv, acc);
-    }
-    th[c] = cf * acc;
-  }
-  return true;
+LQCD_D uint32_t bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
 }
+
+LQCD_D bool wait_or_flag(uint64_t* mbar, uint32_t parity, volatile int* fail) {
+  if (*fail) return false;
+  if (tc::mbar_wait(mbar, parity, kNNWaitLimit)) return true;
+  *fail = 1;
+  return false;
+}
+
+// Tile order.  Sites are visited slab by slab, a slab being Bz consecutive z-planes of one
+// timeslice (slabs ordered by z-block, then t), each slab as alternating even / odd tiles of 128
+// (site, sample) pairs.  Bz is chosen so that three slabs' input channels fit in L2, so a site's
+// channels, read as the centre and as a neighbour in every direction (the z-hops across a block
+// edge excepted), come from DRAM about once per layer.
+struct NNTiles {
+  int Bz;      // z-planes per slab
+  long tps;    // tiles per parity per slab
+  long ntiles; // all tiles
+};
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) k_nn_layer_tc(const float2* in, float2* out, const __nv_bfloat162* W,
-                                                     NNGeo G) {
+__global__ void __launch_bounds__(kNNThreads, 3) k_nn_layer_tc(const float2* in, float2* out,
+                                                               const __nv_bfloat162* W, NNGeo G, NNTiles TL) {
+  constexpr int NCH = nn_tc_chunks<CIN>();
   constexpr int K = nn_tc_k<CIN>();
-  constexpr int KH = NN_PATHS * CIN;  // offset of the imaginary parts in K
   extern __shared__ __align__(128) unsigned char nn_sm[];
-  unsigned char* sA = nn_sm;                 // 128 x K bf16
-  unsigned char* sB = nn_sm + 128 * K * 2;   // 16 x K bf16
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 16 * K * 2);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(mbar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* ring = nn_sm;                         // [kRing][3 colours][128 x 16] BF16
+  unsigned char* sB = ring + kRing * kChunkBytes;      // 16 x K BF16
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 16 * K * 2);
+  uint64_t* full = bars;                               // [kRing]
+  uint64_t* empty = bars + kRing;                      // [kRing]
+  uint64_t* dfull = bars + 2 * kRing;                  // [2]
+  uint64_t* dempty = bars + 2 * kRing + 2;             // [2]
+  uint64_t* drain = bars + 2 * kRing + 4;              // [1] (failure path)
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 2 * kRing + 5);
+  volatile int* fail = reinterpret_cast<volatile int*>(tbase + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long V = 2 * G.g.Vh;
-  const long npairs = V * G.N;
-  // weights -> B (zero where N or K is padding)
-  for (int e = tid; e < 16 * K; e += 128) {
+  const long slab_cb = (long)G.g.Lxh * G.g.Ly * TL.Bz;  // sites of one parity in a slab
+  const long slab_pairs = slab_cb * G.N;
+  const long ntiles = TL.ntiles;
+
+  // weights -> B in the K-major canonical layout (zero where N is padding)
+  for (int e = tid; e < 16 * K; e += kNNThreads) {
     const int j = e / K, k = e - j * K;
     float v = 0.f;
-    if (j < 2 * COUT && k < 2 * KH) {
-      const int part = k / KH, pc = k - part * KH, pth = pc / CIN, c = pc - pth * CIN;
+    const int pth = k / (2 * CIN), r = k - pth * 2 * CIN, part = r / CIN, c = r - part * CIN;
+    if (j < 2 * COUT && pth < NN_PATHS) {
       const int o = j % COUT, im_out = j / COUT;
       const float2 w = __bfloat1622float2(W[(pth * COUT + o) * CIN + c]);
       v = im_out == 0 ? (part == 0 ? w.x : -w.y) : (part == 0 ? w.y : w.x);
     }
     *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j, k, K)) = __float2bfloat16(v);
   }
-  // this thread's row: pair q, colour a
-  const int lp = tid / 3, a = tid - 3 * lp;
-  const long q = (long)blockIdx.x * kNNPairs + lp;
-  const bool valid = tid < 3 * kNNPairs && q < npairs;
-  long se = 0;
-  int n = 0;
-  if (valid) {
-    se = q / G.N;
-    n = (int)(q - se * G.N);
-    int par, x, y, z, t;
-    long cb;
-    nn_site(G, se, par, cb, x, y, z, t);
-#pragma unroll 1
-    for (int p = 0; p < NN_PATHS; p++) {
-      cplx<float> th[CIN];
-      if (!path_colour<CIN>(G, in, p, par, cb, x, y, z, t, n, a, th)) {
-#pragma unroll
-        for (int c = 0; c < CIN; c++) th[c] = {0.f, 0.f};
-      }
-#pragma unroll
-      for (int c = 0; c < CIN; c++) {
-        *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(tid, p * CIN + c, K)) = __float2bfloat16(th[c].re);
-        *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(tid, KH + p * CIN + c, K)) =
-            __float2bfloat16(th[c].im);
-      }
+  if (tid == 0) {
+    for (int i = 0; i < kRing; i++) {
+      tc::mbar_init(full + i, 128);
+      tc::mbar_init(empty + i, 1);
     }
-    for (int k = 2 * KH; k < K; k++)
-      *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(tid, k, K)) = __float2bfloat16(0.f);
-  } else {
-    for (int k = 0; k < K; k++)
-      *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(tid, k, K)) = __float2bfloat16(0.f);
+    for (int i = 0; i < 2; i++) {
+      tc::mbar_init(dfull + i, 1);
+      tc::mbar_init(dempty + i, 128);
+    }
+    tc::mbar_init(drain, 1);
+    *fail = 0;
   }
-  if (warp == 0) tc::tmem_alloc(tbase, 32);
-  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (warp == 4) tc::tmem_alloc(tbase, 128);
   tc::fence_proxy_async();
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tbase;
-  if (tid == 0) {
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 16);
-    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+
+  if (warp < 4) {  // ---------------------------------------------------------------- producers
+    long it = 0;      // tiles done by this CTA
+    long chunk = 0;   // chunks staged by this CTA
+    for (long tile = blockIdx.x; tile < ntiles && !*fail; tile += gridDim.x, it++) {
+      const long sl = tile / (2 * TL.tps), r = tile - sl * 2 * TL.tps;
+      const long q = (r >> 1) * kNNTile + tid;  // pair within the slab's sites of parity r & 1
+      const bool valid = q < slab_pairs;
+      long se = 0, cb = 0;
+      int n = 0, par = 0, x = 0, y = 0, z = 0, t = 0;
+      if (valid) {
+        const long zb = sl / G.g.Lt, ts = sl - zb * G.g.Lt;
+        const long cb0 = (long)G.g.Lxh * G.g.Ly * (zb * TL.Bz + (long)G.g.Lz * ts);
+        const long i = q / G.N;
+        n = (int)(q - i * G.N);
+        se = (r & 1) * G.g.Vh + cb0 + i;
+        nn_site(G, se, par, cb, x, y, z, t);
+      }
+      const uint32_t roff = (uint32_t)((tid >> 3) * 256 + (tid & 7) * 16);  // row offset in a chunk
+      for (int ch = 0; ch < NCH; ch++, chunk++) {
+        const int slot = (int)(chunk % kRing);
+        const long use = chunk / kRing;
+        if (use > 0 && !wait_or_flag(empty + slot, (uint32_t)((use - 1) & 1), fail)) break;
+        unsigned char* buf = ring + slot * kChunkBytes + roff;
 #pragma unroll
-    for (int ks = 0; ks < K / 16; ks++)
-      tc::mma_bf16(tmem, tc::smem_desc(a0 + ks * 256, 128, (K / 8) * 128),
-                   tc::smem_desc(b0 + ks * 256, 128, (K / 8) * 128), idesc, ks > 0);
-    tc::mma_commit(mbar);
-  }
-  const bool ok = tc::mbar_wait(mbar, 0, kNNWaitLimit);
-  tc::fence_after_sync();
-  if (ok) {
-    float v[16];
-    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
-    if (valid) {
+        for (int h = 0; h < 16 / (2 * CIN); h++) {  // paths of this chunk
+          const int p = ch * (16 / (2 * CIN)) + h;
+          cplx<float> th[CIN][3];
+          bool on = false;
+          if (valid && p < NN_PATHS) on = path_vectors<CIN>(G, in, p, par, cb, x, y, z, t, n, th);
+          if (!on) {
 #pragma unroll
-      for (int o = 0; o < COUT; o++) out[((long)(o * 3 + a) * V + se) * G.N + n] = make_float2(v[o], v[COUT + o]);
+            for (int c = 0; c < CIN; c++)
+#pragma unroll
+              for (int a = 0; a < 3; a++) th[c][a] = {0.f, 0.f};
+          }
+#pragma unroll
+          for (int a = 0; a < 3; a++) {
+            if (CIN == 8) {  // re of the 8 channels in core column 0, im in core column 1
+              uint4 vr, vi;
+              vr.x = bf16x2(th[0][a].re, th[1 % CIN][a].re);
+              vr.y = bf16x2(th[2 % CIN][a].re, th[3 % CIN][a].re);
+              vr.z = bf16x2(th[4 % CIN][a].re, th[5 % CIN][a].re);
+              vr.w = bf16x2(th[6 % CIN][a].re, th[7 % CIN][a].re);
+              vi.x = bf16x2(th[0][a].im, th[1 % CIN][a].im);
+              vi.y = bf16x2(th[2 % CIN][a].im, th[3 % CIN][a].im);
+              vi.z = bf16x2(th[4 % CIN][a].im, th[5 % CIN][a].im);
+              vi.w = bf16x2(th[6 % CIN][a].im, th[7 % CIN][a].im);
+              *reinterpret_cast<uint4*>(buf + a * kChunkColour) = vr;
+              *reinterpret_cast<uint4*>(buf + a * kChunkColour + 128) = vi;
+            } else {  // 4 channels: re 0..3 then im 0..3 in core column h
+              uint4 v;
+              v.x = bf16x2(th[0][a].re, th[1 % CIN][a].re);
+              v.y = bf16x2(th[2 % CIN][a].re, th[3 % CIN][a].re);
+              v.z = bf16x2(th[0][a].im, th[1 % CIN][a].im);
+              v.w = bf16x2(th[2 % CIN][a].im, th[3 % CIN][a].im);
+              *reinterpret_cast<uint4*>(buf + a * kChunkColour + h * 128) = v;
+            }
+          }
+        }
+        tc::fence_proxy_async();  // these generic-proxy writes, before the MMA reads them
+        tc::mbar_arrive(full + slot);
+      }
+      if (*fail) break;
+      // read-out of this tile's result buffer
+      const int d = (int)(it & 1);
+      if (!wait_or_flag(dfull + d, (uint32_t)((it >> 1) & 1), fail)) break;
+      tc::fence_after_sync();
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * 64 + a * 16), v);
+        if (valid) {
+#pragma unroll
+          for (int o = 0; o < COUT; o++) out[((long)(o * 3 + a) * V + se) * G.N + n] = make_float2(v[o], v[COUT + o]);
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(dempty + d);
     }
-  } else if (tid == 0) {
-    atomicAdd(&g_nn_tc_timeouts, 1);
+  } else {  // ---------------------------------------------------------------------- MMA issuer
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 16);
+    const uint32_t r0 = tc::smem_u32(ring), b0 = tc::smem_u32(sB);
+    long it = 0, chunk = 0;
+    for (long tile = blockIdx.x; tile < ntiles && !*fail; tile += gridDim.x, it++) {
+      const int d = (int)(it & 1);
+      if (it >= 2 && !wait_or_flag(dempty + d, (uint32_t)(((it >> 1) - 1) & 1), fail)) break;
+      tc::fence_after_sync();
+      for (int ch = 0; ch < NCH; ch++, chunk++) {
+        const int slot = (int)(chunk % kRing);
+        if (!wait_or_flag(full + slot, (uint32_t)((chunk / kRing) & 1), fail)) break;
+        tc::fence_after_sync();
+        if (lane == 0) {
+#pragma unroll
+          for (int a = 0; a < 3; a++)
+            tc::mma_bf16(tmem + (uint32_t)(d * 64 + a * 16),
+                         tc::smem_desc(r0 + slot * kChunkBytes + a * kChunkColour, 128, 256),
+                         tc::smem_desc(b0 + ch * 256, 128, (K / 8) * 128), idesc, ch > 0);
+          tc::mma_commit(empty + slot);
+          if (ch == NCH - 1) tc::mma_commit(dfull + d);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  if (*fail) {
+    if (tid == 0) atomicAdd(&g_nn_tc_timeouts, 1);
+    // let MMAs already issued finish before the tensor memory is freed: one more commit, waited
+    // on with a limit
+    if (warp == 4) {
+      if (lane == 0) tc::mma_commit(drain);
+      __syncwarp();
+      tc::mbar_wait(drain, 0, kNNWaitLimit);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 32);
+  tc::fence_after_sync();
+  if (warp == 4) tc::tmem_dealloc(tmem, 128);
 }
 
 template <int CIN, int COUT>
 static size_t nn_tc_smem() {
-  constexpr int K = nn_tc_k<CIN>();
-  return (size_t)128 * K * 2 + (size_t)16 * K * 2 + 16;
+  return (size_t)kRing * kChunkBytes + (size_t)16 * nn_tc_k<CIN>() * 2 + (2 * kRing + 5) * 8 + 16;
 }
+
+// Three CTAs per SM: 128 registers x 160 threads each, 52-54 KB of shared memory each, and
+// 3 x 128 of the SM's 512 tensor-memory columns.
+constexpr int kNNCtasPerSM = 3;
 
 template <int CIN, int COUT>
 static void tc_open() {
-  cudaFuncSetAttribute(k_nn_layer_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)nn_tc_smem<CIN, COUT>());
+  const int shm = (int)nn_tc_smem<CIN, COUT>();
+  cudaFuncSetAttribute(k_nn_layer_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_nn_layer_tc<CIN, COUT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
 }
 
-// Raise the shared-memory limit of every tensor-core layer instantiation once, before any launch
-// (and so before any stream capture).
+// Raise the shared-memory limit of every tensor-core layer instantiation and size its
+// persistent grid once, before any launch (and so before any stream capture).
+static int g_tc_ctas = 148 * kNNCtasPerSM;
 static void tc_open_all() {
   static bool done = false;
   if (done) return;
   done = true;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  g_tc_ctas = sms * kNNCtasPerSM;
   tc_open<4, 8>();
   tc_open<8, 8>();
   tc_open<8, 4>();
@@ -354,12 +445,19 @@ static void tc_open_all() {
 }
 
 template <int CIN, int COUT>
-static void tc_launch(const float2* in, float2* out, const __nv_bfloat162* W, const NNGeo& G, cudaStream_t st) {
+static void tc_launch(const float2* in, float2* out, const __nv_bfloat162* W, const NNGeo& G,
+                      cudaStream_t st) {
   tc_open_all();
-  const size_t shm = nn_tc_smem<CIN, COUT>();
-  const long npairs = 2 * G.g.Vh * (long)G.N;
-  const long blocks = (npairs + kNNPairs - 1) / kNNPairs;
-  k_nn_layer_tc<CIN, COUT><<<blocks, 128, shm, st>>>(in, out, W, G);
+  // largest Bz dividing Lz whose slab (both parities) holds at most 28 MB of input channels
+  const double site_bytes = (double)CIN * 3 * G.N * sizeof(float2);
+  NNTiles TL;
+  TL.Bz = 1;
+  for (int b = 1; b <= G.g.Lz; b++)
+    if (G.g.Lz % b == 0 && (double)G.g.Lx * G.g.Ly * b * site_bytes <= 28e6) TL.Bz = b;
+  TL.tps = ((long)G.g.Lxh * G.g.Ly * TL.Bz * G.N + kNNTile - 1) / kNNTile;
+  TL.ntiles = (long)(G.g.Lz / TL.Bz) * G.g.Lt * 2 * TL.tps;
+  const long blocks = TL.ntiles < g_tc_ctas ? TL.ntiles : g_tc_ctas;
+  k_nn_layer_tc<CIN, COUT><<<(unsigned)blocks, kNNThreads, nn_tc_smem<CIN, COUT>(), st>>>(in, out, W, G, TL);
   count_launch();
 }
 
@@ -386,8 +484,13 @@ int nn_tc_timeouts(bool reset) {
 }
 
 // T[p][k][se][n] = (T_p in)[k] for every path (training: the weight gradient needs them)
-template <int C>
-__global__ void k_nn_transport(const float2* in, float2* T, NNGeo G) {
+LQCD_D void store_t(float2* T, long i, cplx<float> v) { T[i] = make_float2(v.re, v.im); }
+LQCD_D void store_t(__nv_bfloat162* T, long i, cplx<float> v) { T[i] = __floats2bfloat162_rn(v.re, v.im); }
+LQCD_D float2 load_t(const float2* T, long i) { return T[i]; }
+LQCD_D float2 load_t(const __nv_bfloat162* T, long i) { return __bfloat1622float2(T[i]); }
+
+template <int C, typename TT>
+__global__ void k_nn_transport(const float2* in, TT* T, NNGeo G) {
   const long V = 2 * G.g.Vh;
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long se = tid / G.N;
@@ -404,14 +507,13 @@ __global__ void k_nn_transport(const float2* in, float2* T, NNGeo G) {
     for (int c = 0; c < C; c++)
 #pragma unroll
       for (int a = 0; a < 3; a++)
-        T[((long)p * C * 3 + c * 3 + a) * VN + se * G.N + n] =
-            on ? make_float2(th[c][a].re, th[c][a].im) : make_float2(0.f, 0.f);
+        store_t(T, ((long)p * C * 3 + c * 3 + a) * VN + se * G.N + n, on ? th[c][a] : cplx<float>{0.f, 0.f});
   }
 }
 
 // partial[block][p][o][c] = sum over the block's site-samples of sum_a d_o[a] conj(T_p h_c[a])
-template <int CIN, int COUT>
-__global__ void k_nn_wgrad(const float2* T, const float2* d, float* partial, long VN, long per_block) {
+template <int CIN, int COUT, typename TT>
+__global__ void k_nn_wgrad(const TT* T, const float2* d, float* partial, long VN, long per_block) {
   constexpr int TS = 16;
   extern __shared__ float2 smw[];
   float2* Ds = smw;                       // [TS][COUT*3]
@@ -431,7 +533,7 @@ __global__ void k_nn_wgrad(const float2* T, const float2* d, float* partial, lon
     for (int e = threadIdx.x; e < TS * NN_PATHS * CIN * 3; e += blockDim.x) {
       int i = e / (NN_PATHS * CIN * 3), k = e % (NN_PATHS * CIN * 3);
       long q = qb + i;
-      Ts[e] = q < q1 ? T[(long)k * VN + q] : make_float2(0.f, 0.f);
+      Ts[e] = q < q1 ? load_t(T, (long)k * VN + q) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     if (me < nthr) {
@@ -543,14 +645,16 @@ __global__ void k_nn_to_bf16(const float2* W, __nv_bfloat162* W16, int n) {
   if (i < n) W16[i] = __floats2bfloat162_rn(W[i].x, W[i].y);
 }
 
-// Adjoint weights: Wa[p][c][o] = conj(W[pbar][o][c]) with pbar the reverse path.
-__global__ void k_nn_adjoint_weights(const float2* W, float2* Wa, int cin, int cout) {
+// Adjoint weights: Wa[p][c][o] = conj(W[pbar][o][c]) with pbar the reverse path (FP32 and, for the
+// tensor-core backward pass, a BF16 copy).
+__global__ void k_nn_adjoint_weights(const float2* W, float2* Wa, __nv_bfloat162* Wa16, int cin, int cout) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NN_PATHS * cin * cout) return;
   int p = i / (cin * cout), c = (i / cout) % cin, o = i % cout;
   int pb = p == 0 ? 0 : (p <= 4 ? p + 4 : p - 4);
   float2 w = W[(pb * cout + o) * cin + c];
   Wa[i] = make_float2(w.x, -w.y);
+  if (Wa16) Wa16[i] = __floats2bfloat162_rn(w.x, -w.y);
 }
 
 // even-half FP32 spinor [6 float4][cb][nrhs] <-> NN field (4 spin channels, full lattice)
@@ -751,8 +855,12 @@ int nn_reserve(lqcd_ctx* c, int nrhs) {
 
 // Forward + loss + backward (and optionally Adam) on NN-layout input/target of N samples.
 // Returns the loss through *loss; grad_host (may be NULL) receives dL/dconj(W) as float pairs.
+// bf16: the training kernels of the BF16 path -- forward and backward-data layers on the tensor
+// cores with BF16 weights and activations (FP32 accumulation), the transported activations kept
+// in BF16 for the weight gradient (accumulated in FP32), FP32 master weights and Adam.  Otherwise
+// everything in FP32 (the reference gradients of lqcd_nn_loss_grad).
 static int nn_step(lqcd_ctx* c, const float2* h0, const float2* tgt, int N, int domain, int even_only,
-                   double* loss, float* grad_host, bool adam, float lr) {
+                   double* loss, float* grad_host, bool adam, float lr, bool bf16) {
   cudaStream_t st = c->work;
   const Geom& g = c->g;
   const long V = 2 * g.Vh, VN = V * N;
@@ -760,12 +868,15 @@ static int nn_step(lqcd_ctx* c, const float2* h0, const float2* tgt, int N, int 
   // activations h1..h4 (up to 8 channels) and transported copies of h0..h3
   float2* act[NN_LAYERS + 1];
   act[0] = (float2*)h0;
-  float2* T[NN_LAYERS];
+  void* T[NN_LAYERS];
+  const size_t tsz = bf16 ? sizeof(__nv_bfloat162) : sizeof(float2);
   for (int l = 0; l < NN_LAYERS; l++) {
     act[l + 1] = (float2*)ws_get(c, "nn_act" + std::to_string(l), (size_t)NN_W[l + 1] * 3 * VN * sizeof(float2));
-    T[l] = (float2*)ws_get(c, "nn_T" + std::to_string(l), (size_t)NN_PATHS * NN_W[l] * 3 * VN * sizeof(float2));
+    T[l] = ws_get(c, "nn_T" + std::to_string(l), (size_t)NN_PATHS * NN_W[l] * 3 * VN * tsz);
     if (!act[l + 1] || !T[l]) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory (training)");
   }
+  __nv_bfloat162* Wa16 = (__nv_bfloat162*)ws_get(c, "nn_Wadj16", (size_t)NN_PATHS * 64 * sizeof(__nv_bfloat162));
+  if (!Wa16) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
   float2* d0 = (float2*)ws_get(c, "nn_d0", (size_t)24 * VN * sizeof(float2));
   float2* d1 = (float2*)ws_get(c, "nn_d1", (size_t)24 * VN * sizeof(float2));
   float2* Wa = (float2*)ws_get(c, "nn_Wadj", (size_t)NN_PATHS * 64 * sizeof(float2));
@@ -777,13 +888,22 @@ static int nn_step(lqcd_ctx* c, const float2* h0, const float2* tgt, int N, int 
   const int tpb = 128;
   const long nb = (VN + tpb - 1) / tpb;
   for (int l = 0; l < NN_LAYERS; l++) {
-    if (NN_W[l] == 4)
-      k_nn_transport<4><<<nb, tpb, 0, st>>>(act[l], T[l], G);
-    else
-      k_nn_transport<8><<<nb, tpb, 0, st>>>(act[l], T[l], G);
+    if (bf16) {
+      if (NN_W[l] == 4)
+        k_nn_transport<4><<<nb, tpb, 0, st>>>(act[l], (__nv_bfloat162*)T[l], G);
+      else
+        k_nn_transport<8><<<nb, tpb, 0, st>>>(act[l], (__nv_bfloat162*)T[l], G);
+      layer_launch_tc(NN_W[l], NN_W[l + 1], act[l], act[l + 1],
+                      (const __nv_bfloat162*)c->nn_w16 + nn_layer_offset(l), G, st);
+    } else {
+      if (NN_W[l] == 4)
+        k_nn_transport<4><<<nb, tpb, 0, st>>>(act[l], (float2*)T[l], G);
+      else
+        k_nn_transport<8><<<nb, tpb, 0, st>>>(act[l], (float2*)T[l], G);
+      layer_launch<float2>(NN_W[l], NN_W[l + 1], act[l], act[l + 1],
+                           (const float2*)c->nn_weights + nn_layer_offset(l), G, st);
+    }
     count_launch();
-    layer_launch<float2>(NN_W[l], NN_W[l + 1], act[l], act[l + 1], (const float2*)c->nn_weights + nn_layer_offset(l),
-                         G, st);
   }
   k_nn_loss_partial<<<lblocks, 256, 0, st>>>(act[NN_LAYERS], tgt, VN, g.Vh, N, even_only, lpart);
   k_nn_loss_final<<<1, 1, 0, st>>>(lpart, lblocks, sums);
@@ -798,19 +918,33 @@ static int nn_step(lqcd_ctx* c, const float2* h0, const float2* tgt, int N, int 
     float* wpart = (float*)ws_get(c, "nn_wpart", (size_t)nblk * 2 * NN_PATHS * 64 * sizeof(float));
     if (!wpart) return set_error(c, LQCD_ERR_OOM, "nn: out of device memory");
     const size_t shm = (size_t)16 * (cout * 3 + NN_PATHS * cin * 3) * sizeof(float2);
-    if (cin == 4)
-      k_nn_wgrad<4, 8><<<nblk, nval, shm, st>>>(T[l], dcur, wpart, VN, per_block);
-    else if (cout == 8)
-      k_nn_wgrad<8, 8><<<nblk, nval, shm, st>>>(T[l], dcur, wpart, VN, per_block);
-    else
-      k_nn_wgrad<8, 4><<<nblk, nval, shm, st>>>(T[l], dcur, wpart, VN, per_block);
+    if (bf16) {
+      const __nv_bfloat162* Tl = (const __nv_bfloat162*)T[l];
+      if (cin == 4)
+        k_nn_wgrad<4, 8><<<nblk, nval, shm, st>>>(Tl, dcur, wpart, VN, per_block);
+      else if (cout == 8)
+        k_nn_wgrad<8, 8><<<nblk, nval, shm, st>>>(Tl, dcur, wpart, VN, per_block);
+      else
+        k_nn_wgrad<8, 4><<<nblk, nval, shm, st>>>(Tl, dcur, wpart, VN, per_block);
+    } else {
+      const float2* Tl = (const float2*)T[l];
+      if (cin == 4)
+        k_nn_wgrad<4, 8><<<nblk, nval, shm, st>>>(Tl, dcur, wpart, VN, per_block);
+      else if (cout == 8)
+        k_nn_wgrad<8, 8><<<nblk, nval, shm, st>>>(Tl, dcur, wpart, VN, per_block);
+      else
+        k_nn_wgrad<8, 4><<<nblk, nval, shm, st>>>(Tl, dcur, wpart, VN, per_block);
+    }
     k_nn_sum_blocks<<<(2 * nval + 255) / 256, 256, 0, st>>>(wpart, nblk, 2 * nval, grad + 2 * nn_layer_offset(l));
     count_launch(2);
     if (l > 0) {  // delta of the layer input: adjoint layer
       k_nn_adjoint_weights<<<(nval + 127) / 128, 128, 0, st>>>((const float2*)c->nn_weights + nn_layer_offset(l), Wa,
-                                                               cin, cout);
+                                                               Wa16, cin, cout);
       count_launch();
-      layer_launch<float2>(cout, cin, dcur, dnext, Wa, G, st);
+      if (bf16)
+        layer_launch_tc(cout, cin, dcur, dnext, Wa16, G, st);
+      else
+        layer_launch<float2>(cout, cin, dcur, dnext, Wa, G, st);
       std::swap(dcur, dnext);
     }
   }
@@ -852,7 +986,7 @@ int nn_apply_lex(lqcd_ctx* c, const float2* in_dev, float2* out_dev, int N, int 
 }
 
 int nn_loss_grad_lex(lqcd_ctx* c, const float2* in_dev, const float2* tgt_dev, int N, int domain, int even_only,
-                     double* loss, float* grad_host) {
+                     double* loss, float* grad_host, bool bf16) {
   if (!c->nn_weights) return set_error(c, LQCD_ERR_STATE, "nn: no weights");
   const long VN = 2 * c->g.Vh * (long)N;
   float2* h0 = (float2*)ws_get(c, "nn_h0", (size_t)12 * VN * sizeof(float2));
@@ -861,7 +995,7 @@ int nn_loss_grad_lex(lqcd_ctx* c, const float2* in_dev, const float2* tgt_dev, i
   k_nn_lex<<<(VN + 255) / 256, 256, 0, c->work>>>(in_dev, h0, c->g, N, 1, c->d_coord);
   k_nn_lex<<<(VN + 255) / 256, 256, 0, c->work>>>(tgt_dev, tg, c->g, N, 1, c->d_coord);
   count_launch(2);
-  return nn_step(c, h0, tg, N, domain, even_only, loss, grad_host, false, 0.f);
+  return nn_step(c, h0, tg, N, domain, even_only, loss, grad_host, false, 0.f, bf16);
 }
 
 // Training pairs (r, e) with M e = r for the even-odd Schur operator M, from the plain FP64
@@ -923,7 +1057,7 @@ int nn_train(lqcd_ctx* c, int n_pairs, int epochs, int batch, double lr, int dom
       for (int kk = 0; kk < nk; kk++) {
         double L = 0;
         int rc = nn_step(c, R + (size_t)kk * 12 * V * batch, E + (size_t)kk * 12 * V * batch, batch, domain, 1, &L,
-                         nullptr, true, (float)lr);
+                         nullptr, true, (float)lr, true);
         if (rc != LQCD_OK) return rc;
         acc += L;
       }

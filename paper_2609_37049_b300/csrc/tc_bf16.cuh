@@ -17,7 +17,7 @@
 //   instruction descriptor: [4,6) D format (1 = F32), [7,10) A format (1 = BF16),
 //                    [10,13) B format (1 = BF16), [15] A major (0 = K), [16] B major (0 = K),
 //                    [17,23) N >> 3, [24,29) M >> 4.
-// Every wait on an mbarrier has an iteration limit; a wait that runs out sets a flag the kernel
+// Every wait on an mbarrier has an iteration limit and a time limit; a wait that runs out sets a flag the kernel
 // reports, and the kernel still deallocates its tensor memory before it returns.
 #pragma once
 #include <cuda_bf16.h>
@@ -79,19 +79,36 @@ LQCD_D void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
 
-// Wait for phase `parity` of mbar to complete; false if it did not within `limit` polls.
+// One arrival on mbar (release: this thread's earlier writes are visible to whoever sees the
+// phase complete).
+LQCD_D void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Wait for phase `parity` of mbar to complete; false if it did not within `limit` polls or
+// about two seconds (global timer), whichever comes first.  Each poll may suspend the thread for
+// up to kSuspendNs (it resumes as soon as the phase completes), so a waiting warp takes no issue
+// slots from the warps it waits for.
+constexpr uint32_t kSuspendNs = 20000;
 LQCD_D bool mbar_wait(uint64_t* mbar, uint32_t parity, int limit) {
   const uint32_t a = smem_u32(mbar);
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   for (int i = 0; i < limit; i++) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
+    if ((i & 15) == 15) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 2000000000ull) return false;
+    }
   }
   return false;
 }

@@ -35,7 +35,7 @@ EXPORTED = [
     "lqcd_phase_times", "lqcd_nn_num_weights", "lqcd_nn_set_weights", "lqcd_nn_get_weights", "lqcd_nn_apply",
     "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant", "lqcd_schur_apply",
     "lqcd_conn_correlator", "lqcd_nr_estimator", "lqcd_ape_smear", "lqcd_smeared_links",
-    "lqcd_perambulator_cols", "lqcd_window_average", "lqcd_nn_apply_tc",
+    "lqcd_perambulator_cols", "lqcd_window_average", "lqcd_nn_apply_tc", "lqcd_nn_loss_grad_bf16",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -143,6 +143,7 @@ def load_library(path=_LIB_PATH):
         "lqcd_nn_apply_tc": (ip, [vp, vp, vp, ip, ip, ip]),
         "lqcd_nn_loss_grad": (ip, [vp, vp, vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_double), vp]),
         "lqcd_nn_train": (ip, [vp, ip, ip, ip, ctypes.c_double, ip, ctypes.c_uint, vp]),
+        "lqcd_nn_loss_grad_bf16": (ip, [vp, vp, vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_double), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -390,12 +391,13 @@ class Context:
         return self._check(_lib.lqcd_nn_apply_tc(self.h, _ptr(x, np.complex64), _ptr(out, np.complex64), x.shape[0],
                                                  int(domain), _where(x, out)))
 
-    def nn_loss_grad(self, x, target, domain=False, even_only=False):
+    def nn_loss_grad(self, x, target, domain=False, even_only=False, bf16=False):
+        """Loss and dL/dconj(W): FP32 kernels, or (bf16=True) the BF16 training kernels."""
         loss = ctypes.c_double()
         g = np.zeros(2 * _lib.lqcd_nn_num_weights(), dtype=np.float32)
-        self._check(_lib.lqcd_nn_loss_grad(self.h, _ptr(x, np.complex64), _ptr(target, np.complex64), x.shape[0],
-                                           int(domain), int(even_only), _where(x, target), ctypes.byref(loss),
-                                           ctypes.c_void_p(g.ctypes.data)))
+        f = _lib.lqcd_nn_loss_grad_bf16 if bf16 else _lib.lqcd_nn_loss_grad
+        self._check(f(self.h, _ptr(x, np.complex64), _ptr(target, np.complex64), x.shape[0], int(domain),
+                      int(even_only), _where(x, target), ctypes.byref(loss), ctypes.c_void_p(g.ctypes.data)))
         return loss.value, nn_unflatten(g)
 
     def nn_train(self, n_pairs, epochs, batch, lr, domain=False, seed=1):

@@ -87,6 +87,25 @@ def test_loss_and_gradient_match_oracle(even_only):
         assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
 
 
+def test_bf16_training_gradient_within_bound():
+    """The BF16 training kernels (tensor-core forward / backward-data layers, BF16 transported
+    activations) give the loss to BF16 rounding and a gradient within 3% (Frobenius, per layer) of
+    the FP64 oracle's."""
+    case = ROUGH
+    U = gauge(case, 82)
+    ctx = _ctx(case, U)
+    Ws = _bf16_safe(nn.init_weights(8, 0.3))
+    ctx.nn_set_weights(Ws)
+    x, tgt = _fields(case, 2, 4), _fields(case, 2, 5)
+    dims = case["dims"]
+    mask = (parity_table(dims) == 0).reshape(dims[3], dims[2], dims[1], dims[0]).astype(float)
+    L, G = ctx.nn_loss_grad(x, tgt, even_only=True, bf16=True)
+    Lo, Go = nn.loss_and_grad(Ws, fermion_links(U), x.astype(np.complex128), tgt.astype(np.complex128), mask)
+    assert abs(L - Lo) < 2e-2 * Lo
+    for g, go in zip(G, Go):
+        assert np.linalg.norm(g - go) < 3e-2 * np.linalg.norm(go)
+
+
 def test_training_lowers_loss_and_preconditions_fgcr():
     """Training on pairs from the plain solver lowers the loss; the trained network inside FGCR
     reaches FP64 true residual 1e-10 (checked with the oracle's operator) in fewer iterations than
