@@ -298,7 +298,7 @@ class Workload:
         from paper_2609_37049_b300 import autotune, default_params
         lq = self.lqcd
         self.tuning = autotune.tune(self.ctx, cache=os.path.join(tempfile.gettempdir(), "lqcd_tuning.json"),
-                                    precisions=(lq.LQCD_PREC_F32, lq.LQCD_PREC_F64),
+                                    precisions=(lq.LQCD_PREC_F32, lq.LQCD_PREC_F64, lq.LQCD_PREC_DF),
                                     blocks=(self.rhs_block // self.pipeline,))
         self.params = default_params(solver=lq.LQCD_SOLVER_MIXED, inner_prec=lq.LQCD_PREC_F32,
                                      rhs_block=self.rhs_block // self.pipeline, pipeline=self.pipeline,
@@ -606,8 +606,9 @@ def profile_dslash(args):
     ctx.gauge_upload(gauge_field(wl["dims"], wl["eps"], wl["gauge_seed"]), wl["kappa"], wl["csw"])
     nr = args.dslash_nrhs or (args.rhs_block or wl["rhs_block"])
     out = {}
-    for name, prec in (("f32", lqcd.LQCD_PREC_F32), ("f16", lqcd.LQCD_PREC_F16), ("f64", lqcd.LQCD_PREC_F64)):
-        for v in (range(3) if prec == lqcd.LQCD_PREC_F64 else range(5)):
+    for name, prec in (("f32", lqcd.LQCD_PREC_F32), ("f16", lqcd.LQCD_PREC_F16), ("f64", lqcd.LQCD_PREC_F64),
+                       ("df_res", lqcd.LQCD_PREC_DF)):
+        for v in (range(3) if prec in (lqcd.LQCD_PREC_F64, lqcd.LQCD_PREC_DF) else range(5)):
             if args.dslash_variant >= 0 and v != args.dslash_variant:
                 continue
             ctx.set_dslash_variant(prec, nr, v)

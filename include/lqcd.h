@@ -76,7 +76,9 @@ enum {
   LQCD_SOLVER_MIXED = 1,
   LQCD_SOLVER_FGCR_NN = 2
 };
-enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2 };
+/* LQCD_PREC_DF: FP64 fields with double-float arithmetic; used by the true-residual kernel only
+ * (lqcd_tune_dslash / lqcd_set_dslash_variant tune and set that kernel's launch variant). */
+enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2, LQCD_PREC_DF = 3 };
 
 typedef struct {
   double tol;        /* target true relative residual per RHS (and per domain); 0 -> 1e-10 */
@@ -98,6 +100,12 @@ typedef struct {
   int projection;    /* perambulator projection V^dag X: 0 double-float arithmetic (pairs of floats,
                         48-bit significands, FP64 accumulation every 512 terms) on the FP32 pipe;
                         1 native FP64.  Both agree to about 1e-13 relative */
+  int residual;      /* arithmetic of the defect correction's true residual b - D x (read from and
+                        written to the FP64 fields): 0 double-float (pairs of floats, 48-bit
+                        significands) on the FP32 pipe; 1 native FP64.  The double-float residual
+                        errs by about 1e-13 of ||b|| + ||D|| ||x||, far below any tolerance >= 1e-12,
+                        for entries of magnitude 2^-74 (5e-23) to 2^127; use 1 for fields outside
+                        that range */
 } lqcd_solve_params;
 
 typedef struct {
@@ -300,6 +308,9 @@ int lqcd_laplace_eigs(lqcd_ctx* ctx, int n_ev, double* V, double* lambda, int wh
  *   ms_per_launch:        average kernel duration [ms]
  *   algo_bytes_per_launch: Vh * (8 links + clover + 2 * nrhs spinors) in the stored formats
  *                          (ideal reuse: every input read once, output written once).
+ * With prec = LQCD_PREC_DF it times the defect correction's true-residual kernel instead,
+ * out = z - (A y - kappa H x) with x = y = z = the input, in double-float arithmetic on the FP64
+ * fields: algo_bytes_per_launch = Vh * (8 links + clover + 4 * nrhs FP64 spinors).
  * Fills the input with deterministic non-zero data.  Needs a gauge field.  Errors: INVALID_ARG. */
 int lqcd_dslash_bench(lqcd_ctx* ctx, int prec, int nrhs, int n_iter, int flush_l2, double* ms_per_launch,
                       double* algo_bytes_per_launch);
@@ -374,8 +385,9 @@ int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, 
  * clover copied once per site into shared memory, 32-bit indexing, register cap 80 (FP32 and
  * FP16, nrhs a power of two in [8, 128]); 4: the neighbour spinors staged in shared memory by
  * bulk asynchronous copies 3 hops ahead (FP32 and FP16, nrhs a multiple of 32).  Where a variant does
- * not apply it runs as variant 0.  FP64 has variants 0 / 1 / 2 with register caps 128 / 255 / 168.  All variants compute the same arithmetic in the
- * same order.  lqcd_set_dslash_variant
+ * not apply it runs as variant 0.  FP64 has variants 0 / 1 / 2 with register caps 128 / 255 / 168;
+ * LQCD_PREC_DF (the true-residual kernel, timed as such) variants 0 / 1 / 2 with caps 255 / 168 /
+ * 128.  All variants compute the same arithmetic in the same order.  lqcd_set_dslash_variant
  * installs a known choice (e.g. from a cache) without timing.  Errors: INVALID_ARG (variant
  * outside 0..4), STATE (no gauge), TIMEOUT (a staged copy did not complete within its wait
  * limit; the solvers report the same). */

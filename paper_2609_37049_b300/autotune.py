@@ -31,7 +31,7 @@ def _key(ctx):
 
 
 def _spinor_bytes(ctx, prec, nrhs):
-    per = {lqcd.LQCD_PREC_F64: 16, lqcd.LQCD_PREC_F32: 8, lqcd.LQCD_PREC_F16: 4}[prec]
+    per = {lqcd.LQCD_PREC_F64: 16, lqcd.LQCD_PREC_F32: 8, lqcd.LQCD_PREC_F16: 4, lqcd.LQCD_PREC_DF: 16}[prec]
     return ctx.volume // 2 * nrhs * 12 * per
 
 
@@ -44,7 +44,8 @@ def _device_budget():
         return 64 << 30
 
 
-def tune(ctx, cache=None, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F16, lqcd.LQCD_PREC_F64),
+def tune(ctx, cache=None, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F16, lqcd.LQCD_PREC_F64,
+                                      lqcd.LQCD_PREC_DF),
          blocks=CANDIDATE_BLOCKS, memory_budget=None, retune=False):
     """Tune (or load from `cache`) and install the launch choices on ctx; returns the choice dict.
     memory_budget (bytes; default 60% of the device memory) bounds the RHS blocks tried."""

@@ -360,6 +360,7 @@ void lqcd_default_params(lqcd_solve_params* p) {
   p->precond_iters = 6;
   p->pipeline = 1;
   p->projection = 0;
+  p->residual = 0;
 }
 
 int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
@@ -423,8 +424,6 @@ int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream) {
   {
     const char* tv = getenv("LQCD_PHASE_TIMING");
     c->timing = tv && tv[0] == '1';
-    const char* rp = getenv("LQCD_RES_PERSISTENT");
-    c->res_persistent = rp ? atoi(rp) : 0;
   }
   fill_tables(c);
   M4 G[16], Gt[16];
@@ -473,7 +472,7 @@ int lqcd_destroy(lqcd_ctx* c) {
   if (c->slot_stream) cudaStreamDestroy(c->slot_stream);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev_slot) cudaEventDestroy(c->ev_slot);
-  void* bufs[] = {c->U64, c->U32, c->U16, c->Usm, c->A64, c->Ainv64, c->Ainv32, c->Ainv16, c->A32,
+  void* bufs[] = {c->U64, c->U32, c->U16, c->Usm, c->A64, c->Ainv64, c->Ainv32, c->Ainv16, c->A32, c->Udf, c->Adf,
                   c->d_tc_full, c->d_tc_dom, c->d_seg_full, c->d_seg_dom, c->d_gamma, c->d_coord,
                   c->nn_weights, c->nn_w16, c->nn_m, c->nn_v};
   for (void* p : bufs)
@@ -507,7 +506,8 @@ int lqcd_gauge_upload(lqcd_ctx* c, const double* links, int where, double kappa,
   bool ok = need(c->U64, link_bytes(g, P64)) && need(c->U32, link_bytes(g, P32)) &&
             need(c->U16, link_bytes(g, P16)) && need(c->A64, 2 * clover_bytes(g, P64)) &&
             need(c->Ainv64, 2 * clover_bytes(g, P64)) && need(c->A32, 2 * clover_bytes(g, P32)) &&
-            need(c->Ainv32, 2 * clover_bytes(g, P32)) && need(c->Ainv16, 2 * clover_bytes(g, P16));
+            need(c->Ainv32, 2 * clover_bytes(g, P32)) && need(c->Ainv16, 2 * clover_bytes(g, P16)) &&
+            need(c->Udf, link_bytes(g, P64)) && need(c->Adf, 2 * clover_bytes(g, P64));
   if (!ok) {
     cudaGetLastError();
     return set_error(c, LQCD_ERR_OOM, "gauge_upload: out of device memory");
@@ -522,6 +522,8 @@ int lqcd_gauge_upload(lqcd_ctx* c, const double* links, int where, double kappa,
   if (!d || !bad) return set_error(c, LQCD_ERR_OOM, "gauge_upload: out of device memory");
   cudaMemsetAsync(bad, 0, sizeof(int), c->work);
   build_gauge(c, d, bad);
+  split_field(c->U64, c->Udf, (long)(link_bytes(g, P64) / 16), c->work);
+  split_field(c->A64, c->Adf, (long)(2 * clover_bytes(g, P64) / 16), c->work);
   int hb = 0;
   cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, c->work);
   cudaError_t e = cudaStreamSynchronize(c->work);
@@ -828,8 +830,7 @@ static int perambulator_impl(lqcd_ctx* c, const double* Vt, int n_ev, const int*
       make_sources(g, dV, n_ev, S.jb, S.jb + blk, S.mask, S.z + 2 * LQCD_MAXT, S.eb, nb, ss);
       if (int e = solve_batch_enqueue(c, s, S.eb, S.ex, nb, domain, q, S.h)) return e;
       S.busy = true;
-      // beside a batch in flight the projection (FP64 pipe) takes few blocks per SM
-      const int pbs = nsl > 1 && c->res_persistent > 0 ? c->res_persistent : 4;
+      const int pbs = 4;  // blocks per SM of the projection
       const int ks = project_ksplit(g, n_ev, nb, nz, pbs);
       double2* Cp = (double2*)ws_get(c, s ? "p_Cpart#1" : "p_Cpart", (size_t)ks * nz * n_ev * 4 * nb * sizeof(double2));
       if (!Cp) return set_error(c, LQCD_ERR_OOM, "perambulator: OOM");
@@ -1024,12 +1025,15 @@ int lqcd_window_average(lqcd_ctx* c, const double* C, const double* dC, const in
 
 }  // extern "C"
 
+static int internal_prec(int prec) {
+  return prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : (prec == LQCD_PREC_F16 ? P16 : PDF));
+}
+
 extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_variant, double* best_ms) {
-  if (!c || nrhs < 1 || !best_variant || !best_ms ||
-      (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
+  if (!c || nrhs < 1 || !best_variant || !best_ms || prec < LQCD_PREC_F64 || prec > LQCD_PREC_DF)
     return set_error(c, LQCD_ERR_INVALID_ARG, "tune_dslash: bad arguments");
   if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "tune_dslash: no gauge field uploaded");
-  const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);
+  const int P = internal_prec(prec);
   const Geom& g = c->g;
   const size_t sb = spinor_bytes(g, P, nrhs);
   void* in = ws_get(c, "bench_in", sb);
@@ -1037,21 +1041,29 @@ extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_varia
   if (!in || !out) return set_error(c, LQCD_ERR_OOM, "tune_dslash: OOM");
   Scope sc(c);
   cudaMemsetAsync(in, 0, sb, c->work);
-  const void* U = P == P64 ? c->U64 : (P == P32 ? c->U32 : c->U16);
+  const void* U = P == P64 || P == PDF ? c->U64 : (P == P32 ? c->U32 : c->U16);
   const void* Ainv = P == P64 ? c->Ainv64 : (P == P32 ? c->Ainv32 : c->Ainv16);
   DslashCall k{P, EPI_CH, 0, in, nullptr, nullptr, out, U, (const char*)Ainv + clover_bytes(g, P), 1, nrhs, 0.0, 1.0,
                c->d_tc_full};
   k.coord = coord_of(c, 1);
+  // LQCD_PREC_DF: the true-residual kernel z - (A y - kappa H x) with x = y = z = the input
+  auto launch = [&](int var) {
+    if (P == PDF)
+      launch_residual_df(g, in, in, in, out, c->Udf, (const char*)c->Adf + clover_bytes(g, P64), coord_of(c, 1),
+                         c->d_tc_full, 1, nrhs, c->kappa, var, c->work);
+    else
+      launch_dslash(g, k, c->work, var);
+  };
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = 1e30;
   int bt = 0;
-  const int nvar = P == P64 ? 3 : 5;  // the staged variants 3, 4 are FP32 / FP16 only
+  const int nvar = P == P64 || P == PDF ? 3 : 5;  // the staged variants 3, 4 are FP32 / FP16 only
   for (int var = 0; var < nvar; var++) {
-    launch_dslash(g, k, c->work, var);
+    launch(var);
     cudaEventRecord(e0, c->work);
-    for (int i = 0; i < 5; i++) launch_dslash(g, k, c->work, var);
+    for (int i = 0; i < 5; i++) launch(var);
     cudaEventRecord(e1, c->work);
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -1073,10 +1085,9 @@ extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_varia
 }
 
 extern "C" int lqcd_set_dslash_variant(lqcd_ctx* c, int prec, int nrhs, int variant) {
-  if (!c || nrhs < 1 || variant < 0 || variant > 4 ||
-      (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
+  if (!c || nrhs < 1 || variant < 0 || variant > 4 || prec < LQCD_PREC_F64 || prec > LQCD_PREC_DF)
     return set_error(c, LQCD_ERR_INVALID_ARG, "set_dslash_variant: bad arguments");
-  const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);
+  const int P = internal_prec(prec);
   c->tuned_variant[(long)P * 100000 + nrhs] = variant;
   return LQCD_OK;
 }
@@ -1203,11 +1214,11 @@ __global__ void k_flush(float4* p, long n) {
 
 extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, int flush_l2, double* ms_per_launch,
                                  double* algo_bytes_per_launch) {
-  if (!c || nrhs < 1 || n_iter < 1 || !ms_per_launch || !algo_bytes_per_launch ||
-      (prec != LQCD_PREC_F64 && prec != LQCD_PREC_F32 && prec != LQCD_PREC_F16))
+  if (!c || nrhs < 1 || n_iter < 1 || !ms_per_launch || !algo_bytes_per_launch || prec < LQCD_PREC_F64 ||
+      prec > LQCD_PREC_DF)
     return set_error(c, LQCD_ERR_INVALID_ARG, "dslash_bench: bad arguments");
   if (!c->have_gauge) return set_error(c, LQCD_ERR_STATE, "dslash_bench: no gauge field uploaded");
-  const int P = prec == LQCD_PREC_F64 ? P64 : (prec == LQCD_PREC_F32 ? P32 : P16);
+  const int P = internal_prec(prec);
   const Geom& g = c->g;
   const size_t sb = spinor_bytes(g, P, nrhs);
   void* in = ws_get(c, "bench_in", sb);
@@ -1222,9 +1233,8 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
   } else {
     long nf = (long)(sb / sizeof(float));
     k_fill_pattern<<<(nf + 255) / 256, 256, 0, c->work>>>((float*)in, nf, 12345u); lqcd::count_launch();
-    if (P == P64) cudaMemsetAsync(in, 0, 0, c->work);
   }
-  if (P == P64) {
+  if (P == P64 || P == PDF) {
     // reinterpret the float pattern as doubles would give garbage exponents: write doubles instead
     std::vector<double> h(4096);
     for (size_t i = 0; i < h.size(); i++) h[i] = 0.01 * (double)((i * 7919) % 200) - 1.0;
@@ -1233,16 +1243,28 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
       cudaMemcpyAsync((char*)in + o, h.data(), n, cudaMemcpyHostToDevice, c->work);
     }
   }
-  const void* U = P == P64 ? c->U64 : (P == P32 ? c->U32 : c->U16);
+  const void* U = P == P64 || P == PDF ? c->U64 : (P == P32 ? c->U32 : c->U16);
   const void* Ainv = P == P64 ? c->Ainv64 : (P == P32 ? c->Ainv32 : c->Ainv16);
   const void* Ao = (const char*)Ainv + clover_bytes(g, P);
   DslashCall k{P, EPI_CH, 0, in, nullptr, nullptr, out, U, Ao, 1, nrhs, 0.0, 1.0, c->d_tc_full};
   k.coord = coord_of(c, 1);
+  // LQCD_PREC_DF: the true-residual kernel z - (A y - kappa H x), reading x (split once, as the
+  // solver does), y, z, writing out
+  void* xs = P == PDF ? ws_get(c, "bench_split", sb) : nullptr;
+  if (P == PDF && !xs) return set_error(c, LQCD_ERR_OOM, "dslash_bench: OOM");
+  if (P == PDF) split_field(in, xs, (long)(sb / 16), c->work);
+  auto launch = [&](int var) {
+    if (P == PDF)
+      launch_residual_df(g, xs, in, in, out, c->Udf, (const char*)c->Adf + clover_bytes(g, P64), coord_of(c, 1),
+                         c->d_tc_full, 1, nrhs, c->kappa, var, c->work);
+    else
+      launch_dslash(g, k, c->work, var);
+  };
   int variant = 0;
   auto it = c->tuned_variant.find((long)P * 100000 + nrhs);
   if (it != c->tuned_variant.end()) variant = it->second;
   // warm-up
-  launch_dslash(g, k, c->work, variant);
+  launch(variant);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1253,7 +1275,7 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
       lqcd::count_launch();
     }
     cudaEventRecord(e0, c->work);
-    launch_dslash(g, k, c->work, variant);
+    launch(variant);
     cudaEventRecord(e1, c->work);
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -1264,9 +1286,9 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
   cudaEventDestroy(e1);
   if (int e = cuda_check(c, "dslash_bench")) return e;
   *ms_per_launch = total / n_iter;
-  const double lb = P == P64 ? 144.0 : (P == P32 ? 48.0 : 24.0);
-  const double cb = P == P64 ? 576.0 : (P == P32 ? 288.0 : 144.0);
-  const double spb = P == P64 ? 192.0 : (P == P32 ? 96.0 : 48.0);
-  *algo_bytes_per_launch = (double)g.Vh * (8 * lb + cb + 2.0 * nrhs * spb);
+  const double lb = P == P64 || P == PDF ? 144.0 : (P == P32 ? 48.0 : 24.0);
+  const double cb = P == P64 || P == PDF ? 576.0 : (P == P32 ? 288.0 : 144.0);
+  const double spb = P == P64 || P == PDF ? 192.0 : (P == P32 ? 96.0 : 48.0);
+  *algo_bytes_per_launch = (double)g.Vh * (8 * lb + cb + (P == PDF ? 4.0 : 2.0) * nrhs * spb);
   return LQCD_OK;
 }

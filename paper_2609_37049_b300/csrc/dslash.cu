@@ -53,53 +53,6 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(const DslashParams pr
   dslash_body<P, EPI, DAG, RED>(pr, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// Persistent form (no fused reductions): a grid of a few blocks per SM walks every (site, rhs)
-// pair.  Used for the FP64 true residual: a handful of warps keeps B300's FP64 pipe busy, so the
-// kernel leaves most of each SM to the FP32 kernels of the other batch in flight.
-template <int P, int EPI, int MINB>
-__global__ void __launch_bounds__(128, MINB) dslash_persistent_kernel(const DslashParams pr) {
-  const long n = pr.g.Vh * (long)pr.nrhs;
-  for (long tid = (long)blockIdx.x * blockDim.x + threadIdx.x; tid < n; tid += (long)gridDim.x * blockDim.x)
-    dslash_body<P, EPI, false, RED_NONE>(pr, tid);
-}
-
-static int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
-  }
-  return n;
-}
-
-static int high_priority() {
-  static int p = 1;
-  if (p == 1) {
-    int lo = 0, hi = 0;
-    cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    p = hi;
-  }
-  return p;
-}
-
-// The FP64 EPI_RES hopping kernel in persistent form: blocks_per_sm blocks per SM, launched with
-// the device's highest priority so its blocks are placed before queued blocks of other streams.
-static void launch_persistent_res(const DslashParams& pr, int blocks_per_sm, cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(sm_count() * blocks_per_sm));
-  cfg.blockDim = dim3(128);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributePriority;
-  attr[0].val.priority = high_priority();
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, dslash_persistent_kernel<P64, EPI_RES, 2>, pr);
-  lqcd::count_launch();
-}
-
 template <int P>
 __global__ void clover_only_kernel(const void* C, const void* in, void* out, long Vh, int nrhs) {
   using R = typename Traits<P>::real;
@@ -186,10 +139,6 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int vari
   pr.pipe_off = 0;
   const bool dag = c.dagger != 0;
   if (variant < 0 || variant > 4) variant = 0;
-  if (c.persistent > 0 && c.prec == P64 && c.epi == EPI_RES && c.red == RED_NONE && !dag) {
-    launch_persistent_res(pr, c.persistent, st);
-    return;
-  }
   if (c.red == RED_NONE) {
     long nthreads = g.Vh * (long)c.nrhs;
     const int tpb = 128;

@@ -29,13 +29,13 @@
 namespace lqcd {
 
 size_t spinor_bytes(const Geom& g, int prec, int nrhs) {
-  return (size_t)g.Vh * nrhs * 12 * (prec == P64 ? 16 : (prec == P32 ? 8 : 4));
+  return (size_t)g.Vh * nrhs * 12 * (prec == P64 || prec == PDF ? 16 : (prec == P32 ? 8 : 4));
 }
 size_t clover_bytes(const Geom& g, int prec) {
-  return (size_t)g.Vh * 2 * (prec == P64 ? 18 * 16 : (prec == P32 ? 9 * 16 : 9 * 8));
+  return (size_t)g.Vh * 2 * (prec == P64 || prec == PDF ? 18 * 16 : (prec == P32 ? 9 * 16 : 9 * 8));
 }
 size_t link_bytes(const Geom& g, int prec) {
-  return (size_t)g.Vh * 8 * (prec == P64 ? 9 * 16 : (prec == P32 ? 3 * 16 : 3 * 8));
+  return (size_t)g.Vh * 8 * (prec == P64 || prec == PDF ? 9 * 16 : (prec == P32 ? 3 * 16 : 3 * 8));
 }
 
 static inline void* off(void* base, size_t b, int p) { return reinterpret_cast<char*>(base) + b * p; }
@@ -291,7 +291,9 @@ struct Batch {
   int* ctr;  // device loop counters: inner iterations, cycles, inner chunks
   Inner in;
   Fgcr f;
-  int v64;
+  int v64;       // launch variant of the true-residual kernel
+  int res_prec;  // its arithmetic: PDF (double-float) or P64
+  void* xdf;     // PDF: one parity of x split to double-float
   size_t sb64, sbP;
   char* hbuf;  // pinned read-back: rel [nsys] doubles, iters [nsys] ints, counters [4] ints
   long long dslash_host;  // host path: dslash launches counted on the host
@@ -499,6 +501,14 @@ static int plan_batch(lqcd_ctx* c, int slot, int nrhs, int domain, const lqcd_so
   }
   const auto tv64 = c->tuned_variant.find((long)P64 * 100000 + nrhs);
   B.v64 = tv64 != c->tuned_variant.end() ? tv64->second : 0;  // FP64 residual launch variant
+  B.res_prec = prm.residual == 1 ? P64 : PDF;
+  B.xdf = nullptr;
+  if (B.res_prec == PDF) {
+    const auto tvd = c->tuned_variant.find((long)PDF * 100000 + nrhs);
+    B.v64 = tvd != c->tuned_variant.end() ? tvd->second : 0;
+    B.xdf = ws_get(c, wsn("r_xdf", slot), spinor_bytes(g, P64, nrhs));
+    if (!B.xdf) return set_error(c, LQCD_ERR_OOM, "solve: out of device memory (residual)");
+  }
   return LQCD_OK;
 }
 
@@ -545,10 +555,15 @@ static void batch_finish_cycle(lqcd_ctx* c, Batch& B, const double2* b, double2*
   v_axpy_mixed(P, x, B.ein, B.vgF, B.si, B.nseg, B.iscale, B.oact, B.st);
   const size_t cb64 = clover_bytes(g, P64);
   for (int p = 0; p < 2; p++) {
-    DslashCall k = call(c, P64, EPI_RES, off(x, B.sb64, 1 - p), off(x, B.sb64, p), off(b, B.sb64, p),
-                        off(B.r64, B.sb64, p), c->U64, off(c->A64, cb64, p), p, B.nrhs, 1.0, -c->kappa, B.tc);
-    k.persistent = c->res_persistent;
-    launch_dslash(g, k, B.st, B.v64);
+    if (B.res_prec == PDF) {
+      split_field(off(x, B.sb64, 1 - p), B.xdf, (long)(B.sb64 / 16), B.st);
+      launch_residual_df(g, B.xdf, off(x, B.sb64, p), off(b, B.sb64, p), off(B.r64, B.sb64, p), c->Udf,
+                         off(c->Adf, cb64, p), coord_of(c, p), B.tc, p, B.nrhs, c->kappa, B.v64, B.st);
+    } else {
+      DslashCall k = call(c, P64, EPI_RES, off(x, B.sb64, 1 - p), off(x, B.sb64, p), off(b, B.sb64, p),
+                          off(B.r64, B.sb64, p), c->U64, off(c->A64, cb64, p), p, B.nrhs, 1.0, -c->kappa, B.tc);
+      launch_dslash(g, k, B.st, B.v64);
+    }
   }
   v_norm2(P64, B.r64, B.vgF, B.si, B.nseg, B.partial, B.r2, B.st);
   outer_update(B.r2, B.b2, B.nsys, B.tol, B.inner_tol, B.oact, B.delta, B.scale, B.rel, 0, B.st);
@@ -761,8 +776,9 @@ int solve_batch_enqueue(lqcd_ctx* c, int slot, const double2* b, double2* x, int
   const bool use_graph = prm.use_graph != 0;
   if (use_graph && !c->loop_graphs_unavailable && !c->timing) {
     char key[512];
-    snprintf(key, sizeof key, "loop:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%p", slot, B.P,
+    snprintf(key, sizeof key, "loop:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%p", slot, B.P,
              nrhs, domain, B.nseg, B.chunk, B.tol, B.inner_tol, B.max_iter, B.max_outer, B.in.variant, B.v64,
+             B.res_prec,
              B.pkind, (const void*)b, (void*)x, (void*)B.r64, B.in.r, (void*)B.hbuf, (const void*)B.tc,
              (const void*)B.si, B.in.U);
     std::string k = key;

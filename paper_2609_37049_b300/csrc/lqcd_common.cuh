@@ -62,7 +62,67 @@ template <typename R> LQCD_HD cplx<R> cfms(cplx<R> a, cplx<R> b, cplx<R> c) {
   return {fmx(a.im, b.im, fmx(-a.re, b.re, c.re)), fmx(-a.im, b.re, fmx(-a.re, b.im, c.im))};
 }
 
-enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+// ------------------------------------------------------------------ double-float arithmetic
+// A value held as an unevaluated sum hi + lo of two floats (|lo| below an ulp of hi): about 48
+// significant bits, computed on the FP32 pipe, which on B300 issues 64 times the FP64 pipe's
+// operations.  Products use the FMA error-free product (TwoProduct: p = a b, e = fma(a, b, -p)
+// exactly); sums add the high parts with Knuth's TwoSum and fold in the low parts, then
+// renormalise with Quick-Two-Sum (Dekker 1971; Hida, Li & Bailey 2001).  Each operation errs by
+// a few units of 2^-47 of its operands' magnitude.  The compiler must not reassociate these
+// expressions, which holds without fast-math flags.
+struct dfl {
+  float hi, lo;
+  dfl() = default;
+  LQCD_HD dfl(float h, float l) : hi(h), lo(l) {}
+  // conversion of a scalar parameter (a few per thread: FP64 arithmetic is fine here)
+  LQCD_HD explicit dfl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  LQCD_HD explicit dfl(int i) : hi((float)i), lo(0.f) {}
+  LQCD_HD explicit operator double() const { return (double)hi + (double)lo; }
+};
+LQCD_HD dfl df_quick(float s, float e) {
+  const float h = s + e;
+  return dfl(h, e - (h - s));
+}
+LQCD_HD dfl operator+(dfl a, dfl b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  return df_quick(s, e);
+}
+LQCD_HD dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+LQCD_HD dfl operator-(dfl a, dfl b) { return a + (-b); }
+LQCD_HD dfl operator*(dfl a, dfl b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return df_quick(p, e);
+}
+LQCD_HD dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
+LQCD_HD dfl fmx(dfl a, dfl b, dfl c) { return a * b + c; }
+
+// hi + lo = d from the bits of d, with integer operations and one int-to-float conversion (no
+// FP64 arithmetic): hi = d truncated to 24 significant bits, lo = the remaining 29 bits rounded
+// to 24, so |hi + lo - d| <= 2^-47 |d| for |d| >= 2^-74; below that lo loses bits gradually
+// (absolute error under 2^-126 while hi is normal; |d| < 2^-126 gives zero).  |d| >= 2^128,
+// infinities and NaN go to hi (lo = 0).
+LQCD_D dfl split_d(double d) {
+  const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+  const unsigned sgn = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;  // unbiased exponent
+  if (e > 127) return dfl(__double2float_rn(d), 0.f);
+  if (e < -126) return dfl(__uint_as_float(sgn), 0.f);
+  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  // the low 29 bits are worth m 2^(e - 52): scaled in two steps, a normal power of two first, so
+  // that only the last product may underflow
+  const float m = __uint2float_rn(lw & 0x1fffffffu);
+  const int e1 = e >= -100 ? e - 26 : e;
+  const float lo = m * __uint_as_float((unsigned)(e1 + 127) << 23) * (e >= -100 ? 0x1p-26f : 0x1p-52f);
+  return dfl(hi, sgn ? -lo : lo);
+}
+
+// PDF: FP64 fields, double-float arithmetic (the true-residual kernel of dslash_df.cu)
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PDF = 3 };
 
 template <int P> struct Traits;
 template <> struct Traits<P64> {
@@ -210,6 +270,7 @@ LQCD_D void load_clover(const void* base, long Vh, int chir, long cb, typename T
       r[2 * c] = v.x;
       r[2 * c + 1] = v.y;
     }
+
   } else if constexpr (P == P32) {
     const float4* f = reinterpret_cast<const float4*>(base) + (long)chir * 9 * Vh + cb;
 #pragma unroll

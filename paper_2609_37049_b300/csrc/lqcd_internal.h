@@ -95,8 +95,16 @@ struct DslashCall {
   const void* zred = nullptr;
   int red = RED_NONE;
   int red_sites = 0;
-  int persistent = 0;  // FP64 EPI_RES only: > 0 launches the persistent kernel with this many blocks per SM
 };
+
+// dslash_df.cu: split an FP64 field of n_complex entries to double-float (float4 per entry), and
+// the true residual out = z - (A y - kappa H xn) of parity out_par in double-float arithmetic
+// (xn: the neighbour parity, split; y, z, out: FP64; U_split, A_split: split links and the
+// parity's clover; variant 0 / 1 / 2: register caps 255 / 168 / 128).
+void split_field(const void* in, void* out, long n_complex, cudaStream_t st);
+void launch_residual_df(const Geom& g, const void* xn_split, const void* y, const void* z, void* out,
+                        const void* U_split, const void* A_split, const unsigned* coord, const signed char* tc,
+                        int out_par, int nrhs, double kappa, int variant, cudaStream_t st);
 
 // variant: register cap of the FP32 / FP16 kernels (0: 128, 1: 80, 2: 64 registers per thread)
 void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int variant = 0);
@@ -132,6 +140,10 @@ struct lqcd_ctx {
   void* Ainv32 = nullptr;
   void* Ainv16 = nullptr;
   void* A32 = nullptr;
+  // U64 and A64 split to double-float (float4 = (re.hi, re.lo, im.hi, im.lo) per complex entry,
+  // same indexing), read by the true-residual kernel
+  void* Udf = nullptr;
+  void* Adf = nullptr;
   // domain tiling of the time axis
   std::vector<int> extents;
   int t_start = 0;  // first timeslice of domain 0 (the tiling wraps around the time boundary)
@@ -169,9 +181,6 @@ struct lqcd_ctx {
   };
   std::map<std::string, LoopGraph> loop_graphs;
   bool loop_graphs_unavailable = false;  // set when the driver refused a conditional graph
-  // FP64 true residual as a persistent kernel of this many blocks per SM (0: one thread per site
-  // and right-hand side over the whole grid); see dslash_persistent_kernel
-  int res_persistent = 0;
   // a second right-hand-side batch in flight (pipelined perambulators): slot 1's stream (slot 0
   // is `work`), an event to order it, and per-slot pinned buffers for the batch read-back
   cudaStream_t slot_stream = 0;

@@ -25,7 +25,7 @@ LQCD_HOST, LQCD_DEVICE = 0, 1
 LQCD_MODE_FULL, LQCD_MODE_DOMAIN = 0, 1
 LQCD_SINKS_DIAG, LQCD_SINKS_ALL, LQCD_SINKS_DIAG_SRCV = 0, 1, 2
 LQCD_SOLVER_BICGSTAB64, LQCD_SOLVER_MIXED, LQCD_SOLVER_FGCR_NN = 0, 1, 2
-LQCD_PREC_F64, LQCD_PREC_F32, LQCD_PREC_F16 = 0, 1, 2
+LQCD_PREC_F64, LQCD_PREC_F32, LQCD_PREC_F16, LQCD_PREC_DF = 0, 1, 2, 3
 
 EXPORTED = [
     "lqcd_default_params", "lqcd_create", "lqcd_destroy", "lqcd_set_stream", "lqcd_last_error",
@@ -80,7 +80,7 @@ class lqcd_solve_params(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("gcr_nkrylov", ctypes.c_int),
                 ("precond_iters", ctypes.c_int), ("pipeline", ctypes.c_int),
-                ("projection", ctypes.c_int)]
+                ("projection", ctypes.c_int), ("residual", ctypes.c_int)]
 
 
 class lqcd_solve_stats(ctypes.Structure):

@@ -38,7 +38,8 @@ def test_struct_layout_matches_header(tmp_path):
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lqcd.h"\n'
                    'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lqcd_solve_params),'
                    ' sizeof(lqcd_solve_stats), offsetof(lqcd_solve_params, projection),'
-                   ' offsetof(lqcd_solve_stats, device_loops)); return 0;}\n')
+                   ' offsetof(lqcd_solve_stats, device_loops)); printf("%zu\\n",'
+                   ' offsetof(lqcd_solve_params, residual)); return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
@@ -46,6 +47,7 @@ def test_struct_layout_matches_header(tmp_path):
     assert int(out[1]) == ctypes.sizeof(lqcd.lqcd_solve_stats)
     assert int(out[2]) == lqcd.lqcd_solve_params.projection.offset
     assert int(out[3]) == lqcd.lqcd_solve_stats.device_loops.offset
+    assert int(out[4]) == lqcd.lqcd_solve_params.residual.offset
 
 
 def test_default_params():

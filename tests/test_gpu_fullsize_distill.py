@@ -166,7 +166,7 @@ def scale():
     ctx.gauge_upload(U, s["kappa"], s["c_sw"])
     ctx.set_domains(s["extents"])
     from paper_2609_37049_b300 import autotune
-    autotune.tune(ctx, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F64), blocks=(s["rhs_block"],))
+    autotune.tune(ctx, precisions=(lqcd.LQCD_PREC_F32, lqcd.LQCD_PREC_F64, lqcd.LQCD_PREC_DF), blocks=(s["rhs_block"],))
     return dict(U=U, ctx=ctx, dims=dims)
 
 
