@@ -18,8 +18,9 @@ namespace lqcd {
 // MINB: minimum resident blocks of 128 threads the compiler must allow (register cap 255 / 168 /
 // 128 / 80 / 64 per thread for MINB = 2 / 3 / 4 / 6 / 8).  Launch variants 0-2 are this kernel
 // with MINB 4 / 6 / 8 (FP64: 4 / 2 / 3);
-// variants 3 / 4 are the staged kernels of dslash_staged.cu (3: links and clover staged once per
-// site in shared memory; 4: neighbour spinors staged by bulk copies) where they apply (FP32 /
+// variants 3-6 are the staged kernels of dslash_staged.cu (3: links and clover staged once per
+// site in shared memory; 4: neighbour spinors staged by bulk copies; 5: as 3 on paired FP32
+// arithmetic; 6: as 5 with per-thread asynchronous spinor copies) where they apply (FP32 /
 // FP16, the solver's epilogues, RHS counts as stated there), else variant 0.  The autotuner picks
 // the variant per precision and RHS count.
 template <int P, int EPI, bool DAG, int RED>
@@ -138,7 +139,7 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int vari
   pr.b = c.b;
   pr.pipe_off = 0;
   const bool dag = c.dagger != 0;
-  if (variant < 0 || variant > 4) variant = 0;
+  if (variant < 0 || variant > 6) variant = 0;
   if (c.red == RED_NONE) {
     long nthreads = g.Vh * (long)c.nrhs;
     const int tpb = 128;

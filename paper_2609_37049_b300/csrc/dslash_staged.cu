@@ -6,6 +6,13 @@
 //   into shared memory; the hopping threads then read them as broadcasts instead of each
 //   rebuilding the links (the direct kernel repeats the rebuild for every right-hand side).  Site
 //   and element indices are 32-bit (the host checks that the fields fit).  Register cap 80.
+// * variant 5 (dslash_sl2_kernel): variant 3 with the hopping arithmetic on paired FP32 operations
+//   (fma.rn.f32x2 / add.f32x2: two lanes per instruction).  The two spin components of a projected
+//   half spinor form the pairs, (h_0[c], h_1[c]), so the SU(3) product is 36 paired FMAs per hop
+//   instead of 72, with the links staged as (re, re, im, im) per entry; the upper accumulators pair
+//   the same way, and the lower ones wherever the direction's spin reconstruction keeps the pair
+//   order (mu = z, t).  Same arithmetic as variant 3 (each output lane rounds like the scalar
+//   code), other than the order of the two products in an imaginary part.
 // * variant 4 (dslash_pipe_kernel): the eight neighbour spinors of every output site staged by
 //   bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier) 3 hops ahead of
 //   the arithmetic.  One warp = 32 right-hand sides of one output site (nrhs a multiple of 32),
@@ -352,29 +359,410 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl_kernel(const DslashParams
   dslash_epilogue<P, EPI, RED, true>(pr, cb, (long)cb * nr + rhs, (long)stride, rhs, acc, sclov[sl]);
 }
 
+// ------------------------------------------------------------------ variant 5: paired FP32
+// w = U h (DAG: U^dag h) for the spin pair: hr[b] = (Re h_0[b], Re h_1[b]), hi[b] likewise; L holds
+// the link as 9 float4 (re, re, im, im), row-major.
+template <bool DAG>
+LQCD_D void su3_pair(const float4* L, const float2 (&hr)[3], const float2 (&hi)[3], float2 (&wr)[3],
+                     float2 (&wi)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const float4 u = L[DAG ? b * 3 + a : a * 3 + b];
+      const float2 ur = make_float2(u.x, u.y), ui = make_float2(u.z, u.w), mui = make_float2(-u.z, -u.w);
+      if (b == 0) {
+        wr[a] = __fmul2_rn(ur, hr[0]);
+        wi[a] = __fmul2_rn(ur, hi[0]);
+      } else {
+        wr[a] = __ffma2_rn(ur, hr[b], wr[a]);
+        wi[a] = __ffma2_rn(ur, hi[b], wi[a]);
+      }
+      wr[a] = __ffma2_rn(DAG ? ui : mui, hi[b], wr[a]);  // U h: - Im u Im h;  U^dag h: + Im u Im h
+      wi[a] = __ffma2_rn(DAG ? mui : ui, hr[b], wi[a]);  // U h: + Im u Re h;  U^dag h: - Im u Re h
+    }
+  }
+}
+
+// acc += [ w ; S X_MU^dag w ] on the paired accumulators: ur / ui = (spin 0, spin 1) real / imaginary
+// parts per colour, lr / li = (spin 2, spin 3).
+template <int MU, int S>
+LQCD_D void accumulate_pair(const float2 (&wr)[3], const float2 (&wi)[3], float2 (&ur)[3], float2 (&ui)[3],
+                            float2 (&lr)[3], float2 (&li)[3]) {
+  constexpr float s = (float)S;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    ur[c] = __fadd2_rn(ur[c], wr[c]);
+    ui[c] = __fadd2_rn(ui[c], wi[c]);
+    if constexpr (MU == 0) {  // X^dag w = (i w1, i w0)
+      lr[c].x -= s * wi[c].y;
+      lr[c].y -= s * wi[c].x;
+      li[c].x += s * wr[c].y;
+      li[c].y += s * wr[c].x;
+    } else if constexpr (MU == 1) {  // X^dag w = (w1, -w0)
+      lr[c].x += s * wr[c].y;
+      lr[c].y -= s * wr[c].x;
+      li[c].x += s * wi[c].y;
+      li[c].y -= s * wi[c].x;
+    } else if constexpr (MU == 2) {  // X^dag w = (i w0, -i w1)
+      lr[c] = __ffma2_rn(make_float2(-s, s), wi[c], lr[c]);
+      li[c] = __ffma2_rn(make_float2(s, -s), wr[c], li[c]);
+    } else {  // X^dag w = (w0, w1)
+      lr[c] = __ffma2_rn(make_float2(s, s), wr[c], lr[c]);
+      li[c] = __ffma2_rn(make_float2(s, s), wi[c], li[c]);
+    }
+  }
+}
+
+template <int MU, bool FWD>
+LQCD_D void hop_pair_p(const cplx<float> (&p)[12], int coef, const float4* L, float2 (&ur)[3], float2 (&ui)[3],
+                       float2 (&lr)[3], float2 (&li)[3]) {
+  constexpr int S = FWD ? -1 : 1;  // H (not H^dag): forward projector 1 - gamma_mu
+  cplx<float> h[2][3];
+  project<MU, S>(p, h);
+  float2 hr[3], hi[3], wr[3], wi[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    hr[c] = make_float2(h[0][c].re, h[1][c].re);
+    hi[c] = make_float2(h[0][c].im, h[1][c].im);
+  }
+  su3_pair<!FWD>(L, hr, hi, wr, wi);
+  if (coef < 0) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      wr[c] = make_float2(-wr[c].x, -wr[c].y);
+      wi[c] = make_float2(-wi[c].x, -wi[c].y);
+    }
+  }
+  accumulate_pair<MU, S>(wr, wi, ur, ui, lr, li);
+}
+
+template <int P, int MU, bool FWD>
+LQCD_D void hop_pair(const DslashParams& pr, int nb_idx, int coef, int stride, const float4* L, float2 (&ur)[3],
+                     float2 (&ui)[3], float2 (&lr)[3], float2 (&li)[3]) {
+  cplx<float> p[12];
+  load_spinor32<P>(pr.in, stride, nb_idx, p);
+  hop_pair_p<MU, FWD>(p, coef, L, ur, ui, lr, li);
+}
+
+template <int P, int MU>
+LQCD_D void hop_dir_pair(const DslashParams& pr, int s, int cmu, int Lmu, int smu, int coef_f, int coef_b, int rhs,
+                         int stride, int nrhs, const float4* lf, const float4* lb, float2 (&ur)[3], float2 (&ui)[3],
+                         float2 (&lr)[3], float2 (&li)[3]) {
+  if (coef_f != 0) {
+    const int sn = s + ((cmu + 1 == Lmu) ? smu * (1 - Lmu) : smu);
+    hop_pair<P, MU, true>(pr, (sn >> 1) * nrhs + rhs, coef_f, stride, lf, ur, ui, lr, li);
+  }
+  if (coef_b != 0) {
+    const int sn = s + ((cmu == 0) ? smu * (Lmu - 1) : -smu);
+    hop_pair<P, MU, false>(pr, (sn >> 1) * nrhs + rhs, coef_b, stride, lb, ur, ui, lr, li);
+  }
+}
+
+// Blocks as variant 3 (128 threads = 128 / nrhs sites x nrhs right-hand sides).
 template <int P, int EPI, int RED, int MINB>
-void launch_sl(const DslashParams& pr, long blocks, size_t shm, cudaStream_t st) {
-  dslash_sl_kernel<P, EPI, RED, MINB><<<blocks, 128, shm, st>>>(pr);
+__global__ void __launch_bounds__(128, MINB) dslash_sl2_kernel(const DslashParams pr) {
+  __shared__ float4 slink[kMaxSites][8][9];  // [site][hop: 2 mu (fwd), 2 mu + 1 (bwd)][entry]: (re, re, im, im)
+  __shared__ float4 sclov[kMaxSites][18];    // [site][chirality x 9 packed chunks]
+  const Geom& g = pr.g;
+  const int nr = pr.nrhs;
+  const int lg = __ffs(nr) - 1;
+  const int S = 128 >> lg;
+  const int cb0 = blockIdx.x * S;
+  const int Vh = (int)g.Vh;
+  const int sy = g.Lx, sz = g.Lx * g.Ly, sw = sz * g.Lz;
+  for (int j = threadIdx.x; j < 26 * S; j += 128) {
+    if (j < 8 * S) {  // link j & 7 of site j >> 3, third row rebuilt once
+      const int site = j >> 3, k = j & 7, c = cb0 + site;
+      if (c < Vh) {
+        const int mu = k >> 1;
+        int lcb = c, par = pr.out_par;
+        if (k & 1) {  // backward hop: the link of the neighbour s - mu
+          const int xh = c % g.Lxh, yzt = c / g.Lxh, y = yzt % g.Ly, zt = yzt / g.Ly, z = zt % g.Lz,
+                    t = zt / g.Lz;
+          const int x = 2 * xh + ((pr.out_par + y + z + t) & 1);
+          const int s = x + sy * y + sz * z + sw * t;
+          const int cm = mu == 0 ? x : (mu == 1 ? y : (mu == 2 ? z : t));
+          const int Lm = mu == 0 ? g.Lx : (mu == 1 ? g.Ly : (mu == 2 ? g.Lz : g.Lt));
+          const int sm = mu == 0 ? 1 : (mu == 1 ? sy : (mu == 2 ? sz : sw));
+          lcb = (s + (cm == 0 ? sm * (Lm - 1) : -sm)) >> 1;
+          par = 1 - pr.out_par;
+        }
+        cplx<float> u[3][3];
+        load_link<P>(pr.U, g.Vh, mu, par, lcb, u);
+        float4* L = slink[site][k];
+#pragma unroll
+        for (int e = 0; e < 9; e++) {
+          const cplx<float> v = u[e / 3][e % 3];
+          L[e] = make_float4(v.re, v.re, v.im, v.im);
+        }
+      }
+    } else {  // clover chunk e of site q / 18
+      const int q = j - 8 * S, site = q / 18, e = q - site * 18, c = cb0 + site;
+      if (c < Vh) {
+        if constexpr (P == P32) {
+          sclov[site][e] = __ldg(reinterpret_cast<const float4*>(pr.C) + (long)e * Vh + c);
+        } else {
+          const uint2 v = __ldg(reinterpret_cast<const uint2*>(pr.C) + (long)e * Vh + c);
+          const float2 a = h2f(v.x), b = h2f(v.y);
+          sclov[site][e] = make_float4(a.x, a.y, b.x, b.y);
+        }
+      }
+    }
+  }
+  const int tid = blockIdx.x * 128 + threadIdx.x;
+  const int cb = tid >> lg;
+  const int rhs = tid & (nr - 1);
+  const unsigned cw = cb < Vh ? __ldg(pr.coord + cb) : 0u;  // issued before the barrier
+  __syncthreads();
+
+  if (RED == RED_NONE && cb >= Vh) return;
+  const int sl = threadIdx.x >> lg;
+  const int x = cw & 0xff, y = (cw >> 8) & 0xff, z = (cw >> 16) & 0xff, t = cw >> 24;
+  const int s = x + sy * y + sz * z + sw * t;
+  const int stride = Vh * nr;
+
+  float2 ur[3], ui[3], lr[3], li[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) ur[c] = ui[c] = lr[c] = li[c] = make_float2(0.f, 0.f);
+  hop_dir_pair<P, 0>(pr, s, x, g.Lx, 1, 1, 1, rhs, stride, nr, slink[sl][0], slink[sl][1], ur, ui, lr, li);
+  hop_dir_pair<P, 1>(pr, s, y, g.Ly, sy, 1, 1, rhs, stride, nr, slink[sl][2], slink[sl][3], ur, ui, lr, li);
+  hop_dir_pair<P, 2>(pr, s, z, g.Lz, sz, 1, 1, rhs, stride, nr, slink[sl][4], slink[sl][5], ur, ui, lr, li);
+  const int cf = __ldg(pr.tc + t), cbk = __ldg(pr.tc + (t == 0 ? g.Lt - 1 : t - 1));
+  hop_dir_pair<P, 3>(pr, s, t, g.Lt, sw, cf, cbk, rhs, stride, nr, slink[sl][6], slink[sl][7], ur, ui, lr, li);
+  cplx<float> acc[12];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc[c] = {ur[c].x, ui[c].x};
+    acc[3 + c] = {ur[c].y, ui[c].y};
+    acc[6 + c] = {lr[c].x, li[c].x};
+    acc[9 + c] = {lr[c].y, li[c].y};
+  }
+  dslash_epilogue<P, EPI, RED, true>(pr, cb, (long)cb * nr + rhs, (long)stride, rhs, acc, sclov[sl]);
+}
+
+// ------------------------------------------------------------------ variant 6: paired FP32 + pipelined spinors
+// Variant 5 whose eight neighbour spinors are fetched by each thread into its own slots of a
+// kPipe-deep ring in shared memory with asynchronous copies (cp.async, 16 bytes each, L2 only),
+// kPipe - 1 hops ahead of the arithmetic, so a thread has up to kPipe - 1 hops of loads in flight
+// without holding them in registers.  Ring layout [stage][chunk][thread] (float4): each thread
+// reads back only what it copied (a wait on its own copy groups, no barrier), and a warp's
+// accesses are contiguous.  FP32 storage only.
+constexpr int kPipe = 3;
+constexpr size_t kPipeBytes = (size_t)kPipe * 6 * 128 * sizeof(float4);
+
+LQCD_D void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+LQCD_D void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+LQCD_D void cp_async_wait_pipe() { asm volatile("cp.async.wait_group %0;" ::"n"(kPipe - 1) : "memory"); }
+
+template <int K>
+LQCD_D void pipe_issue(const DslashParams& pr, float4* ring, const int (&nb)[8], int stride, bool valid) {
+  if constexpr (K < 8) {
+    if (valid) {
+      float4* dst = ring + (K % kPipe) * 6 * 128 + threadIdx.x;
+      const float4* src = reinterpret_cast<const float4*>(pr.in) + nb[K];
+#pragma unroll
+      for (int c = 0; c < 6; c++) cp_async16(dst + c * 128, src + (long)c * stride);
+    }
+  }
+  cp_async_commit();  // one group per hop (empty past the last), so the wait count stays uniform
+}
+
+template <int K>
+LQCD_D void pipe_hop(const DslashParams& pr, float4* ring, const int (&nb)[8], int stride, int coef, bool valid,
+                     const float4* L, float2 (&ur)[3], float2 (&ui)[3], float2 (&lr)[3], float2 (&li)[3]) {
+  pipe_issue<K + kPipe - 1>(pr, ring, nb, stride, valid);
+  cp_async_wait_pipe();  // this thread's copies of hop K have landed
+  const float4* src = ring + (K % kPipe) * 6 * 128 + threadIdx.x;
+  cplx<float> p[12];
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    const float4 v = src[c * 128];
+    p[2 * c] = {v.x, v.y};
+    p[2 * c + 1] = {v.z, v.w};
+  }
+  if (coef != 0) hop_pair_p<K / 2, (K % 2) == 0>(p, coef, L, ur, ui, lr, li);
+}
+
+// Dynamic shared memory: [fused-reduction scratch | ring | links S x 8 x 9 | clover S x 18] (float4).
+template <int EPI, int RED, int MINB>
+__global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParams pr) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int nr = pr.nrhs;
+  const int lg = __ffs(nr) - 1;
+  const int S = 128 >> lg;
+  float4* ring = reinterpret_cast<float4*>(dsm + pr.pipe_off);
+  float4 (*slink)[8][9] = reinterpret_cast<float4 (*)[8][9]>(ring + kPipe * 6 * 128);
+  float4 (*sclov)[18] = reinterpret_cast<float4 (*)[18]>(slink + S);
+  const Geom& g = pr.g;
+  const int cb0 = blockIdx.x * S;
+  const int Vh = (int)g.Vh;
+  const int sy = g.Lx, sz = g.Lx * g.Ly, sw = sz * g.Lz;
+  const int tid = blockIdx.x * 128 + threadIdx.x;
+  const int cb = tid >> lg;
+  const int rhs = tid & (nr - 1);
+  const bool valid = cb < Vh;
+  const unsigned cw = valid ? __ldg(pr.coord + cb) : 0u;
+  const int x = cw & 0xff, y = (cw >> 8) & 0xff, z = (cw >> 16) & 0xff, t = cw >> 24;
+  const int s = x + sy * y + sz * z + sw * t;
+  const int stride = Vh * nr;
+  int nb[8];  // spinor index of the neighbour of each hop (2 mu: s + mu, 2 mu + 1: s - mu)
+  {
+    const int cm[4] = {x, y, z, t}, Lm[4] = {g.Lx, g.Ly, g.Lz, g.Lt}, sm[4] = {1, sy, sz, sw};
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      nb[2 * mu] = ((s + ((cm[mu] + 1 == Lm[mu]) ? sm[mu] * (1 - Lm[mu]) : sm[mu])) >> 1) * nr + rhs;
+      nb[2 * mu + 1] = ((s + ((cm[mu] == 0) ? sm[mu] * (Lm[mu] - 1) : -sm[mu])) >> 1) * nr + rhs;
+    }
+  }
+  static_assert(kPipe == 3, "two hops are issued ahead");
+  pipe_issue<0>(pr, ring, nb, stride, valid);  // the first hops' copies run under the link staging
+  pipe_issue<1>(pr, ring, nb, stride, valid);
+  for (int j = threadIdx.x; j < 26 * S; j += 128) {
+    if (j < 8 * S) {  // link j & 7 of site j >> 3, third row rebuilt once
+      const int site = j >> 3, k = j & 7, c = cb0 + site;
+      if (c < Vh) {
+        const int mu = k >> 1;
+        int lcb = c, par = pr.out_par;
+        if (k & 1) {  // backward hop: the link of the neighbour s - mu
+          const int xh = c % g.Lxh, yzt = c / g.Lxh, yy = yzt % g.Ly, zt = yzt / g.Ly, zz = zt % g.Lz,
+                    tt = zt / g.Lz;
+          const int xx = 2 * xh + ((pr.out_par + yy + zz + tt) & 1);
+          const int ss = xx + sy * yy + sz * zz + sw * tt;
+          const int cmu = mu == 0 ? xx : (mu == 1 ? yy : (mu == 2 ? zz : tt));
+          const int Lmu = mu == 0 ? g.Lx : (mu == 1 ? g.Ly : (mu == 2 ? g.Lz : g.Lt));
+          const int smu = mu == 0 ? 1 : (mu == 1 ? sy : (mu == 2 ? sz : sw));
+          lcb = (ss + (cmu == 0 ? smu * (Lmu - 1) : -smu)) >> 1;
+          par = 1 - pr.out_par;
+        }
+        cplx<float> u[3][3];
+        load_link<P32>(pr.U, g.Vh, mu, par, lcb, u);
+        float4* L = slink[site][k];
+#pragma unroll
+        for (int e = 0; e < 9; e++) {
+          const cplx<float> v = u[e / 3][e % 3];
+          L[e] = make_float4(v.re, v.re, v.im, v.im);
+        }
+      }
+    } else {  // clover chunk e of site q / 18
+      const int q = j - 8 * S, site = q / 18, e = q - site * 18, c = cb0 + site;
+      if (c < Vh) sclov[site][e] = __ldg(reinterpret_cast<const float4*>(pr.C) + (long)e * Vh + c);
+    }
+  }
+  __syncthreads();
+  if (RED == RED_NONE && !valid) {
+    asm volatile("cp.async.wait_all;" ::: "memory");  // nothing was issued; kept for symmetry
+    return;
+  }
+  const int sl = threadIdx.x >> lg;
+  const int cf = __ldg(pr.tc + t), cbk = __ldg(pr.tc + (t == 0 ? g.Lt - 1 : t - 1));
+  float2 ur[3], ui[3], lr[3], li[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) ur[c] = ui[c] = lr[c] = li[c] = make_float2(0.f, 0.f);
+  pipe_hop<0>(pr, ring, nb, stride, 1, valid, slink[sl][0], ur, ui, lr, li);
+  pipe_hop<1>(pr, ring, nb, stride, 1, valid, slink[sl][1], ur, ui, lr, li);
+  pipe_hop<2>(pr, ring, nb, stride, 1, valid, slink[sl][2], ur, ui, lr, li);
+  pipe_hop<3>(pr, ring, nb, stride, 1, valid, slink[sl][3], ur, ui, lr, li);
+  pipe_hop<4>(pr, ring, nb, stride, 1, valid, slink[sl][4], ur, ui, lr, li);
+  pipe_hop<5>(pr, ring, nb, stride, 1, valid, slink[sl][5], ur, ui, lr, li);
+  pipe_hop<6>(pr, ring, nb, stride, cf, valid, slink[sl][6], ur, ui, lr, li);
+  pipe_hop<7>(pr, ring, nb, stride, cbk, valid, slink[sl][7], ur, ui, lr, li);
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  cplx<float> acc[12];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc[c] = {ur[c].x, ui[c].x};
+    acc[3 + c] = {ur[c].y, ui[c].y};
+    acc[6 + c] = {lr[c].x, li[c].x};
+    acc[9 + c] = {lr[c].y, li[c].y};
+  }
+  dslash_epilogue<P32, EPI, RED, true>(pr, cb, (long)cb * nr + rhs, (long)stride, rhs, acc, sclov[sl]);
+}
+
+// largest dynamic shared memory of a variant-6 launch: 8-double reduction scratch per thread,
+// the ring, and the links and clover of 16 sites
+constexpr size_t kSl3MaxShm = 8 * 128 * sizeof(double) + kPipeBytes + (size_t)kMaxSites * (72 + 18) * sizeof(float4);
+
+template <int EPI, int RED>
+void open_sl3() {
+  cudaFuncSetAttribute(dslash_sl3_kernel<EPI, RED, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSl3MaxShm);
+}
+
+// Raise the dynamic shared-memory limit of every variant-6 instantiation once, before its first
+// launch.
+void open_sl3_all() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  open_sl3<EPI_Y_CH, RED_TS_R0>();
+  open_sl3<EPI_Y_CH, RED_DOT_Z>();
+  open_sl3<EPI_Y_CH, RED_DOT_Y_NORM>();
+  open_sl3<EPI_CH, RED_NONE>();
+  open_sl3<EPI_Y_CH, RED_NONE>();
+  open_sl3<EPI_C_YH, RED_NONE>();
+}
+
+template <int EPI, int RED>
+void launch_sl3(const DslashParams& pr, long blocks, size_t red_shm, cudaStream_t st) {
+  DslashParams q = pr;
+  q.pipe_off = (int)((red_shm + 127) / 128 * 128);
+  const int S = 128 / pr.nrhs;
+  const size_t shm = q.pipe_off + kPipeBytes + (size_t)S * (72 + 18) * sizeof(float4);
+  dslash_sl3_kernel<EPI, RED, 4><<<blocks, 128, shm, st>>>(q);
+  lqcd::count_launch();
+}
+
+bool launch_sl3_e(const DslashParams& pr, int epi, int red, long blocks, size_t red_shm, cudaStream_t st) {
+  if (red == RED_TS_R0) {
+    if (epi != EPI_Y_CH) return false;
+    launch_sl3<EPI_Y_CH, RED_TS_R0>(pr, blocks, red_shm, st);
+  } else if (red == RED_DOT_Z) {
+    if (epi != EPI_Y_CH) return false;
+    launch_sl3<EPI_Y_CH, RED_DOT_Z>(pr, blocks, red_shm, st);
+  } else if (red == RED_DOT_Y_NORM) {
+    if (epi != EPI_Y_CH) return false;
+    launch_sl3<EPI_Y_CH, RED_DOT_Y_NORM>(pr, blocks, red_shm, st);
+  } else if (epi == EPI_CH) {
+    launch_sl3<EPI_CH, RED_NONE>(pr, blocks, red_shm, st);
+  } else if (epi == EPI_Y_CH) {
+    launch_sl3<EPI_Y_CH, RED_NONE>(pr, blocks, red_shm, st);
+  } else if (epi == EPI_C_YH) {
+    launch_sl3<EPI_C_YH, RED_NONE>(pr, blocks, red_shm, st);
+  } else {
+    return false;
+  }
+  return true;
+}
+
+template <int P, int EPI, int RED, int MINB>
+void launch_sl(const DslashParams& pr, long blocks, size_t shm, cudaStream_t st, bool paired) {
+  if (paired)
+    dslash_sl2_kernel<P, EPI, RED, MINB><<<blocks, 128, shm, st>>>(pr);
+  else
+    dslash_sl_kernel<P, EPI, RED, MINB><<<blocks, 128, shm, st>>>(pr);
   lqcd::count_launch();
 }
 
 template <int P, int MINB>
-bool launch_sl_e(const DslashParams& pr, int epi, int red, long blocks, size_t shm, cudaStream_t st) {
+bool launch_sl_e(const DslashParams& pr, int epi, int red, long blocks, size_t shm, cudaStream_t st,
+                 bool paired) {
   if (red == RED_TS_R0) {
     if (epi != EPI_Y_CH) return false;
-    launch_sl<P, EPI_Y_CH, RED_TS_R0, MINB>(pr, blocks, shm, st);
+    launch_sl<P, EPI_Y_CH, RED_TS_R0, MINB>(pr, blocks, shm, st, paired);
   } else if (red == RED_DOT_Z) {
     if (epi != EPI_Y_CH) return false;
-    launch_sl<P, EPI_Y_CH, RED_DOT_Z, MINB>(pr, blocks, shm, st);
+    launch_sl<P, EPI_Y_CH, RED_DOT_Z, MINB>(pr, blocks, shm, st, paired);
   } else if (red == RED_DOT_Y_NORM) {
     if (epi != EPI_Y_CH) return false;
-    launch_sl<P, EPI_Y_CH, RED_DOT_Y_NORM, MINB>(pr, blocks, shm, st);
+    launch_sl<P, EPI_Y_CH, RED_DOT_Y_NORM, MINB>(pr, blocks, shm, st, paired);
   } else if (epi == EPI_CH) {
-    launch_sl<P, EPI_CH, RED_NONE, MINB>(pr, blocks, shm, st);
+    launch_sl<P, EPI_CH, RED_NONE, MINB>(pr, blocks, shm, st, paired);
   } else if (epi == EPI_Y_CH) {
-    launch_sl<P, EPI_Y_CH, RED_NONE, MINB>(pr, blocks, shm, st);
+    launch_sl<P, EPI_Y_CH, RED_NONE, MINB>(pr, blocks, shm, st, paired);
   } else if (epi == EPI_C_YH) {
-    launch_sl<P, EPI_C_YH, RED_NONE, MINB>(pr, blocks, shm, st);
+    launch_sl<P, EPI_C_YH, RED_NONE, MINB>(pr, blocks, shm, st, paired);
   } else {
     return false;
   }
@@ -455,7 +843,7 @@ bool launch_p(const DslashParams& pr, int epi, int red, long blocks, int tpb, si
 
 bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, int red, long blocks, int tpb,
                           size_t red_shm, int variant, cudaStream_t st) {
-  if (prec == P64 || dag || variant < 3 || variant > 4) return false;
+  if (prec == P64 || dag || variant < 3 || variant > 6) return false;
   const long nr = pr.nrhs;
   if (variant == 4) {  // bulk-copy staged spinors, staging depth 3
     if (nr % 32 != 0 || tpb % 32 != 0) return false;
@@ -467,8 +855,17 @@ bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, i
   if (nr < 8 || nr > 128 || (nr & (nr - 1)) != 0 || tpb != 128) return false;
   if (pr.g.Vh % (128 / nr) != 0 || blocks * (128 / nr) != pr.g.Vh) return false;
   if (12 * pr.g.Vh * nr >= (1L << 31)) return false;
-  if (prec == P32) return launch_sl_e<P32, 6>(pr, epi, red, blocks, red_shm, st);
-  return launch_sl_e<P16, 6>(pr, epi, red, blocks, red_shm, st);
+  if (variant == 6) {  // paired arithmetic and pipelined spinor copies: FP32 storage only
+    if (prec != P32 || red_shm > 8 * 128 * sizeof(double)) return false;
+    open_sl3_all();
+    return launch_sl3_e(pr, epi, red, blocks, red_shm, st);
+  }
+  if (variant == 5) {  // paired operands take aligned register pairs: cap 96 instead of 80
+    if (prec == P32) return launch_sl_e<P32, 5>(pr, epi, red, blocks, red_shm, st, true);
+    return launch_sl_e<P16, 5>(pr, epi, red, blocks, red_shm, st, true);
+  }
+  if (prec == P32) return launch_sl_e<P32, 6>(pr, epi, red, blocks, red_shm, st, false);
+  return launch_sl_e<P16, 6>(pr, epi, red, blocks, red_shm, st, false);
 }
 
 unsigned long long dslash_pipe_timeouts(bool reset) {
