@@ -182,17 +182,19 @@ __global__ void k_nn_layer(const float2* in, float2* out, const WT* W, NNGeo G) 
 //   B[o][(p, 0, c)] = Re W[p][o][c],  B[o][(p, 1, c)] = -Im W,  B[C_out + o][(p, 0, c)] = Im W,
 //   B[C_out + o][(p, 1, c)] = Re W,   D_a[q][o] = Re out_o(q)[a],  D_a[q][C_out + o] = Im out_o(q)[a].
 //
-// Persistent, warp-specialised CTA of 160 threads over tiles of 128 pairs:
-//   warps 0-3 (one thread per pair, row = thread) transport every input channel along one path
-//     chunk (one path for C_in = 8, two for C_in = 4: 16 K columns per colour) and write the three
-//     colours' rows into a ring of kRing chunk buffers; after the tile's last chunk they read the
-//     FP32 result rows out of tensor memory and store them;
-//   warp 4 allocates tensor memory and, one lane, issues the three MMAs (M = 128, N = 16, K = 16)
-//     of each staged chunk, accumulating into one of two tensor-memory result buffers (so the
-//     next tile's MMAs overlap the previous tile's read-out).
-// Hand-offs are mbarriers: full[s] (128 producer arrivals) / empty[s] (MMA completion) per ring
-// slot, dfull[d] (MMA completion) / dempty[d] (128 producer arrivals) per result buffer.  Every wait has an
-// iteration limit; a wait that runs out raises a CTA flag that stops every loop, the kernel
+// Persistent CTA of 128 threads (one thread per pair, row = thread) over tiles of 128 pairs.  Each
+// thread transports every input channel along one path chunk (one path for C_in = 8, two for
+// C_in = 4: 16 K columns per colour) and writes the three colours' rows into a ring of kRing chunk
+// buffers; one lane of warp 0, once the whole chunk is staged, issues its three MMAs (M = 128,
+// N = 16, K = 16), accumulating into one of two tensor-memory result buffers (so a tile's MMAs
+// overlap the previous tile's read-out); after a tile's last chunk every thread reads its FP32
+// result row out of tensor memory and stores it.  No warp is set aside for the MMAs, so four CTAs
+// (16 warps of transports) fit an SM.
+// Hand-offs are mbarriers: full[s] (128 arrivals) / empty[s] (MMA completion) per ring slot and
+// dfull[d] (MMA completion) per result buffer.  A result buffer is reused two tiles later, after
+// every thread has read it out and then staged its part of the next tile (so the full barrier of
+// that tile's first chunk orders the read-out before the new MMAs).  Every wait has an iteration
+// and a time limit; a wait that runs out raises a CTA flag that stops every loop, the kernel
 // counts it in g_nn_tc_timeouts, waits (bounded) for its MMAs in flight and frees its tensor
 // memory before returning.
 constexpr int kNNTile = 128;                      // pairs per tile (MMA M)
@@ -200,7 +202,7 @@ constexpr int kRing = 4;                          // staged chunks in flight
 constexpr int kChunkColour = kNNTile * 16 * 2;    // bytes of one colour's 128 x 16 BF16 chunk
 constexpr int kChunkBytes = 3 * kChunkColour;     // one ring slot
 constexpr int kNNWaitLimit = 1 << 22;
-constexpr int kNNThreads = 160;
+constexpr int kNNThreads = 128;
 __device__ int g_nn_tc_timeouts;
 
 template <int CIN>
@@ -233,10 +235,13 @@ struct NNTiles {
   int Bz;      // z-planes per slab
   long tps;    // tiles per parity per slab
   long ntiles; // all tiles
+  int npar;    // 2: even and odd output sites; 1: even output sites only (the odd ones are not needed)
+  int in_even; // 1: the input is zero on odd sites, so even outputs take the identity path only and
+               // odd outputs the eight hops only
 };
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kNNThreads, 3) k_nn_layer_tc(const float2* in, float2* out,
+__global__ void __launch_bounds__(kNNThreads, 4) k_nn_layer_tc(const float2* in, float2* out,
                                                                const __nv_bfloat162* W, NNGeo G, NNTiles TL) {
   constexpr int NCH = nn_tc_chunks<CIN>();
   constexpr int K = nn_tc_k<CIN>();
@@ -247,9 +252,8 @@ __global__ void __launch_bounds__(kNNThreads, 3) k_nn_layer_tc(const float2* in,
   uint64_t* full = bars;                               // [kRing]
   uint64_t* empty = bars + kRing;                      // [kRing]
   uint64_t* dfull = bars + 2 * kRing;                  // [2]
-  uint64_t* dempty = bars + 2 * kRing + 2;             // [2]
-  uint64_t* drain = bars + 2 * kRing + 4;              // [1] (failure path)
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 2 * kRing + 5);
+  uint64_t* drain = bars + 2 * kRing + 2;              // [1] (failure path)
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 2 * kRing + 3);
   volatile int* fail = reinterpret_cast<volatile int*>(tbase + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long V = 2 * G.g.Vh;
@@ -271,114 +275,90 @@ __global__ void __launch_bounds__(kNNThreads, 3) k_nn_layer_tc(const float2* in,
   }
   if (tid == 0) {
     for (int i = 0; i < kRing; i++) {
-      tc::mbar_init(full + i, 128);
+      tc::mbar_init(full + i, kNNThreads);
       tc::mbar_init(empty + i, 1);
     }
-    for (int i = 0; i < 2; i++) {
-      tc::mbar_init(dfull + i, 1);
-      tc::mbar_init(dempty + i, 128);
-    }
+    tc::mbar_init(dfull, 1);
+    tc::mbar_init(dfull + 1, 1);
     tc::mbar_init(drain, 1);
     *fail = 0;
   }
-  if (warp == 4) tc::tmem_alloc(tbase, 128);
+  if (warp == 0) tc::tmem_alloc(tbase, 128);
   tc::fence_proxy_async();
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tbase;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 16);
+  const uint32_t r0 = tc::smem_u32(ring), b0 = tc::smem_u32(sB);
 
-  if (warp < 4) {  // ---------------------------------------------------------------- producers
-    long it = 0;      // tiles done by this CTA
-    long chunk = 0;   // chunks staged by this CTA
-    for (long tile = blockIdx.x; tile < ntiles && !*fail; tile += gridDim.x, it++) {
-      const long sl = tile / (2 * TL.tps), r = tile - sl * 2 * TL.tps;
-      const long q = (r >> 1) * kNNTile + tid;  // pair within the slab's sites of parity r & 1
-      const bool valid = q < slab_pairs;
-      long se = 0, cb = 0;
-      int n = 0, par = 0, x = 0, y = 0, z = 0, t = 0;
-      if (valid) {
-        const long zb = sl / G.g.Lt, ts = sl - zb * G.g.Lt;
-        const long cb0 = (long)G.g.Lxh * G.g.Ly * (zb * TL.Bz + (long)G.g.Lz * ts);
-        const long i = q / G.N;
-        n = (int)(q - i * G.N);
-        se = (r & 1) * G.g.Vh + cb0 + i;
-        nn_site(G, se, par, cb, x, y, z, t);
-      }
-      const uint32_t roff = (uint32_t)((tid >> 3) * 256 + (tid & 7) * 16);  // row offset in a chunk
-      for (int ch = 0; ch < NCH; ch++, chunk++) {
-        const int slot = (int)(chunk % kRing);
-        const long use = chunk / kRing;
-        if (use > 0 && !wait_or_flag(empty + slot, (uint32_t)((use - 1) & 1), fail)) break;
-        unsigned char* buf = ring + slot * kChunkBytes + roff;
-#pragma unroll
-        for (int h = 0; h < 16 / (2 * CIN); h++) {  // paths of this chunk
-          const int p = ch * (16 / (2 * CIN)) + h;
-          cplx<float> th[CIN][3];
-          bool on = false;
-          if (valid && p < NN_PATHS) on = path_vectors<CIN>(G, in, p, par, cb, x, y, z, t, n, th);
-          if (!on) {
-#pragma unroll
-            for (int c = 0; c < CIN; c++)
-#pragma unroll
-              for (int a = 0; a < 3; a++) th[c][a] = {0.f, 0.f};
-          }
-#pragma unroll
-          for (int a = 0; a < 3; a++) {
-            if (CIN == 8) {  // re of the 8 channels in core column 0, im in core column 1
-              uint4 vr, vi;
-              vr.x = bf16x2(th[0][a].re, th[1 % CIN][a].re);
-              vr.y = bf16x2(th[2 % CIN][a].re, th[3 % CIN][a].re);
-              vr.z = bf16x2(th[4 % CIN][a].re, th[5 % CIN][a].re);
-              vr.w = bf16x2(th[6 % CIN][a].re, th[7 % CIN][a].re);
-              vi.x = bf16x2(th[0][a].im, th[1 % CIN][a].im);
-              vi.y = bf16x2(th[2 % CIN][a].im, th[3 % CIN][a].im);
-              vi.z = bf16x2(th[4 % CIN][a].im, th[5 % CIN][a].im);
-              vi.w = bf16x2(th[6 % CIN][a].im, th[7 % CIN][a].im);
-              *reinterpret_cast<uint4*>(buf + a * kChunkColour) = vr;
-              *reinterpret_cast<uint4*>(buf + a * kChunkColour + 128) = vi;
-            } else {  // 4 channels: re 0..3 then im 0..3 in core column h
-              uint4 v;
-              v.x = bf16x2(th[0][a].re, th[1 % CIN][a].re);
-              v.y = bf16x2(th[2 % CIN][a].re, th[3 % CIN][a].re);
-              v.z = bf16x2(th[0][a].im, th[1 % CIN][a].im);
-              v.w = bf16x2(th[2 % CIN][a].im, th[3 % CIN][a].im);
-              *reinterpret_cast<uint4*>(buf + a * kChunkColour + h * 128) = v;
-            }
-          }
-        }
-        tc::fence_proxy_async();  // these generic-proxy writes, before the MMA reads them
-        tc::mbar_arrive(full + slot);
-      }
-      if (*fail) break;
-      // read-out of this tile's result buffer
-      const int d = (int)(it & 1);
-      if (!wait_or_flag(dfull + d, (uint32_t)((it >> 1) & 1), fail)) break;
-      tc::fence_after_sync();
-#pragma unroll
-      for (int a = 0; a < 3; a++) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * 64 + a * 16), v);
-        if (valid) {
-#pragma unroll
-          for (int o = 0; o < COUT; o++) out[((long)(o * 3 + a) * V + se) * G.N + n] = make_float2(v[o], v[COUT + o]);
-        }
-      }
-      tc::fence_before_sync();
-      tc::mbar_arrive(dempty + d);
+  long it = 0;     // tiles done by this CTA
+  long chunk = 0;  // chunks staged by this CTA
+  for (long tile = blockIdx.x; tile < ntiles && !*fail; tile += gridDim.x, it++) {
+    const long sl = tile / (TL.npar * TL.tps), r = tile - sl * TL.npar * TL.tps;
+    const int tpar = TL.npar == 2 ? (int)(r & 1) : 0;
+    const long q = (TL.npar == 2 ? r >> 1 : r) * kNNTile + tid;  // pair within the slab's sites of parity tpar
+    const bool valid = q < slab_pairs;
+    long se = 0, cb = 0;
+    int n = 0, par = 0, x = 0, y = 0, z = 0, t = 0;
+    if (valid) {
+      const long zb = sl / G.g.Lt, ts = sl - zb * G.g.Lt;
+      const long cb0 = (long)G.g.Lxh * G.g.Ly * (zb * TL.Bz + (long)G.g.Lz * ts);
+      const long i = q / G.N;
+      n = (int)(q - i * G.N);
+      se = tpar * G.g.Vh + cb0 + i;
+      nn_site(G, se, par, cb, x, y, z, t);
     }
-  } else {  // ---------------------------------------------------------------------- MMA issuer
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 16);
-    const uint32_t r0 = tc::smem_u32(ring), b0 = tc::smem_u32(sB);
-    long it = 0, chunk = 0;
-    for (long tile = blockIdx.x; tile < ntiles && !*fail; tile += gridDim.x, it++) {
-      const int d = (int)(it & 1);
-      if (it >= 2 && !wait_or_flag(dempty + d, (uint32_t)(((it >> 1) - 1) & 1), fail)) break;
-      tc::fence_after_sync();
-      for (int ch = 0; ch < NCH; ch++, chunk++) {
-        const int slot = (int)(chunk % kRing);
-        if (!wait_or_flag(full + slot, (uint32_t)((chunk / kRing) & 1), fail)) break;
+    const int d = (int)(it & 1);
+    const uint32_t roff = (uint32_t)((tid >> 3) * 256 + (tid & 7) * 16);  // row offset in a chunk
+    for (int ch = 0; ch < NCH; ch++, chunk++) {
+      const int slot = (int)(chunk % kRing);
+      const long use = chunk / kRing;
+      if (use > 0 && !wait_or_flag(empty + slot, (uint32_t)((use - 1) & 1), fail)) break;
+      unsigned char* buf = ring + slot * kChunkBytes + roff;
+#pragma unroll
+      for (int h = 0; h < 16 / (2 * CIN); h++) {  // paths of this chunk
+        const int p = ch * (16 / (2 * CIN)) + h;
+        cplx<float> th[CIN][3];
+        bool on = false;
+        const bool live = !TL.in_even || ((tpar == 0) == (p == 0));  // else the input there is zero
+        if (valid && p < NN_PATHS && live) on = path_vectors<CIN>(G, in, p, par, cb, x, y, z, t, n, th);
+        if (!on) {
+#pragma unroll
+          for (int c = 0; c < CIN; c++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) th[c][a] = {0.f, 0.f};
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          if (CIN == 8) {  // re of the 8 channels in core column 0, im in core column 1
+            uint4 vr, vi;
+            vr.x = bf16x2(th[0][a].re, th[1 % CIN][a].re);
+            vr.y = bf16x2(th[2 % CIN][a].re, th[3 % CIN][a].re);
+            vr.z = bf16x2(th[4 % CIN][a].re, th[5 % CIN][a].re);
+            vr.w = bf16x2(th[6 % CIN][a].re, th[7 % CIN][a].re);
+            vi.x = bf16x2(th[0][a].im, th[1 % CIN][a].im);
+            vi.y = bf16x2(th[2 % CIN][a].im, th[3 % CIN][a].im);
+            vi.z = bf16x2(th[4 % CIN][a].im, th[5 % CIN][a].im);
+            vi.w = bf16x2(th[6 % CIN][a].im, th[7 % CIN][a].im);
+            *reinterpret_cast<uint4*>(buf + a * kChunkColour) = vr;
+            *reinterpret_cast<uint4*>(buf + a * kChunkColour + 128) = vi;
+          } else {  // 4 channels: re 0..3 then im 0..3 in core column h
+            uint4 v;
+            v.x = bf16x2(th[0][a].re, th[1 % CIN][a].re);
+            v.y = bf16x2(th[2 % CIN][a].re, th[3 % CIN][a].re);
+            v.z = bf16x2(th[0][a].im, th[1 % CIN][a].im);
+            v.w = bf16x2(th[2 % CIN][a].im, th[3 % CIN][a].im);
+            *reinterpret_cast<uint4*>(buf + a * kChunkColour + h * 128) = v;
+          }
+        }
+      }
+      tc::fence_proxy_async();  // these generic-proxy writes, before the MMA reads them
+      tc::fence_before_sync();  // and this thread's earlier read-out, before the MMAs that follow
+      tc::mbar_arrive(full + slot);
+      if (warp == 0) {  // the chunk's MMAs, once every thread has staged its row
+        if (!wait_or_flag(full + slot, (uint32_t)(use & 1), fail)) break;
         tc::fence_after_sync();
         if (lane == 0) {
 #pragma unroll
@@ -392,13 +372,26 @@ __global__ void __launch_bounds__(kNNThreads, 3) k_nn_layer_tc(const float2* in,
         __syncwarp();
       }
     }
+    if (*fail) break;
+    // read-out of this tile's result buffer
+    if (!wait_or_flag(dfull + d, (uint32_t)((it >> 1) & 1), fail)) break;
+    tc::fence_after_sync();
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * 64 + a * 16), v);
+      if (valid) {
+#pragma unroll
+        for (int o = 0; o < COUT; o++) out[((long)(o * 3 + a) * V + se) * G.N + n] = make_float2(v[o], v[COUT + o]);
+      }
+    }
   }
   __syncthreads();
   if (*fail) {
     if (tid == 0) atomicAdd(&g_nn_tc_timeouts, 1);
     // let MMAs already issued finish before the tensor memory is freed: one more commit, waited
     // on with a limit
-    if (warp == 4) {
+    if (warp == 0) {
       if (lane == 0) tc::mma_commit(drain);
       __syncwarp();
       tc::mbar_wait(drain, 0, kNNWaitLimit);
@@ -407,17 +400,17 @@ __global__ void __launch_bounds__(kNNThreads, 3) k_nn_layer_tc(const float2* in,
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 4) tc::tmem_dealloc(tmem, 128);
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
 
 template <int CIN, int COUT>
 static size_t nn_tc_smem() {
-  return (size_t)kRing * kChunkBytes + (size_t)16 * nn_tc_k<CIN>() * 2 + (2 * kRing + 5) * 8 + 16;
+  return (size_t)kRing * kChunkBytes + (size_t)16 * nn_tc_k<CIN>() * 2 + (2 * kRing + 3) * 8 + 16;
 }
 
-// Three CTAs per SM: 128 registers x 160 threads each, 52-54 KB of shared memory each, and
-// 3 x 128 of the SM's 512 tensor-memory columns.
-constexpr int kNNCtasPerSM = 3;
+// Four CTAs per SM: 128 registers x 128 threads each, 52-54 KB of shared memory each, and
+// 4 x 128 of the SM's 512 tensor-memory columns.
+constexpr int kNNCtasPerSM = 4;
 
 template <int CIN, int COUT>
 static void tc_open() {
@@ -445,8 +438,8 @@ static void tc_open_all() {
 }
 
 template <int CIN, int COUT>
-static void tc_launch(const float2* in, float2* out, const __nv_bfloat162* W, const NNGeo& G,
-                      cudaStream_t st) {
+static void tc_launch(const float2* in, float2* out, const __nv_bfloat162* W, const NNGeo& G, cudaStream_t st,
+                      bool in_even, bool out_even) {
   tc_open_all();
   // largest Bz dividing Lz whose slab (both parities) holds at most 28 MB of input channels
   const double site_bytes = (double)CIN * 3 * G.N * sizeof(float2);
@@ -455,22 +448,25 @@ static void tc_launch(const float2* in, float2* out, const __nv_bfloat162* W, co
   for (int b = 1; b <= G.g.Lz; b++)
     if (G.g.Lz % b == 0 && (double)G.g.Lx * G.g.Ly * b * site_bytes <= 28e6) TL.Bz = b;
   TL.tps = ((long)G.g.Lxh * G.g.Ly * TL.Bz * G.N + kNNTile - 1) / kNNTile;
-  TL.ntiles = (long)(G.g.Lz / TL.Bz) * G.g.Lt * 2 * TL.tps;
+  TL.npar = out_even ? 1 : 2;
+  TL.in_even = in_even ? 1 : 0;
+  TL.ntiles = (long)(G.g.Lz / TL.Bz) * G.g.Lt * TL.npar * TL.tps;
   const long blocks = TL.ntiles < g_tc_ctas ? TL.ntiles : g_tc_ctas;
   k_nn_layer_tc<CIN, COUT><<<(unsigned)blocks, kNNThreads, nn_tc_smem<CIN, COUT>(), st>>>(in, out, W, G, TL);
   count_launch();
 }
 
+// in_even: the input vanishes on odd sites; out_even: only the even output sites are wanted.
 static void layer_launch_tc(int l_in, int l_out, const float2* in, float2* out, const __nv_bfloat162* W,
-                            const NNGeo& G, cudaStream_t st) {
+                            const NNGeo& G, cudaStream_t st, bool in_even = false, bool out_even = false) {
   if (l_in == 4 && l_out == 8)
-    tc_launch<4, 8>(in, out, W, G, st);
+    tc_launch<4, 8>(in, out, W, G, st, in_even, out_even);
   else if (l_in == 8 && l_out == 8)
-    tc_launch<8, 8>(in, out, W, G, st);
+    tc_launch<8, 8>(in, out, W, G, st, in_even, out_even);
   else if (l_in == 8 && l_out == 4)
-    tc_launch<8, 4>(in, out, W, G, st);
+    tc_launch<8, 4>(in, out, W, G, st, in_even, out_even);
   else
-    tc_launch<4, 4>(in, out, W, G, st);
+    tc_launch<4, 4>(in, out, W, G, st, in_even, out_even);
 }
 
 int nn_tc_timeouts(bool reset) {
@@ -803,8 +799,11 @@ int nn_get_weights(lqcd_ctx* c, float* w_host) {
 
 // Network on NN-layout fields (N samples); bf16 = 1 uses the inference weights.  a, b: ping-pong
 // buffers of 8 channels; the result is in the returned pointer (4 channels).
+// eo (tensor-core path): h0 vanishes on odd sites and only the even sites of the result are used
+// (the even-odd preconditioned system's residual and correction), so the first layer skips the
+// zero paths and the last layer the odd sites.
 static float2* nn_forward(lqcd_ctx* c, const float2* h0, float2* a, float2* b, int N, int domain, bool bf16,
-                          cudaStream_t st, bool tc = false) {
+                          cudaStream_t st, bool tc = false, bool eo = false) {
   NNGeo G = nn_geo(c, N, domain);
   const float2* cur = h0;
   float2* bufs[2] = {a, b};
@@ -812,7 +811,8 @@ static float2* nn_forward(lqcd_ctx* c, const float2* h0, float2* a, float2* b, i
     float2* out = bufs[l & 1];
     const int off = nn_layer_offset(l);
     if (tc)
-      layer_launch_tc(NN_W[l], NN_W[l + 1], cur, out, (const __nv_bfloat162*)c->nn_w16 + off, G, st);
+      layer_launch_tc(NN_W[l], NN_W[l + 1], cur, out, (const __nv_bfloat162*)c->nn_w16 + off, G, st,
+                      eo && l == 0, eo && l == NN_LAYERS - 1);
     else if (bf16)
       layer_launch<__nv_bfloat162>(NN_W[l], NN_W[l + 1], cur, out, (const __nv_bfloat162*)c->nn_w16 + off, G, st);
     else
@@ -836,7 +836,7 @@ void nn_precondition(lqcd_ctx* c, const Inner& in, const void* r, void* z, const
   k_nn_from_spinor<<<(n + 255) / 256, 256, 0, st>>>(r, h0, g, N, in.si, in.nseg, pscale);
   count_launch();
   const int domain = in.tc == c->d_tc_dom && c->d_tc_dom != c->d_tc_full;
-  float2* out = nn_forward(c, h0, a, b, N, domain, true, st, true);
+  float2* out = nn_forward(c, h0, a, b, N, domain, true, st, true, true);
   k_nn_to_spinor<<<(g.Vh * N + 255) / 256, 256, 0, st>>>(out, z, g, N, in.si, in.nseg, ipscale);
   count_launch();
 }
