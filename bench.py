@@ -89,6 +89,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement (tuning runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps and e2e (no solver comparison, sweep or roofline)")
+    ap.add_argument("--profile-nn", action="store_true",
+                    help="time the network preconditioner (FP32 CUDA-core and tensor-core forms) on the workload's "
+                         "lattice with --dslash-nrhs samples (default 16), a few applications each (small command "
+                         "for ncu)")
     ap.add_argument("--profile-dslash", action="store_true",
                     help="only time the dslash kernels of the workload (small command for ncu captures)")
     ap.add_argument("--profile-step", action="store_true",
@@ -542,6 +546,28 @@ def run_ours(args, rank, world):
     return res
 
 
+def captured_traffic(variant, site_rhs):
+    """DRAM bytes of one FP32 variant-3 launch, scaled from the committed ncu capture
+    (profiles/dslash_f32_24x24x24x48_nrhs16.md: bytes per (site, RHS)) to site_rhs pairs; None
+    when another variant runs or the kernel's sources changed since the capture."""
+    import hashlib
+    if variant != 3:
+        return None
+    try:
+        with open(os.path.join(ROOT, "profiles", "dslash_f32_24x24x24x48_nrhs16.md")) as f:
+            rec = dict(line.split(":", 1) for line in f.read().splitlines()
+                       if line.startswith(("source_sha256_16:", "traffic_bytes_per_site_rhs:")))
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for name in ("dslash_staged.cu", "dslash_ops.cuh", "lqcd_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_37049_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if rec.get("source_sha256_16", "").split()[0:1] != [h.hexdigest()[:16]]:
+        return None
+    return float(rec["traffic_bytes_per_site_rhs"]) * float(site_rhs)
+
+
 def extras(W, peak, peak_kind, dev):
     """Solvers on one sample, domain extents 8 and 12, and the dslash rooflines (outside the timed
     region)."""
@@ -583,7 +609,10 @@ def extras(W, peak, peak_kind, dev):
     out["solver_sample"] = "full-operator perambulator columns of %d RHS (t=%d, colour vectors 0..%d, 4 spins)" % (
         4 * nj, W.t_src[0], nj - 1)
     out["speedup_vs_plain"] = {k: v["rhs_per_s"] / plain for k, v in solvers.items()}
-    # domain extents swept beside the timed tiling: one source group, the first block
+    # domain extents swept beside the timed tiling: one source group, the first block (the solver
+    # samples' work buffers released first: the sweep's inputs are torch allocations)
+    ctx.release_workspace()
+    torch.cuda.empty_cache()
     sweep = {}
     for ext, tiling in W.wl["sweep"].items():
         ctx.set_domains(tiling)
@@ -609,6 +638,8 @@ def extras(W, peak, peak_kind, dev):
     if sweep:
         out["domain_sweep"] = sweep
     # dslash rooflines of the dominant kernel (FP32 hopping + inverse clover at the RHS block)
+    ctx.release_workspace()
+    torch.cuda.empty_cache()
     dsl = {}
     nbat = W.rhs_block // W.pipeline  # right-hand sides of one launch
     n64 = min(nbat, 4 if np.prod(W.dims) > 24 ** 3 * 48 else nbat)
@@ -619,7 +650,7 @@ def extras(W, peak, peak_kind, dev):
     v32 = int(W.tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(nbat), 0))
     kname = {3: "dslash_sl_kernel", 4: "dslash_pipe_kernel"}.get(v32, "dslash_kernel")
     out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                       "traffic": None, "peak_kind": peak_kind,
+                       "traffic": captured_traffic(v32, np.prod(W.dims) // 2 * nbat), "peak_kind": peak_kind,
                        "kernel": "%s<P32,EPI_CH> (launch variant %d: eo hopping + A^-1, %d RHS)" % (kname, v32,
                                                                                                   nbat),
                        "algo_bytes_per_launch": dsl["f32"]["bytes"]}
@@ -655,6 +686,36 @@ def profile_dslash(args):
             ctx.set_dslash_variant(prec, nr, v)
             ms, by = ctx.dslash_bench(prec, nr, 3, True)
             out["%s_v%d" % (name, v)] = {"nrhs": nr, "ms": ms, "GBs": by / ms / 1e6, "algo_bytes": by}
+    print(json.dumps(out), flush=True)
+
+
+def profile_nn(args):
+    """The gauge-covariant network on the workload's lattice: FP32 CUDA-core layers and the
+    tensor-core layers, 2 + 3 applications each on N random samples (device buffers)."""
+    import torch
+    from lqcd_inputs import gauge_field
+    from paper_2609_37049_b300 import Context, lqcd
+    wl = WORKLOADS[args.workload]
+    torch.cuda.set_device(0)
+    ctx = Context(wl["dims"])
+    ctx.gauge_upload(gauge_field(wl["dims"], wl["eps"], wl["gauge_seed"]), wl["kappa"], wl["csw"])
+    ctx.nn_set_weights(lqcd.nn_initial_weights(3))
+    n = args.dslash_nrhs or 16
+    g = torch.Generator(device="cuda").manual_seed(11)
+    x = torch.randn((n, int(np.prod(wl["dims"])), 4, 3), dtype=torch.complex64, device="cuda", generator=g)
+    out = {}
+    for name, f in (("fp32", ctx.nn_apply), ("tensor_core", ctx.nn_apply_tc)):
+        o = torch.zeros_like(x)
+        for _ in range(2):
+            f(x, o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            f(x, o)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"samples": n, "ms_per_application": e0.elapsed_time(e1) / 3}
     print(json.dumps(out), flush=True)
 
 
@@ -729,6 +790,9 @@ def main():
     args = parse()
     if args.profile_dslash:
         profile_dslash(args)
+        return
+    if args.profile_nn:
+        profile_nn(args)
         return
     rank, world = dist_init()
     if args.impl == "reference":

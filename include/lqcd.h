@@ -133,6 +133,11 @@ void lqcd_default_params(lqcd_solve_params* p);
 int lqcd_create(lqcd_ctx** out, const int L[4], int bc_t, void* stream);
 int lqcd_destroy(lqcd_ctx* ctx);
 int lqcd_set_stream(lqcd_ctx* ctx, void* stream);
+/* Free the device work buffers the context keeps between calls (solver vectors, scratch) and the
+ * CUDA graphs captured on them, after waiting for the context's queued work.  The next call that
+ * needs them allocates them again.  For callers that make large allocations of their own between
+ * library calls.  The gauge field, clover and network weights stay.  Errors: INVALID_ARG (NULL). */
+int lqcd_release_workspace(lqcd_ctx* ctx);
 /* Message of the last error on this context; with ctx = NULL, of the last failed call that takes
  * no context (lqcd_create, lqcd_disc_correlator_noalloc). */
 const char* lqcd_last_error(const lqcd_ctx* ctx);

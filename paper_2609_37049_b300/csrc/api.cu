@@ -485,6 +485,15 @@ int lqcd_destroy(lqcd_ctx* c) {
   return LQCD_OK;
 }
 
+int lqcd_release_workspace(lqcd_ctx* c) {
+  if (!c) return LQCD_ERR_INVALID_ARG;
+  drop_graphs(c);
+  for (auto& kv : c->ws) cudaFree(kv.second.p);
+  c->ws.clear();
+  for (int i = 0; i < 3; i++) c->nn_buf[i] = nullptr;
+  return cuda_check(c, "release_workspace");
+}
+
 int lqcd_set_stream(lqcd_ctx* c, void* stream) {
   if (!c) return LQCD_ERR_INVALID_ARG;
   c->user_stream = (cudaStream_t)stream;

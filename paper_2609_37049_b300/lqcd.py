@@ -36,6 +36,7 @@ EXPORTED = [
     "lqcd_nn_loss_grad", "lqcd_nn_train", "lqcd_tune_dslash", "lqcd_set_dslash_variant", "lqcd_schur_apply",
     "lqcd_conn_correlator", "lqcd_nr_estimator", "lqcd_ape_smear", "lqcd_smeared_links",
     "lqcd_perambulator_cols", "lqcd_window_average", "lqcd_nn_apply_tc", "lqcd_nn_loss_grad_bf16",
+    "lqcd_release_workspace",
 ]
 
 NN_WIDTHS = (4, 8, 8, 8, 4)
@@ -367,6 +368,10 @@ class Context:
         bt, ms = ctypes.c_int(), ctypes.c_double()
         self._check(_lib.lqcd_tune_dslash(self.h, int(prec), int(nrhs), ctypes.byref(bt), ctypes.byref(ms)))
         return bt.value, ms.value
+
+    def release_workspace(self):
+        """Free the library's work buffers (re-created on demand), e.g. before large torch allocations."""
+        return self._check(_lib.lqcd_release_workspace(self.h))
 
     def set_dslash_variant(self, prec, nrhs, variant):
         return self._check(_lib.lqcd_set_dslash_variant(self.h, int(prec), int(nrhs), int(variant)))

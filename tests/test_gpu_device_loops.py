@@ -110,3 +110,17 @@ def test_pipelined_perambulators_match_the_oracle():
         want = perambulators(o, V, t_src)
         for k in range(len(t_src)):
             assert np.linalg.norm(taus[2][k] - want[k]) / np.linalg.norm(want[k]) < 1e-9
+
+
+def test_release_workspace_then_solve_again():
+    """lqcd_release_workspace frees the work vectors and the graphs captured on them; the next solve
+    allocates and captures them again and returns the same solution bit for bit."""
+    case = ROUGH
+    U = gauge(case, 1405)
+    ctx = _ctx(case, U)
+    b = random_spinors(case["dims"], 4, 1406)
+    kw = dict(SOLVERS["mixed32"], rhs_block=4, use_graph=1)
+    x1, s1, _ = _solve(ctx, b, False, **kw)
+    ctx.release_workspace()
+    x2, s2, _ = _solve(ctx, b, False, **kw)
+    assert np.array_equal(x1, x2) and np.array_equal(s1.iters, s2.iters) and s2.device_loops == s1.device_loops
