@@ -680,7 +680,7 @@ def profile_dslash(args):
     out = {}
     for name, prec in (("f32", lqcd.LQCD_PREC_F32), ("f16", lqcd.LQCD_PREC_F16), ("f64", lqcd.LQCD_PREC_F64),
                        ("df_res", lqcd.LQCD_PREC_DF)):
-        for v in (range(3) if prec in (lqcd.LQCD_PREC_F64, lqcd.LQCD_PREC_DF) else range(7)):
+        for v in (range(3) if prec in (lqcd.LQCD_PREC_F64, lqcd.LQCD_PREC_DF) else range(8)):
             if args.dslash_variant >= 0 and v != args.dslash_variant:
                 continue
             ctx.set_dslash_variant(prec, nr, v)

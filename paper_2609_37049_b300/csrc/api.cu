@@ -1068,7 +1068,7 @@ extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_varia
   cudaEventCreate(&e1);
   double best = 1e30;
   int bt = 0;
-  const int nvar = P == P64 || P == PDF ? 3 : 7;  // the staged variants 3-6 are FP32 / FP16 only
+  const int nvar = P == P64 || P == PDF ? 3 : 8;  // the staged variants 3-7 are FP32 / FP16 only
   for (int var = 0; var < nvar; var++) {
     launch(var);
     cudaEventRecord(e0, c->work);
@@ -1094,7 +1094,7 @@ extern "C" int lqcd_tune_dslash(lqcd_ctx* c, int prec, int nrhs, int* best_varia
 }
 
 extern "C" int lqcd_set_dslash_variant(lqcd_ctx* c, int prec, int nrhs, int variant) {
-  if (!c || nrhs < 1 || variant < 0 || variant > 6 || prec < LQCD_PREC_F64 || prec > LQCD_PREC_DF)
+  if (!c || nrhs < 1 || variant < 0 || variant > 7 || prec < LQCD_PREC_F64 || prec > LQCD_PREC_DF)
     return set_error(c, LQCD_ERR_INVALID_ARG, "set_dslash_variant: bad arguments");
   const int P = internal_prec(prec);
   c->tuned_variant[(long)P * 100000 + nrhs] = variant;

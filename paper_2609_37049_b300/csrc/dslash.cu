@@ -139,7 +139,7 @@ void launch_dslash(const Geom& g, const DslashCall& c, cudaStream_t st, int vari
   pr.b = c.b;
   pr.pipe_off = 0;
   const bool dag = c.dagger != 0;
-  if (variant < 0 || variant > 6) variant = 0;
+  if (variant < 0 || variant > 7) variant = 0;
   if (c.red == RED_NONE) {
     long nthreads = g.Vh * (long)c.nrhs;
     const int tpb = 128;

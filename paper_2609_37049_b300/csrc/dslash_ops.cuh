@@ -272,6 +272,9 @@ LQCD_D void dslash_epilogue(const DslashParams& pr, long cb, long idx, long stri
 
 // dslash_staged.cu: launch the staged kernel of launch variant 3-5; false (nothing launched) where
 // it does not apply.  red_shm = dynamic shared memory of the fused reduction.
+// dslash_rb2.cu: launch variant 7 (two right-hand sides per thread), FP32 only.
+bool launch_dslash_rb2(const DslashParams& pr, int epi, int red, long blocks, int tpb, size_t red_shm,
+                       cudaStream_t st);
 bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, int red, long blocks, int tpb,
                           size_t red_shm, int variant, cudaStream_t st);
 

@@ -843,7 +843,7 @@ bool launch_p(const DslashParams& pr, int epi, int red, long blocks, int tpb, si
 
 bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, int red, long blocks, int tpb,
                           size_t red_shm, int variant, cudaStream_t st) {
-  if (prec == P64 || dag || variant < 3 || variant > 6) return false;
+  if (prec == P64 || dag || variant < 3 || variant > 7) return false;
   const long nr = pr.nrhs;
   if (variant == 4) {  // bulk-copy staged spinors, staging depth 3
     if (nr % 32 != 0 || tpb % 32 != 0) return false;
@@ -855,6 +855,10 @@ bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, i
   if (nr < 8 || nr > 128 || (nr & (nr - 1)) != 0 || tpb != 128) return false;
   if (pr.g.Vh % (128 / nr) != 0 || blocks * (128 / nr) != pr.g.Vh) return false;
   if (12 * pr.g.Vh * nr >= (1L << 31)) return false;
+  if (variant == 7) {  // two right-hand sides per thread on paired arithmetic (dslash_rb2.cu)
+    if (prec != P32) return false;
+    return launch_dslash_rb2(pr, epi, red, blocks, tpb, red_shm, st);
+  }
   if (variant == 6) {  // paired arithmetic and pipelined spinor copies: FP32 storage only
     if (prec != P32 || red_shm > 8 * 128 * sizeof(double)) return false;
     open_sl3_all();

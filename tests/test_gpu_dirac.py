@@ -149,7 +149,7 @@ def test_dslash_launch_variants_agree(prec, nrhs):
     for domain in (False, True):
         ref_op = op.restricted(ext) if domain else op
         ref = None
-        for v in range(7):
+        for v in range(8):
             ctx.set_dslash_variant(p, nrhs, v)
             ctx.set_dslash_variant(lqcd.LQCD_PREC_F64, nrhs, v % 3)  # the FP64 true-residual launches
             x = np.zeros_like(b)
@@ -178,7 +178,7 @@ def oracle_schur(op, x):
 
 
 # storage precision -> (launch variants, max relative error against the FP64 oracle)
-SCHUR_PRECS = {"f64": (range(3), 1e-13), "f32": (range(7), 2e-6), "f16": (range(7), 4e-3)}
+SCHUR_PRECS = {"f64": (range(3), 1e-13), "f32": (range(8), 2e-6), "f16": (range(8), 4e-3)}
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
