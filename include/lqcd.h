@@ -390,15 +390,16 @@ int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, 
  * clover copied once per site into shared memory, 32-bit indexing, register cap 80 (FP32 and
  * FP16, nrhs a power of two in [8, 128]); 4: the neighbour spinors staged in shared memory by
  * bulk asynchronous copies 3 hops ahead (FP32 and FP16, nrhs a multiple of 32); 5: as 3 with the
- * hopping arithmetic on paired FP32 instructions (two lanes per fused multiply-add); 6: as 5 with
- * each thread's neighbour spinors copied asynchronously two hops ahead into shared memory (FP32
- * only).  Where a variant does
+ * hopping arithmetic on paired FP32 instructions (two lanes per fused multiply-add); 6: as 3 with
+ * each thread's neighbour spinors copied asynchronously one hop ahead into shared memory; 7: two
+ * right-hand sides per thread on paired FP32 instructions (6 and 7: FP32 only, 7: nrhs >= 16).
+ * Where a variant does
  * not apply it runs as variant 0.  FP64 has variants 0 / 1 / 2 with register caps 128 / 255 / 168;
  * LQCD_PREC_DF (the true-residual kernel, timed as such) variants 0 / 1 / 2 with caps 255 / 168 /
  * 128.  All variants compute the same arithmetic (variant 5 may order the two products of an
- * imaginary part differently; so may 6).  lqcd_set_dslash_variant
+ * imaginary part differently; so may 7).  lqcd_set_dslash_variant
  * installs a known choice (e.g. from a cache) without timing.  Errors: INVALID_ARG (variant
- * outside 0..6), STATE (no gauge), TIMEOUT (a staged copy did not complete within its wait
+ * outside 0..7), STATE (no gauge), TIMEOUT (a staged copy did not complete within its wait
  * limit; the solvers report the same). */
 int lqcd_tune_dslash(lqcd_ctx* ctx, int prec, int nrhs, int* best_variant, double* best_ms);
 int lqcd_set_dslash_variant(lqcd_ctx* ctx, int prec, int nrhs, int variant);

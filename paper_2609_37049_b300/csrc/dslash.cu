@@ -18,9 +18,10 @@ namespace lqcd {
 // MINB: minimum resident blocks of 128 threads the compiler must allow (register cap 255 / 168 /
 // 128 / 80 / 64 per thread for MINB = 2 / 3 / 4 / 6 / 8).  Launch variants 0-2 are this kernel
 // with MINB 4 / 6 / 8 (FP64: 4 / 2 / 3);
-// variants 3-6 are the staged kernels of dslash_staged.cu (3: links and clover staged once per
-// site in shared memory; 4: neighbour spinors staged by bulk copies; 5: as 3 on paired FP32
-// arithmetic; 6: as 5 with per-thread asynchronous spinor copies) where they apply (FP32 /
+// variants 3-7 are the staged kernels of dslash_staged.cu and dslash_rb2.cu (3: links and clover
+// staged once per site in shared memory; 4: neighbour spinors staged by bulk copies; 5: as 3 on
+// paired FP32 arithmetic; 6: as 3 with per-thread asynchronous spinor copies; 7: two right-hand
+// sides per thread on paired FP32 arithmetic) where they apply (FP32 /
 // FP16, the solver's epilogues, RHS counts as stated there), else variant 0.  The autotuner picks
 // the variant per precision and RHS count.
 template <int P, int EPI, bool DAG, int RED>

@@ -13,6 +13,8 @@
 //   the same way, and the lower ones wherever the direction's spin reconstruction keeps the pair
 //   order (mu = z, t).  Same arithmetic as variant 3 (each output lane rounds like the scalar
 //   code), other than the order of the two products in an imaginary part.
+// * variant 6 (dslash_sl3_kernel): variant 3 with each thread's neighbour spinors copied one hop
+//   ahead into its own slots of a shared-memory ring by asynchronous copies (FP32 storage).
 // * variant 4 (dslash_pipe_kernel): the eight neighbour spinors of every output site staged by
 //   bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier) 3 hops ahead of
 //   the arithmetic.  One warp = 32 right-hand sides of one output site (nrhs a multiple of 32),
@@ -541,14 +543,14 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl2_kernel(const DslashParam
   dslash_epilogue<P, EPI, RED, true>(pr, cb, (long)cb * nr + rhs, (long)stride, rhs, acc, sclov[sl]);
 }
 
-// ------------------------------------------------------------------ variant 6: paired FP32 + pipelined spinors
-// Variant 5 whose eight neighbour spinors are fetched by each thread into its own slots of a
+// ------------------------------------------------------------------ variant 6: pipelined neighbour spinors
+// Variant 3 whose eight neighbour spinors are fetched by each thread into its own slots of a
 // kPipe-deep ring in shared memory with asynchronous copies (cp.async, 16 bytes each, L2 only),
-// kPipe - 1 hops ahead of the arithmetic, so a thread has up to kPipe - 1 hops of loads in flight
-// without holding them in registers.  Ring layout [stage][chunk][thread] (float4): each thread
-// reads back only what it copied (a wait on its own copy groups, no barrier), and a warp's
+// kPipe - 1 hops ahead of the arithmetic, so a thread has the next hop's loads in flight while it
+// computes without holding them in registers.  Ring layout [stage][chunk][thread] (float4): each
+// thread reads back only what it copied (a wait on its own copy groups, no barrier), and a warp's
 // accesses are contiguous.  FP32 storage only.
-constexpr int kPipe = 3;
+constexpr int kPipe = 2;
 constexpr size_t kPipeBytes = (size_t)kPipe * 6 * 128 * sizeof(float4);
 
 LQCD_D void cp_async16(void* dst, const void* src) {
@@ -570,9 +572,14 @@ LQCD_D void pipe_issue(const DslashParams& pr, float4* ring, const int (&nb)[8],
   cp_async_commit();  // one group per hop (empty past the last), so the wait count stays uniform
 }
 
+// hop K = 2 mu (+1 for the backward hop) with its neighbour from the ring and its link from the
+// per-site staging (variant-3 format)
 template <int K>
 LQCD_D void pipe_hop(const DslashParams& pr, float4* ring, const int (&nb)[8], int stride, int coef, bool valid,
-                     const float4* L, float2 (&ur)[3], float2 (&ui)[3], float2 (&lr)[3], float2 (&li)[3]) {
+                     const float4* L, cplx<float> (&acc)[12]) {
+  constexpr int MU = K / 2;
+  constexpr bool FWD = (K % 2) == 0;
+  constexpr int S = FWD ? -1 : 1;  // H (not H^dag): forward projector 1 - gamma_mu
   pipe_issue<K + kPipe - 1>(pr, ring, nb, stride, valid);
   cp_async_wait_pipe();  // this thread's copies of hop K have landed
   const float4* src = ring + (K % kPipe) * 6 * 128 + threadIdx.x;
@@ -583,10 +590,24 @@ LQCD_D void pipe_hop(const DslashParams& pr, float4* ring, const int (&nb)[8], i
     p[2 * c] = {v.x, v.y};
     p[2 * c + 1] = {v.z, v.w};
   }
-  if (coef != 0) hop_pair_p<K / 2, (K % 2) == 0>(p, coef, L, ur, ui, lr, li);
+  if (coef == 0) return;
+  cplx<float> h[2][3], w[2][3], u[3][3];
+  project<MU, S>(p, h);
+  link_from_shared(L, u);
+  if constexpr (FWD)
+    su3_mul(u, h, w);
+  else
+    su3_dag_mul(u, h, w);
+  if (coef < 0) {
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) w[q][a] = -w[q][a];
+  }
+  accumulate<MU, S>(acc, w);
 }
 
-// Dynamic shared memory: [fused-reduction scratch | ring | links S x 8 x 9 | clover S x 18] (float4).
+// Dynamic shared memory: [fused-reduction scratch | ring | links S x 8 x 5 | clover S x 18] (float4).
 template <int EPI, int RED, int MINB>
 __global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParams pr) {
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -594,7 +615,7 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParam
   const int lg = __ffs(nr) - 1;
   const int S = 128 >> lg;
   float4* ring = reinterpret_cast<float4*>(dsm + pr.pipe_off);
-  float4 (*slink)[8][9] = reinterpret_cast<float4 (*)[8][9]>(ring + kPipe * 6 * 128);
+  float4 (*slink)[8][5] = reinterpret_cast<float4 (*)[8][5]>(ring + kPipe * 6 * 128);
   float4 (*sclov)[18] = reinterpret_cast<float4 (*)[18]>(slink + S);
   const Geom& g = pr.g;
   const int cb0 = blockIdx.x * S;
@@ -617,9 +638,8 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParam
       nb[2 * mu + 1] = ((s + ((cm[mu] == 0) ? sm[mu] * (Lm[mu] - 1) : -sm[mu])) >> 1) * nr + rhs;
     }
   }
-  static_assert(kPipe == 3, "two hops are issued ahead");
-  pipe_issue<0>(pr, ring, nb, stride, valid);  // the first hops' copies run under the link staging
-  pipe_issue<1>(pr, ring, nb, stride, valid);
+  static_assert(kPipe == 2, "one hop is issued ahead");
+  pipe_issue<0>(pr, ring, nb, stride, valid);  // the first hop's copies run under the link staging
   for (int j = threadIdx.x; j < 26 * S; j += 128) {
     if (j < 8 * S) {  // link j & 7 of site j >> 3, third row rebuilt once
       const int site = j >> 3, k = j & 7, c = cb0 + site;
@@ -640,11 +660,11 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParam
         cplx<float> u[3][3];
         load_link<P32>(pr.U, g.Vh, mu, par, lcb, u);
         float4* L = slink[site][k];
-#pragma unroll
-        for (int e = 0; e < 9; e++) {
-          const cplx<float> v = u[e / 3][e % 3];
-          L[e] = make_float4(v.re, v.re, v.im, v.im);
-        }
+        L[0] = make_float4(u[0][0].re, u[0][0].im, u[0][1].re, u[0][1].im);
+        L[1] = make_float4(u[0][2].re, u[0][2].im, u[1][0].re, u[1][0].im);
+        L[2] = make_float4(u[1][1].re, u[1][1].im, u[1][2].re, u[1][2].im);
+        L[3] = make_float4(u[2][0].re, u[2][0].im, u[2][1].re, u[2][1].im);
+        L[4] = make_float4(u[2][2].re, u[2][2].im, 0.f, 0.f);
       }
     } else {  // clover chunk e of site q / 18
       const int q = j - 8 * S, site = q / 18, e = q - site * 18, c = cb0 + site;
@@ -653,41 +673,33 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParam
   }
   __syncthreads();
   if (RED == RED_NONE && !valid) {
-    asm volatile("cp.async.wait_all;" ::: "memory");  // nothing was issued; kept for symmetry
+    asm volatile("cp.async.wait_all;" ::: "memory");
     return;
   }
   const int sl = threadIdx.x >> lg;
   const int cf = __ldg(pr.tc + t), cbk = __ldg(pr.tc + (t == 0 ? g.Lt - 1 : t - 1));
-  float2 ur[3], ui[3], lr[3], li[3];
-#pragma unroll
-  for (int c = 0; c < 3; c++) ur[c] = ui[c] = lr[c] = li[c] = make_float2(0.f, 0.f);
-  pipe_hop<0>(pr, ring, nb, stride, 1, valid, slink[sl][0], ur, ui, lr, li);
-  pipe_hop<1>(pr, ring, nb, stride, 1, valid, slink[sl][1], ur, ui, lr, li);
-  pipe_hop<2>(pr, ring, nb, stride, 1, valid, slink[sl][2], ur, ui, lr, li);
-  pipe_hop<3>(pr, ring, nb, stride, 1, valid, slink[sl][3], ur, ui, lr, li);
-  pipe_hop<4>(pr, ring, nb, stride, 1, valid, slink[sl][4], ur, ui, lr, li);
-  pipe_hop<5>(pr, ring, nb, stride, 1, valid, slink[sl][5], ur, ui, lr, li);
-  pipe_hop<6>(pr, ring, nb, stride, cf, valid, slink[sl][6], ur, ui, lr, li);
-  pipe_hop<7>(pr, ring, nb, stride, cbk, valid, slink[sl][7], ur, ui, lr, li);
-  asm volatile("cp.async.wait_all;" ::: "memory");
   cplx<float> acc[12];
 #pragma unroll
-  for (int c = 0; c < 3; c++) {
-    acc[c] = {ur[c].x, ui[c].x};
-    acc[3 + c] = {ur[c].y, ui[c].y};
-    acc[6 + c] = {lr[c].x, li[c].x};
-    acc[9 + c] = {lr[c].y, li[c].y};
-  }
+  for (int k = 0; k < 12; k++) acc[k] = {0.f, 0.f};
+  pipe_hop<0>(pr, ring, nb, stride, 1, valid, slink[sl][0], acc);
+  pipe_hop<1>(pr, ring, nb, stride, 1, valid, slink[sl][1], acc);
+  pipe_hop<2>(pr, ring, nb, stride, 1, valid, slink[sl][2], acc);
+  pipe_hop<3>(pr, ring, nb, stride, 1, valid, slink[sl][3], acc);
+  pipe_hop<4>(pr, ring, nb, stride, 1, valid, slink[sl][4], acc);
+  pipe_hop<5>(pr, ring, nb, stride, 1, valid, slink[sl][5], acc);
+  pipe_hop<6>(pr, ring, nb, stride, cf, valid, slink[sl][6], acc);
+  pipe_hop<7>(pr, ring, nb, stride, cbk, valid, slink[sl][7], acc);
+  asm volatile("cp.async.wait_all;" ::: "memory");
   dslash_epilogue<P32, EPI, RED, true>(pr, cb, (long)cb * nr + rhs, (long)stride, rhs, acc, sclov[sl]);
 }
 
 // largest dynamic shared memory of a variant-6 launch: 8-double reduction scratch per thread,
 // the ring, and the links and clover of 16 sites
-constexpr size_t kSl3MaxShm = 8 * 128 * sizeof(double) + kPipeBytes + (size_t)kMaxSites * (72 + 18) * sizeof(float4);
+constexpr size_t kSl3MaxShm = 8 * 128 * sizeof(double) + kPipeBytes + (size_t)kMaxSites * (40 + 18) * sizeof(float4);
 
 template <int EPI, int RED>
 void open_sl3() {
-  cudaFuncSetAttribute(dslash_sl3_kernel<EPI, RED, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSl3MaxShm);
+  cudaFuncSetAttribute(dslash_sl3_kernel<EPI, RED, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSl3MaxShm);
 }
 
 // Raise the dynamic shared-memory limit of every variant-6 instantiation once, before its first
@@ -709,8 +721,8 @@ void launch_sl3(const DslashParams& pr, long blocks, size_t red_shm, cudaStream_
   DslashParams q = pr;
   q.pipe_off = (int)((red_shm + 127) / 128 * 128);
   const int S = 128 / pr.nrhs;
-  const size_t shm = q.pipe_off + kPipeBytes + (size_t)S * (72 + 18) * sizeof(float4);
-  dslash_sl3_kernel<EPI, RED, 4><<<blocks, 128, shm, st>>>(q);
+  const size_t shm = q.pipe_off + kPipeBytes + (size_t)S * (40 + 18) * sizeof(float4);
+  dslash_sl3_kernel<EPI, RED, 6><<<blocks, 128, shm, st>>>(q);
   lqcd::count_launch();
 }
 
