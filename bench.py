@@ -547,17 +547,17 @@ def run_ours(args, rank, world):
 
 
 def captured_traffic(variant, site_rhs):
-    """DRAM bytes of one FP32 variant-3 launch, scaled from the committed ncu capture
-    (profiles/dslash_f32_24x24x24x48_nrhs16.md: bytes per (site, RHS)) to site_rhs pairs; None
-    when another variant runs or the kernel's sources changed since the capture."""
+    """DRAM bytes of one FP32 dslash launch of the captured variant, scaled from the committed ncu
+    capture (profiles/dslash_f32_24x24x24x48_nrhs16.md: bytes per (site, RHS)) to site_rhs pairs;
+    None when another variant runs or the kernel's sources changed since the capture."""
     import hashlib
-    if variant != 3:
-        return None
     try:
         with open(os.path.join(ROOT, "profiles", "dslash_f32_24x24x24x48_nrhs16.md")) as f:
             rec = dict(line.split(":", 1) for line in f.read().splitlines()
-                       if line.startswith(("source_sha256_16:", "traffic_bytes_per_site_rhs:")))
+                       if line.startswith(("source_sha256_16:", "traffic_bytes_per_site_rhs:", "traffic_variant:")))
     except OSError:
+        return None
+    if rec.get("traffic_variant", "").strip() != str(variant):
         return None
     h = hashlib.sha256()
     for name in ("dslash_staged.cu", "dslash_ops.cuh", "lqcd_common.cuh"):
@@ -648,7 +648,8 @@ def extras(W, peak, peak_kind, dev):
         dsl[name] = {"ms": ms_l, "GBs": by / ms_l / 1e6, "bytes": by, "nrhs": nr}
     achieved = dsl["f32"]["GBs"]
     v32 = int(W.tuning["variant"].get(str(lqcd.LQCD_PREC_F32), {}).get(str(nbat), 0))
-    kname = {3: "dslash_sl_kernel", 4: "dslash_pipe_kernel"}.get(v32, "dslash_kernel")
+    kname = {3: "dslash_sl_kernel", 4: "dslash_pipe_kernel", 5: "dslash_sl2_kernel", 6: "dslash_sl3_kernel",
+             7: "dslash_rb2_kernel"}.get(v32, "dslash_kernel")
     out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "traffic": captured_traffic(v32, np.prod(W.dims) // 2 * nbat), "peak_kind": peak_kind,
                        "kernel": "%s<P32,EPI_CH> (launch variant %d: eo hopping + A^-1, %d RHS)" % (kname, v32,

@@ -693,9 +693,9 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParam
   dslash_epilogue<P32, EPI, RED, true>(pr, cb, (long)cb * nr + rhs, (long)stride, rhs, acc, sclov[sl]);
 }
 
-// largest dynamic shared memory of a variant-6 launch: 8-double reduction scratch per thread,
-// the ring, and the links and clover of 16 sites
-constexpr size_t kSl3MaxShm = 8 * 128 * sizeof(double) + kPipeBytes + (size_t)kMaxSites * (40 + 18) * sizeof(float4);
+// largest dynamic shared memory of a variant-6 launch: the ring, and the links and clover of 16
+// sites
+constexpr size_t kSl3MaxShm = kPipeBytes + (size_t)kMaxSites * (40 + 18) * sizeof(float4);
 
 template <int EPI, int RED>
 void open_sl3() {
@@ -708,9 +708,6 @@ void open_sl3_all() {
   static bool done = false;
   if (done) return;
   done = true;
-  open_sl3<EPI_Y_CH, RED_TS_R0>();
-  open_sl3<EPI_Y_CH, RED_DOT_Z>();
-  open_sl3<EPI_Y_CH, RED_DOT_Y_NORM>();
   open_sl3<EPI_CH, RED_NONE>();
   open_sl3<EPI_Y_CH, RED_NONE>();
   open_sl3<EPI_C_YH, RED_NONE>();
@@ -727,24 +724,15 @@ void launch_sl3(const DslashParams& pr, long blocks, size_t red_shm, cudaStream_
 }
 
 bool launch_sl3_e(const DslashParams& pr, int epi, int red, long blocks, size_t red_shm, cudaStream_t st) {
-  if (red == RED_TS_R0) {
-    if (epi != EPI_Y_CH) return false;
-    launch_sl3<EPI_Y_CH, RED_TS_R0>(pr, blocks, red_shm, st);
-  } else if (red == RED_DOT_Z) {
-    if (epi != EPI_Y_CH) return false;
-    launch_sl3<EPI_Y_CH, RED_DOT_Z>(pr, blocks, red_shm, st);
-  } else if (red == RED_DOT_Y_NORM) {
-    if (epi != EPI_Y_CH) return false;
-    launch_sl3<EPI_Y_CH, RED_DOT_Y_NORM>(pr, blocks, red_shm, st);
-  } else if (epi == EPI_CH) {
+  if (red != RED_NONE) return false;
+  if (epi == EPI_CH)
     launch_sl3<EPI_CH, RED_NONE>(pr, blocks, red_shm, st);
-  } else if (epi == EPI_Y_CH) {
+  else if (epi == EPI_Y_CH)
     launch_sl3<EPI_Y_CH, RED_NONE>(pr, blocks, red_shm, st);
-  } else if (epi == EPI_C_YH) {
+  else if (epi == EPI_C_YH)
     launch_sl3<EPI_C_YH, RED_NONE>(pr, blocks, red_shm, st);
-  } else {
+  else
     return false;
-  }
   return true;
 }
 
@@ -871,8 +859,9 @@ bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, i
     if (prec != P32) return false;
     return launch_dslash_rb2(pr, epi, red, blocks, tpb, red_shm, st);
   }
-  if (variant == 6) {  // paired arithmetic and pipelined spinor copies: FP32 storage only
-    if (prec != P32 || red_shm > 8 * 128 * sizeof(double)) return false;
+  if (variant == 6 && prec == P32 && red == RED_NONE) {  // pipelined neighbour copies
+    // (the launches with fused reductions run as variant 3: the reduction scratch beside the
+    // ring would cost a resident block per SM)
     open_sl3_all();
     return launch_sl3_e(pr, epi, red, blocks, red_shm, st);
   }
