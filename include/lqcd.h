@@ -391,8 +391,7 @@ int lqcd_nn_train(lqcd_ctx* ctx, int n_pairs, int epochs, int batch, double lr, 
  * FP16, nrhs a power of two in [8, 128]); 4: the neighbour spinors staged in shared memory by
  * bulk asynchronous copies 3 hops ahead (FP32 and FP16, nrhs a multiple of 32); 5: as 3 with the
  * hopping arithmetic on paired FP32 instructions (two lanes per fused multiply-add); 6: as 3 with
- * each thread's neighbour spinors copied asynchronously one hop ahead into shared memory (the
- * launches with fused Krylov dot products run as 3); 7: two
+ * each thread's neighbour spinors copied asynchronously one hop ahead into shared memory; 7: two
  * right-hand sides per thread on paired FP32 instructions (6 and 7: FP32 only, 7: nrhs >= 16).
  * Where a variant does
  * not apply it runs as variant 0.  FP64 has variants 0 / 1 / 2 with register caps 128 / 255 / 168;

@@ -607,7 +607,9 @@ LQCD_D void pipe_hop(const DslashParams& pr, float4* ring, const int (&nb)[8], i
   accumulate<MU, S>(acc, w);
 }
 
-// Dynamic shared memory: [fused-reduction scratch | ring | links S x 8 x 5 | clover S x 18] (float4).
+// Dynamic shared memory: [ring | links S x 8 x 5 | clover S x 18] (float4); the fused reductions
+// scratch (at most 8 doubles per thread, smaller than the ring) overlays the ring once the hops are
+// done.
 template <int EPI, int RED, int MINB>
 __global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParams pr) {
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -690,6 +692,9 @@ __global__ void __launch_bounds__(128, MINB) dslash_sl3_kernel(const DslashParam
   pipe_hop<6>(pr, ring, nb, stride, cf, valid, slink[sl][6], acc);
   pipe_hop<7>(pr, ring, nb, stride, cbk, valid, slink[sl][7], acc);
   asm volatile("cp.async.wait_all;" ::: "memory");
+  // the fused reductions' scratch overlays the ring (dynamic offset 0): every thread must be done
+  // with its ring slots first
+  if constexpr (RED != RED_NONE) __syncthreads();
   dslash_epilogue<P32, EPI, RED, true>(pr, cb, (long)cb * nr + rhs, (long)stride, rhs, acc, sclov[sl]);
 }
 
@@ -708,6 +713,9 @@ void open_sl3_all() {
   static bool done = false;
   if (done) return;
   done = true;
+  open_sl3<EPI_Y_CH, RED_TS_R0>();
+  open_sl3<EPI_Y_CH, RED_DOT_Z>();
+  open_sl3<EPI_Y_CH, RED_DOT_Y_NORM>();
   open_sl3<EPI_CH, RED_NONE>();
   open_sl3<EPI_Y_CH, RED_NONE>();
   open_sl3<EPI_C_YH, RED_NONE>();
@@ -716,23 +724,34 @@ void open_sl3_all() {
 template <int EPI, int RED>
 void launch_sl3(const DslashParams& pr, long blocks, size_t red_shm, cudaStream_t st) {
   DslashParams q = pr;
-  q.pipe_off = (int)((red_shm + 127) / 128 * 128);
+  q.pipe_off = 0;
+  (void)red_shm;  // fits in the ring (checked by the caller)
   const int S = 128 / pr.nrhs;
-  const size_t shm = q.pipe_off + kPipeBytes + (size_t)S * (40 + 18) * sizeof(float4);
+  const size_t shm = kPipeBytes + (size_t)S * (40 + 18) * sizeof(float4);
   dslash_sl3_kernel<EPI, RED, 6><<<blocks, 128, shm, st>>>(q);
   lqcd::count_launch();
 }
 
 bool launch_sl3_e(const DslashParams& pr, int epi, int red, long blocks, size_t red_shm, cudaStream_t st) {
-  if (red != RED_NONE) return false;
-  if (epi == EPI_CH)
+  if (red_shm > kPipeBytes) return false;
+  if (red == RED_TS_R0) {
+    if (epi != EPI_Y_CH) return false;
+    launch_sl3<EPI_Y_CH, RED_TS_R0>(pr, blocks, red_shm, st);
+  } else if (red == RED_DOT_Z) {
+    if (epi != EPI_Y_CH) return false;
+    launch_sl3<EPI_Y_CH, RED_DOT_Z>(pr, blocks, red_shm, st);
+  } else if (red == RED_DOT_Y_NORM) {
+    if (epi != EPI_Y_CH) return false;
+    launch_sl3<EPI_Y_CH, RED_DOT_Y_NORM>(pr, blocks, red_shm, st);
+  } else if (epi == EPI_CH) {
     launch_sl3<EPI_CH, RED_NONE>(pr, blocks, red_shm, st);
-  else if (epi == EPI_Y_CH)
+  } else if (epi == EPI_Y_CH) {
     launch_sl3<EPI_Y_CH, RED_NONE>(pr, blocks, red_shm, st);
-  else if (epi == EPI_C_YH)
+  } else if (epi == EPI_C_YH) {
     launch_sl3<EPI_C_YH, RED_NONE>(pr, blocks, red_shm, st);
-  else
+  } else {
     return false;
+  }
   return true;
 }
 
@@ -859,11 +878,9 @@ bool launch_dslash_staged(const DslashParams& pr, int prec, int epi, bool dag, i
     if (prec != P32) return false;
     return launch_dslash_rb2(pr, epi, red, blocks, tpb, red_shm, st);
   }
-  if (variant == 6 && prec == P32 && red == RED_NONE) {  // pipelined neighbour copies
-    // (the launches with fused reductions run as variant 3: the reduction scratch beside the
-    // ring would cost a resident block per SM)
+  if (variant == 6 && prec == P32) {  // pipelined neighbour copies
     open_sl3_all();
-    return launch_sl3_e(pr, epi, red, blocks, red_shm, st);
+    if (launch_sl3_e(pr, epi, red, blocks, red_shm, st)) return true;
   }
   if (variant == 5) {  // paired operands take aligned register pairs: cap 96 instead of 80
     if (prec == P32) return launch_sl_e<P32, 5>(pr, epi, red, blocks, red_shm, st, true);
