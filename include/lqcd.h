@@ -58,8 +58,9 @@ enum { LQCD_HOST = 0, LQCD_DEVICE = 1 };
 enum { LQCD_MODE_FULL = 0, LQCD_MODE_DOMAIN = 1 };
 enum { LQCD_SINKS_DIAG = 0, LQCD_SINKS_ALL = 1, LQCD_SINKS_DIAG_SRCV = 2 };
 
-/* Krylov solvers.  All are judged by the FP64 true residual ||b - D x|| / ||b|| of the
- * unpreconditioned operator (per right-hand side, and per domain for domain solves):
+/* Krylov solvers.  All are judged by the true residual ||b - D x|| / ||b|| of the
+ * unpreconditioned operator computed from the FP64 fields (per right-hand side, and per domain for
+ * domain solves; the residual's arithmetic is lqcd_solve_params.residual):
  *   LQCD_SOLVER_BICGSTAB64: even-odd preconditioned BiCGStab entirely in FP64 (the plain solver);
  *   LQCD_SOLVER_MIXED:      FP64 defect correction around an FP32 even-odd BiCGStab
  *                           (inner_prec = LQCD_PREC_F32) or an FP32 flexible GCR preconditioned

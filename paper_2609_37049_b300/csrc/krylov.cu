@@ -1,8 +1,9 @@
 // Krylov solver driver for the full operator D and the Dirichlet domain operator D_Lambda
 // (Sec. 2.1; the paper's "inversions", Sec. 4).
 //
-// Every solve is an FP64 defect-correction loop judged by the FP64 true residual of the
-// unpreconditioned operator, per system (one right-hand side, or one domain of one right-hand
+// Every solve is an FP64 defect-correction loop judged by the true residual of the
+// unpreconditioned operator, computed from the FP64 fields (in double-float arithmetic, or FP64
+// with residual = 1), per system (one right-hand side, or one domain of one right-hand
 // side: because D_Lambda is block diagonal over domains, a multi-site source with one source
 // timeslice per domain is as many independent systems, each with its own Krylov scalars):
 //
