@@ -70,8 +70,8 @@ LQCD_D cdf ld_split(const double2* f, long i) {
   return {split_d(v.x), split_d(v.y)};
 }
 
-// double(hi) + double(lo): the float-to-double conversions by bit manipulation (exact for normal
-// floats and zero), one FP64 addition
+// The float-to-double conversion by bit manipulation (exact for normal floats and zero; no FP64
+// pipe work).
 LQCD_D double f2d_bits(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned e = (b >> 23) & 0xffu;
@@ -79,7 +79,11 @@ LQCD_D double f2d_bits(float f) {
   const unsigned hw = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
   return __hiloint2double((int)hw, (int)((b & 0x7u) << 29));
 }
-LQCD_D double to_double(dfl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+// The stored residual: its high part.  The cancellation b - D x is what needs the double-float
+// arithmetic; the result, once normalised, is r to 2^-24 of |r| (|lo| <= ulp(hi) / 2), far finer
+// than its uses need (its norm against 1e-10 ||b||, and the FP32 right-hand side of the next inner
+// solve).
+LQCD_D double to_double(dfl a) { return f2d_bits(a.hi); }
 
 struct ResDF {
   Geom g;
