@@ -1261,7 +1261,7 @@ extern "C" int lqcd_dslash_bench(lqcd_ctx* c, int prec, int nrhs, int n_iter, in
   // solver does), y, z, writing out
   void* xs = P == PDF ? ws_get(c, "bench_split", sb) : nullptr;
   if (P == PDF && !xs) return set_error(c, LQCD_ERR_OOM, "dslash_bench: OOM");
-  if (P == PDF) split_field(in, xs, (long)(sb / 16), c->work);
+  if (P == PDF) split_neighbours(in, xs, (long)(sb / 16), nrhs, c->work);
   auto launch = [&](int var) {
     if (P == PDF)
       launch_residual_df(g, xs, in, in, out, c->Udf, (const char*)c->Adf + clover_bytes(g, P64), coord_of(c, 1),

@@ -557,7 +557,7 @@ static void batch_finish_cycle(lqcd_ctx* c, Batch& B, const double2* b, double2*
   const size_t cb64 = clover_bytes(g, P64);
   for (int p = 0; p < 2; p++) {
     if (B.res_prec == PDF) {
-      split_field(off(x, B.sb64, 1 - p), B.xdf, (long)(B.sb64 / 16), B.st);
+      split_neighbours(off(x, B.sb64, 1 - p), B.xdf, (long)(B.sb64 / 16), B.nrhs, B.st);
       launch_residual_df(g, B.xdf, off(x, B.sb64, p), off(b, B.sb64, p), off(B.r64, B.sb64, p), c->Udf,
                          off(c->Adf, cb64, p), coord_of(c, p), B.tc, p, B.nrhs, c->kappa, B.v64, B.st);
     } else {

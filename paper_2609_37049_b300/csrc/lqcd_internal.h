@@ -99,9 +99,12 @@ struct DslashCall {
 
 // dslash_df.cu: split an FP64 field of n_complex entries to double-float (float4 per entry), and
 // the true residual out = z - (A y - kappa H xn) of parity out_par in double-float arithmetic
-// (xn: the neighbour parity, split; y, z, out: FP64; U_split, A_split: split links and the
-// parity's clover; variant 0 / 1 / 2: register caps 255 / 168 / 128).
+// (xn: the neighbour parity, split by split_neighbours; y, z, out: FP64; U_split, A_split: split
+// links and the parity's clover; variant 0 / 1 / 2: register caps 255 / 168 / 128).
 void split_field(const void* in, void* out, long n_complex, cudaStream_t st);
+// the neighbour parity of the residual in the layout launch_residual_df reads for nrhs (pairs of
+// right-hand sides interleaved when nrhs is even)
+void split_neighbours(const void* in, void* out, long n_complex, int nrhs, cudaStream_t st);
 void launch_residual_df(const Geom& g, const void* xn_split, const void* y, const void* z, void* out,
                         const void* U_split, const void* A_split, const unsigned* coord, const signed char* tc,
                         int out_par, int nrhs, double kappa, int variant, cudaStream_t st);
