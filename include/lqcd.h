@@ -90,7 +90,8 @@ typedef struct {
   int use_graph;     /* 1: replay Krylov iterations from a captured CUDA graph */
   double inner_tol;  /* residual reduction per defect-correction cycle; 0 -> default */
   int max_outer;     /* cap on defect-correction cycles; 0 -> 20 */
-  int check_every;   /* Krylov iterations between host convergence checks; 0 -> 8 */
+  int check_every;   /* Krylov iterations between convergence checks; 0 -> 1 for batches of at
+                        least 2^22 (site, RHS) pairs per parity, up to 8 for smaller ones */
   int gcr_nkrylov;   /* flexible GCR restart length; 0 -> 8 */
   int precond_iters; /* FP16 MR preconditioner sweeps per application; 0 -> 6; < 0: no preconditioner
                         (plain FP32 GCR inside the defect correction, for comparisons) */

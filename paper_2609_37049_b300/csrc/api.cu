@@ -355,7 +355,7 @@ void lqcd_default_params(lqcd_solve_params* p) {
   p->use_graph = 1;
   p->inner_tol = 0;
   p->max_outer = 20;
-  p->check_every = 8;
+  p->check_every = 0;  // chosen per batch from its size
   p->gcr_nkrylov = 8;
   p->precond_iters = 6;
   p->pipeline = 1;

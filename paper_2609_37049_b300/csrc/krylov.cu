@@ -347,7 +347,13 @@ static int plan_batch(lqcd_ctx* c, int slot, int nrhs, int domain, const lqcd_so
   B.tol = prm.tol > 0 ? prm.tol : 1e-10;
   B.max_iter = prm.max_iter > 0 ? prm.max_iter : 20000;
   B.max_outer = prm.max_outer > 0 ? prm.max_outer : 20;
-  B.chunk = prm.check_every > 0 ? prm.check_every : 8;
+  // Inner iterations between convergence checks.  A batch runs until its slowest system converges,
+  // rounded up to whole chunks, so a large chunk wastes up to chunk - 1 full iterations per cycle;
+  // a check costs a few microseconds (a small kernel and a conditional graph node, or a 4-byte
+  // read-back).  Default: every iteration once a batch holds >= 2^22 (site, RHS) pairs per parity
+  // (an iteration then takes milliseconds), up to every 8th for small batches.
+  const long pairs = std::max(1L, g.Vh * (long)nrhs);
+  B.chunk = prm.check_every > 0 ? prm.check_every : (int)std::min(8L, std::max(1L, ((1L << 22) + pairs - 1) / pairs));
   B.graph = false;
   B.fallback = 0;
   B.dslash_host = 0;
